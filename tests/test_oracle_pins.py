@@ -1,0 +1,506 @@
+"""Pins for the CPU oracle against things other than itself.
+
+* values printed in the paper (Sec. 3 and Sec. 7.1 worked examples),
+* brute force on tiny inputs through an independent characterisation:
+  the Bic-slice definition of the match (Sec. 3: parenmatch(s)[j] is the
+  largest i with Bic(s[i..j]).b = 1), explicit ancestor enumeration for the
+  clip (Sec. 6.1 definition) and explicit descendant ranges for the union
+  (Sec. 6.2: descendants are the contiguous slice from open to close),
+* invariants that hold at any size,
+* closed forms for the transform monoid and finite differences for its
+  adjoint.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_11659_gb300 import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "paper_examples.json")
+CH = {"(": 1, ")": 3, "L": 0, "C": 1, "B": 2, "X": 3}
+EMPTY = np.array([np.inf, np.inf, -np.inf, -np.inf], np.float32)
+
+
+def gold():
+    with open(GOLD) as f:
+        return json.load(f)
+
+
+def kinds_of(s):
+    return np.array([CH[c] for c in s], np.uint8)
+
+
+# --- independent brute force --------------------------------------------
+
+def bic_elem(k):
+    if k in (1, 2):
+        return (0, 1)
+    if k == 3:
+        return (1, 0)
+    return (0, 0)
+
+
+def bic_cat(x, y):
+    m = min(x[1], y[0])
+    return (x[0] + y[0] - m, x[1] + y[1] - m)
+
+
+def brute_parent(kind):
+    """Sec. 3: parenmatch(s)[j] = max i with Bic(s[i..j]).b == 1 (else -1)."""
+    n = len(kind)
+    par = np.full(n, -1, np.int64)
+    for j in range(n):
+        acc = (0, 0)
+        for i in range(j - 1, -1, -1):
+            acc = bic_cat(bic_elem(int(kind[i])), acc)
+            if acc[1] == 1:
+                par[j] = i
+                break
+    return par
+
+
+def brute_match(kind):
+    """Depth counting: an open's close is the first later element after which
+    the depth returns to the open's depth-before."""
+    k = np.asarray(kind)
+    step = np.where((k == 1) | (k == 2), 1, np.where(k == 3, -1, 0))
+    after = np.cumsum(step)
+    before = after - step
+    m = np.full(len(k), -1, np.int64)
+    for o in np.nonzero(step == 1)[0]:
+        rest = np.nonzero(after[o:] == before[o])[0]
+        c = o + int(rest[0])
+        m[o] = c
+        m[c] = o
+    return m
+
+
+def balanced(kind):
+    k = np.asarray(kind)
+    step = np.where((k == 1) | (k == 2), 1, np.where(k == 3, -1, 0))
+    d = np.cumsum(step)
+    return d.size == 0 or (d.min() >= 0 and d[-1] == 0)
+
+
+def isect(a, b):
+    return np.concatenate([np.maximum(a[:2], b[:2]), np.minimum(a[2:], b[2:])])
+
+
+def unite(a, b):
+    return np.concatenate([np.minimum(a[:2], b[:2]), np.maximum(a[2:], b[2:])])
+
+
+def canon(b):
+    return EMPTY.copy() if (b[0] >= b[2] or b[1] >= b[3]) else b
+
+
+def brute_bboxes(kind, box):
+    par = brute_parent(kind)
+    mat = brute_match(kind)
+    n = len(kind)
+    out = np.zeros((n, 4), np.float32)
+    leaf_out = {}
+    for i in range(n):
+        if kind[i] == 0:
+            acc = box[i].copy()
+            a = par[i]
+            while a >= 0:                      # explicit ancestor enumeration
+                if kind[a] == 1:
+                    acc = isect(acc, box[a])
+                a = par[a]
+            leaf_out[i] = canon(acc)
+            out[i] = leaf_out[i]
+    for o in range(n):
+        if kind[o] in (1, 2):
+            u = EMPTY.copy()
+            for j in range(o + 1, mat[o]):      # contiguous descendant slice
+                if kind[j] == 0:
+                    u = unite(u, leaf_out[j])
+            out[o] = u
+            out[mat[o]] = u
+    return par, mat, out
+
+
+def same_bits(a, b):
+    a = np.ascontiguousarray(a, np.float32)
+    b = np.ascontiguousarray(b, np.float32)
+    return a.shape == b.shape and np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+# --- printed values -------------------------------------------------------
+
+def test_bic_printed_value():
+    g = gold()["bic_example"]
+    assert oracle.bic(kinds_of(g["string"])) == tuple(g["bic"])
+    acc = (0, 0)
+    for k in kinds_of(g["string"]):
+        acc = bic_cat(acc, bic_elem(int(k)))
+    assert acc == tuple(g["bic"])
+
+
+def test_reverse_scan_and_slice_printed_values():
+    g = gold()["reverse_scan_example"]
+    k = kinds_of(g["string"])
+    scan = [oracle.bic(k[i:]) for i in range(len(k))]
+    assert scan == [tuple(x) for x in g["reverse_bic_scan"]]
+    a, lst = oracle.stack_slice(k)
+    assert a == g["unmatched_closes"]
+    assert list(lst) == g["unmatched_opens"]
+    # slot of each unmatched open from the reverse scan, as Sec. 7.1 states
+    total_b = scan[0][1]
+    for i in g["unmatched_opens"]:
+        assert total_b - scan[i][1] == g["slot_of_open"][str(i)]
+        assert list(lst).index(i) == g["slot_of_open"][str(i)]
+
+
+def test_stack_slice_is_bic_with_indices():
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        k = rng.choice([0, 1, 2, 3], size=int(rng.integers(0, 40))).astype(np.uint8)
+        a, lst = oracle.stack_slice(k)
+        assert (a, len(lst)) == oracle.bic(k)
+        # every listed open is unmatched in the string: depth never returns
+        step = np.where((k == 1) | (k == 2), 1, np.where(k == 3, -1, 0))
+        after = np.cumsum(step)
+        for o in lst:
+            assert k[o] in (1, 2)
+            assert after[o:].min() >= after[o]
+
+
+# --- matching -------------------------------------------------------------
+
+def test_matching_exhaustive_small():
+    count = 0
+    for n in range(0, 10):
+        for t in itertools.product((0, 1, 3), repeat=n):
+            k = np.array(t, np.uint8)
+            st, par, mat = oracle.match_parens(k)
+            if not balanced(k):
+                assert st == oracle.UNBALANCED
+                continue
+            count += 1
+            assert st == oracle.OK
+            assert np.array_equal(par, brute_parent(k))
+            assert np.array_equal(mat, brute_match(k))
+    assert count > 1000
+
+
+@pytest.mark.parametrize("n,seed", [(64, 0), (257, 1), (1000, 2), (1500, 3)])
+def test_matching_random_vs_brute(n, seed):
+    k = inputs.random_walk_kinds(n, seed)
+    st, par, mat = oracle.match_parens(k)
+    assert st == oracle.OK
+    assert np.array_equal(par, brute_parent(k))
+    assert np.array_equal(mat, brute_match(k))
+
+
+def test_unbalanced_and_bad_kind():
+    assert oracle.match_parens(kinds_of(")("))[0] == oracle.UNBALANCED
+    assert oracle.match_parens(kinds_of("(()"))[0] == oracle.UNBALANCED
+    assert oracle.match_parens(np.array([0, 4, 0], np.uint8))[0] == oracle.BAD_KIND
+    box = np.zeros((3, 4), np.float32)
+    assert oracle.bboxes(kinds_of("())"), box)[0] == oracle.UNBALANCED
+    assert oracle.bboxes(np.array([1, 7, 3], np.uint8), box)[0] == oracle.BAD_KIND
+    assert oracle.match_parens(np.zeros(0, np.uint8))[0] == oracle.OK
+
+
+def test_matching_invariants_large():
+    k = inputs.random_walk_kinds(200_000, 7)
+    st, par, mat = oracle.match_parens(k)
+    assert st == oracle.OK
+    n = k.size
+    idx = np.arange(n)
+    opens = (k == 1) | (k == 2)
+    closes = k == 3
+    leaves = k == 0
+    step = np.where(opens, 1, np.where(closes, -1, 0))
+    after = np.cumsum(step)
+    before = after - step
+    assert before.min() >= 0 and after[-1] == 0
+    assert np.all(mat[leaves] == -1)
+    assert np.all(mat[mat[~leaves]] == idx[~leaves])
+    assert np.all(mat[opens] > idx[opens]) and np.all(mat[closes] < idx[closes])
+    assert np.all(par < idx)
+    has_p = par >= 0
+    assert np.all(np.isin(k[par[has_p]], (1, 2)))
+    # depth relation: every non-close sits one below its parent's depth-after
+    nc = has_p & ~closes
+    assert np.all(before[nc] == after[par[nc]])
+    assert np.all(before[~has_p & ~closes] == 0)
+    assert np.all(par[closes] == mat[closes])
+    # proper nesting: for opens o1 < o2 < close(o1), close(o2) < close(o1)
+    o = idx[opens]
+    c = mat[opens]
+    enclosing = par[o]
+    ok = enclosing < 0
+    ok |= (o < mat[np.maximum(enclosing, 0)]) & (c < mat[np.maximum(enclosing, 0)])
+    assert np.all(ok)
+
+
+# --- bounding boxes ---------------------------------------------------------
+
+def test_hand_scene():
+    g = gold()["hand_scene"]
+    k = kinds_of(g["kinds"])
+    box = np.zeros((k.size, 4), np.float32)
+    for i, b in g["boxes"].items():
+        box[int(i)] = b
+    st, par, mat, out = oracle.bboxes(k, box)
+    assert st == oracle.OK
+    assert list(par) == g["parent"]
+    assert list(mat) == g["match"]
+    for i, b in g["box_out"].items():
+        want = EMPTY if b == "EMPTY" else np.array(b, np.float32)
+        assert same_bits(out[int(i)], want), (i, out[int(i)], want)
+    p2, m2, o2 = brute_bboxes(k, box)
+    assert np.array_equal(p2, par) and np.array_equal(m2, mat) and same_bits(o2, out)
+
+
+def test_zero_area_is_empty():
+    # a leaf of zero width is empty; a unit-width one is kept
+    k = np.array([0, 0, 1, 0, 3], np.uint8)
+    box = np.array([[10, 10, 10, 20], [10, 10, 11, 20], [0, 0, 100, 100],
+                    [50, 5, 50, 6], [0, 0, 0, 0]], np.float32)
+    st, _, _, out = oracle.bboxes(k, box)
+    assert st == oracle.OK
+    assert same_bits(out[0], EMPTY)
+    assert same_bits(out[1], box[1])
+    assert same_bits(out[3], EMPTY)
+    assert same_bits(out[2], EMPTY) and same_bits(out[4], EMPTY)
+    # touching clip edge: the intersection has zero width, so it is empty
+    k = np.array([1, 0, 3], np.uint8)
+    box = np.array([[0, 0, 10, 10], [10, 0, 20, 10], [0, 0, 0, 0]], np.float32)
+    _, _, _, out = oracle.bboxes(k, box)
+    assert same_bits(out[1], EMPTY)
+
+
+def test_bboxes_exhaustive_shapes():
+    rng = np.random.default_rng(11)
+    tried = 0
+    for n in range(1, 9):
+        for t in itertools.product((0, 1, 2, 3), repeat=n):
+            k = np.array(t, np.uint8)
+            if not balanced(k):
+                continue
+            if n > 6 and rng.random() > 0.2:
+                continue
+            c = rng.uniform(0, 64, (n, 2))
+            wh = rng.uniform(1, 48, (n, 2))
+            box = np.concatenate([c - wh / 2, c + wh / 2], 1).astype(np.float32)
+            box[(k == 2) | (k == 3)] = 0
+            st, par, mat, out = oracle.bboxes(k, box)
+            assert st == oracle.OK
+            p2, m2, o2 = brute_bboxes(k, box)
+            assert np.array_equal(par, p2) and np.array_equal(mat, m2)
+            assert same_bits(out, o2)
+            tried += 1
+    assert tried > 500
+
+
+@pytest.mark.parametrize("maker,n,seed", [
+    (inputs.random_walk_scene, 600, 0),
+    (inputs.random_walk_scene, 1200, 3),
+    (inputs.chain_scene, 150, 1),
+    (inputs.flat_scene, 800, 2),
+])
+def test_bboxes_random_vs_brute(maker, n, seed):
+    k, box = maker(n, seed)
+    st, par, mat, out = oracle.bboxes(k, box)
+    assert st == oracle.OK
+    p2, m2, o2 = brute_bboxes(k, box)
+    assert np.array_equal(par, p2) and np.array_equal(mat, m2)
+    assert same_bits(out, o2)
+
+
+def test_bbox_invariants_large():
+    k, box = inputs.random_walk_scene(100_000, 9)
+    st, par, mat, out = oracle.bboxes(k, box)
+    assert st == oracle.OK
+    n = k.size
+    leaves = np.nonzero(k == 0)[0]
+    # a non-empty leaf output lies inside its own box and every ancestor clip
+    lo = out[leaves]
+    nonempty = lo[:, 0] < lo[:, 2]
+    L = leaves[nonempty]
+    assert np.all(out[L, :2] >= box[L, :2]) and np.all(out[L, 2:] <= box[L, 2:])
+    a = par[L].copy()
+    while np.any(a >= 0):
+        live = a >= 0
+        ai = a[live]
+        clip = k[ai] == 1
+        li, ci = L[live][clip], ai[clip]
+        assert np.all(out[li, :2] >= box[ci, :2]) and np.all(out[li, 2:] <= box[ci, 2:])
+        a[live] = par[ai]
+    # a node box is the union of its children's boxes (leaf children: their
+    # clipped box; node children: their node box)
+    acc = np.tile(EMPTY, (n, 1))
+    child = np.nonzero((par >= 0) & (k != 3))[0]
+    p = par[child]
+    np.minimum.at(acc[:, 0], p, out[child, 0])
+    np.minimum.at(acc[:, 1], p, out[child, 1])
+    np.maximum.at(acc[:, 2], p, out[child, 2])
+    np.maximum.at(acc[:, 3], p, out[child, 3])
+    opens = np.nonzero((k == 1) | (k == 2))[0]
+    assert same_bits(acc[opens], out[opens])
+    assert same_bits(out[mat[opens]], out[opens])
+
+
+def test_batched_oracle_is_per_scene():
+    k, box, off = inputs.batched_scenes(12, 3, 4.0, 9.0)
+    st, par, mat, out = oracle.bboxes_batched(k, box, off)
+    assert st == oracle.OK
+    for s in range(len(off) - 1):
+        b, e = off[s], off[s + 1]
+        st2, p2, m2, o2 = oracle.bboxes(k[b:e], box[b:e])
+        assert st2 == oracle.OK
+        assert np.array_equal(par[b:e], p2) and np.array_equal(mat[b:e], m2)
+        assert same_bits(out[b:e], o2)
+
+
+# --- tree scans over other monoids -----------------------------------------
+
+def _opens_ranges(k):
+    mat = brute_match(k)
+    par = brute_parent(k)
+    opens = np.nonzero((k == 1) | (k == 2))[0]
+    rank = {int(o): r for r, o in enumerate(opens)}
+    return opens, mat, par, rank
+
+
+def test_tree_scan_i32_depth_and_size():
+    k = inputs.random_walk_kinds(700, 4)
+    opens, mat, par, rank = _opens_ranges(k)
+    ones = np.ones(opens.size, np.int32)
+    st, down = oracle.tree_scan_i32(oracle.DOWN, k, ones)
+    assert st == oracle.OK
+    step = np.where((k == 1) | (k == 2), 1, np.where(k == 3, -1, 0))
+    after = np.cumsum(step)
+    assert np.array_equal(down, after[opens])          # depth of each open
+    st, up = oracle.tree_scan_i32(oracle.UP, k, ones)
+    size = [int(np.count_nonzero(((k == 1) | (k == 2))[o:mat[o] + 1])) for o in opens]
+    assert list(up) == size                             # opens in the subtree
+    vals = np.random.default_rng(1).integers(-50, 50, opens.size).astype(np.int32)
+    _, down = oracle.tree_scan_i32(oracle.DOWN, k, vals)
+    _, up = oracle.tree_scan_i32(oracle.UP, k, vals)
+    for o in opens:
+        s, a = 0, int(o)
+        while a >= 0:
+            s += int(vals[rank[a]])
+            a = int(par[a])
+        assert down[rank[int(o)]] == s
+        sub = [rank[int(j)] for j in opens if o <= j < mat[o]]
+        assert up[rank[int(o)]] == int(vals[sub].sum())
+
+
+def test_tree_scan_box_monoids():
+    k = inputs.random_walk_kinds(400, 6)
+    opens, mat, par, rank = _opens_ranges(k)
+    rng = np.random.default_rng(2)
+    c = rng.uniform(0, 100, (opens.size, 2))
+    wh = rng.uniform(10, 200, (opens.size, 2))
+    vals = np.concatenate([c - wh / 2, c + wh / 2], 1).astype(np.float32)
+    _, down = oracle.tree_scan_box(oracle.ISECT, oracle.DOWN, k, vals)
+    _, up = oracle.tree_scan_box(oracle.UNION, oracle.UP, k, vals)
+    for o in opens:
+        acc = vals[rank[int(o)]].copy()
+        a = int(par[o])
+        while a >= 0:
+            acc = isect(acc, vals[rank[a]])
+            a = int(par[a])
+        assert same_bits(down[rank[int(o)]], acc)
+        u = EMPTY.copy()
+        for j in opens:
+            if o <= j < mat[o]:
+                u = unite(u, vals[rank[int(j)]])
+        assert same_bits(up[rank[int(o)]], u)
+
+
+# --- affine transform monoid -------------------------------------------------
+
+def _hom(m):
+    h = np.eye(4)
+    h[:3, :] = m
+    return h
+
+
+def test_affine_forward_vs_ancestor_products():
+    k, L, _ = inputs.skeleton(150, 3, max_depth=12)
+    st, world = oracle.affine_forward(k, L)
+    assert st == oracle.OK
+    opens, mat, par, rank = _opens_ranges(k)
+    for o in opens:
+        chain = []
+        a = int(o)
+        while a >= 0:
+            chain.append(rank[a])
+            a = int(par[a])
+        w = np.eye(4)
+        for r in reversed(chain):               # root first: ancestor on the left
+            w = w @ _hom(L[r].astype(np.float64))
+        assert np.allclose(world[rank[int(o)]], w[:3], rtol=1e-12, atol=1e-12)
+
+
+def test_affine_integer_translations_exact():
+    k = inputs.skeleton_kinds(300, 8, max_depth=20)
+    J = int(np.count_nonzero(k == 1))
+    rng = np.random.default_rng(0)
+    L = np.zeros((J, 3, 4))
+    L[:, :, :3] = np.eye(3)
+    L[:, :, 3] = rng.integers(-1000, 1000, (J, 3))
+    st, world = oracle.affine_forward(k, L)
+    opens, mat, par, rank = _opens_ranges(k)
+    for o in opens:
+        t = np.zeros(3)
+        a = int(o)
+        while a >= 0:
+            t += L[rank[a], :, 3]
+            a = int(par[a])
+        assert np.array_equal(world[rank[int(o)], :, 3], t)
+        assert np.array_equal(world[rank[int(o)], :, :3], np.eye(3))
+    _, up = oracle.affine_up(k, L)
+    for o in opens:
+        sub = [rank[int(j)] for j in opens if o <= j < mat[o]]
+        assert np.array_equal(up[rank[int(o)], :, 3], L[sub, :, 3].sum(0))
+
+
+def test_affine_fixed_axis_angles_add():
+    k = inputs.skeleton_kinds(200, 9, max_depth=30)
+    J = int(np.count_nonzero(k == 1))
+    th = np.random.default_rng(4).normal(0, 0.3, J)
+    L = np.zeros((J, 3, 4))
+    L[:, 0, 0] = np.cos(th)
+    L[:, 0, 1] = -np.sin(th)
+    L[:, 1, 0] = np.sin(th)
+    L[:, 1, 1] = np.cos(th)
+    L[:, 2, 2] = 1.0
+    _, world = oracle.affine_forward(k, L)
+    opens, mat, par, rank = _opens_ranges(k)
+    for o in opens:
+        s, a = 0.0, int(o)
+        while a >= 0:
+            s += th[rank[a]]
+            a = int(par[a])
+        w = world[rank[int(o)]]
+        assert abs(w[0, 0] - np.cos(s)) < 1e-12 and abs(w[1, 0] - np.sin(s)) < 1e-12
+
+
+def test_affine_backward_vs_finite_differences():
+    k, L, W = inputs.skeleton(64, 1, max_depth=64)
+    L = L.astype(np.float64)
+    W = W.astype(np.float64)
+    st, g = oracle.affine_backward(k, L, W)
+    assert st == oracle.OK
+    h = 1e-6
+    fd = np.zeros_like(L)
+    for idx in np.ndindex(*L.shape):
+        Lp = L.copy()
+        Lp[idx] += h
+        Lm = L.copy()
+        Lm[idx] -= h
+        fd[idx] = (oracle.affine_loss(k, Lp, W)[1] - oracle.affine_loss(k, Lm, W)[1]) / (2 * h)
+    err = np.abs(fd - g).max() / np.abs(g).max()
+    assert err < 1e-7, err
