@@ -1,0 +1,349 @@
+"""Benchmark of the bounding-box + parentheses-matching pass on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload rw26|chain24|flat24|batched|rw24|rw16]
+
+One step = one full pass (tile summaries with look-back, tile-level
+resolve, main tile pass, cross-tile unions) over one synthetic scene already
+resident in HBM.  Prints one JSON line (rank 0).  With N > 1 (torchrun), each
+rank runs its own replica of the workload on its own GPU (independent scenes,
+no collective on the data path) and the value is the whole-job throughput.
+
+``--impl reference`` times the sequential CPU oracle (the checker) on the
+same workload on the host cores instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gelem/s bbox+paren pass & fwd+bwd tree scan; % HBM roofline; batched vs plain"
+BYTES_PER_ELEM = 41  # kind 1 + box 16 read; parent 4 + match 4 + box_out 16 written
+
+WORKLOADS = {
+    "rw26": "bbox+paren pass, one random-walk scene (OPEN 0.2 clip/blend 50/50, CLOSE 0.2), N=2^26",
+    "chain24": "bbox+paren pass, one chain scene: 2^23 nested clip opens, a leaf, 2^23 closes",
+    "flat24": "bbox+paren pass, one flat scene of depth <= 4 (~90% leaves), N=2^24",
+    "batched": "bbox+paren pass, 4096 random-walk scenes with N_s = round(2^U[8,18]), one batched call",
+    "rw16": "bbox+paren pass, one random-walk scene, N=2^16 (L2-resident)",
+    "rw24": "bbox+paren pass, one random-walk scene, N=2^24 (profiling size)",
+}
+
+# DRAM bytes per launch of the main tile pass measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the
+# kernel sources they were taken on; a changed kernel reports null.
+NCU_TRAFFIC = {}
+
+
+def make_workload(name, seed=0):
+    from paper_2205_11659_gb300 import inputs
+    if name == "rw26":
+        k, b = inputs.random_walk_scene(1 << 26, seed)
+        return k, b, None
+    if name == "rw24":
+        k, b = inputs.random_walk_scene(1 << 24, seed)
+        return k, b, None
+    if name == "rw16":
+        k, b = inputs.random_walk_scene(1 << 16, seed)
+        return k, b, None
+    if name == "chain24":
+        k, b = inputs.chain_scene(1 << 23, seed)
+        return k, b, None
+    if name == "flat24":
+        k, b = inputs.flat_scene(1 << 24, seed)
+        return k, b, None
+    if name == "batched":
+        return inputs.batched_scenes(4096, seed)
+    raise ValueError(name)
+
+
+def kernel_hash():
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2205_11659_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def time_oracle(kind, box, offsets, budget_s=12.0, min_runs=1, max_runs=50):
+    import oracle
+    oracle.build()
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        if offsets is None:
+            st = oracle.bboxes(kind, box)[0]
+        else:
+            st = oracle.bboxes_batched(kind, box, offsets)[0]
+        assert st == oracle.OK
+        runs += 1
+        el = time.perf_counter() - t0
+        if (runs >= min_runs and el >= budget_s) or runs >= max_runs:
+            return kind.size * runs / el / 1e9, runs, el
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    kind, box, offsets = make_workload(args.workload)
+    import oracle
+    oracle.build()
+
+    def once():
+        if offsets is None:
+            return oracle.bboxes(kind, box)[0]
+        return oracle.bboxes_batched(kind, box, offsets)[0]
+    for _ in range(args.warmup):
+        assert once() == oracle.OK
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        assert once() == oracle.OK
+    el = time.perf_counter() - t0
+    value = kind.size * args.steps / el / 1e9
+    sample = "full workload (%d elements) per step, single thread" % kind.size
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Gelem/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "n": int(kind.size), "seed": 0},
+            "cpu_baseline": {"value": round(value, 4), "unit": "Gelem/s", "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "Gelem/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2205_11659_gb300 import _build, binding
+    _build.build()
+
+    kind, box, offsets = make_workload(args.workload, seed=0)
+    n = int(kind.size)
+    k_d = torch.from_numpy(kind).to(dev)
+    b_d = torch.from_numpy(box).to(dev)
+    off_d = torch.from_numpy(offsets).to(dev) if offsets is not None else None
+    S = 0 if offsets is None else int(offsets.size - 1)
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+    match = torch.empty(n, dtype=torch.int32, device=dev)
+    box_out = torch.empty(n, 4, dtype=torch.float32, device=dev)
+    op = binding.TB_OP_BBOXES if offsets is None else binding.TB_OP_BBOXES_BATCHED
+    nb = binding.tb_workspace_size(op, n, S)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        if offsets is None:
+            rc = binding.tb_bboxes(k_d, b_d, n, parent, match, box_out, ws, nb, status, stream)
+        else:
+            rc = binding.tb_bboxes_batched(k_d, b_d, off_d, S, n, parent, match, box_out, ws, nb,
+                                           status, stream)
+        if rc != binding.TB_OK:
+            raise binding.TBError(rc, "bench step")
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert int(status.item()) == binding.TB_OK, int(status.item())
+
+    # ---- device-timed region: inputs resident in HBM (larger than L2)
+    K = args.steps
+    phase = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    for evs in phase:           # create the event handles
+        for e in evs:
+            e.record(stream)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    for i in range(K):
+        binding.tb_set_phase_events(phase[i])
+        step()
+    ev1.record(stream)
+    binding.tb_set_phase_events(None)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / K
+    assert int(status.item()) == binding.TB_OK
+    names = ["k1_tile_summary", "k2_tile_resolve", "k3_tile", "k4_cross_tile_unions"]
+    phases = {nm: statistics.mean(phase[i][j].elapsed_time(phase[i][j + 1]) for i in range(K))
+              for j, nm in enumerate(names)}
+    value = world * n / (ms_step * 1e-3) / 1e9
+
+    # ---- end to end through the public API with host buffers
+    kind_h = torch.from_numpy(kind).pin_memory()
+    box_h = torch.from_numpy(box).pin_memory()
+    off_h = torch.from_numpy(offsets) if offsets is not None else None
+    outs_h = (torch.empty(n, dtype=torch.int32).pin_memory(),
+              torch.empty(n, dtype=torch.int32).pin_memory(),
+              torch.empty(n, 4, dtype=torch.float32).pin_memory())
+
+    def e2e_step():
+        if offsets is None:
+            binding.bboxes_host(kind_h, box_h, outs_h)
+        else:
+            binding.bboxes_batched_host(kind_h, box_h, off_h, outs_h)
+    e2e_steps = max(2, min(K, 5))
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = kind.nbytes + box.nbytes + (offsets.nbytes if offsets is not None else 0)
+    d2h = 4 * n + 4 * n + 16 * n
+
+    peak, peak_src = measured_peaks()
+    k3_ms = phases["k3_tile"]
+    achieved = BYTES_PER_ELEM * n / (k3_ms * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC.get(kernel_hash(), {}).get(args.workload)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, runs, el = time_oracle(kind, box, offsets)
+        cpu = {"value": round(v, 4), "unit": "Gelem/s", "cores": 1, "kind": "oracle",
+               "sample": "the full workload (%d elements) x %d runs, %.1f s, single thread"
+                         % (n, runs, el)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "Gelem/s", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "n": n, "seed": 0,
+                       "scenes": S if S else 1,
+                       "l2": "inputs (%.2f GB) larger than L2, no flush" % ((kind.nbytes + box.nbytes) / 1e9)
+                       if kind.nbytes + box.nbytes > 130e6 else "L2-resident, no flush",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "kernel": "k3_tile", "achieved": round(achieved, 1),
+                         "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "algorithmic_bytes_per_launch": BYTES_PER_ELEM * n},
+            "step_roofline_frac": round(BYTES_PER_ELEM * n / (ms_step * 1e-3) / 1e9 / peak, 4),
+            "phases_ms": {k: round(v, 4) for k, v in phases.items()},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(world * n / e2e_s / 1e9, 3), "unit": "Gelem/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": 5 * K,
+            "clocks": clk,
+            "kernel_hash": kernel_hash(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rw26", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

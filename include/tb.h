@@ -1,0 +1,126 @@
+/*
+ * tb.h -- C ABI of the GB300 implementation of the data-parallel core of
+ *   R. Levien, "Fast GPU bounding boxes on tree-structured scenes"
+ *   (arXiv 2205.11659).
+ *
+ * A scene is a flattened tree (Sec. 1.1): a node with children is an open
+ * element, its children's encoding, then a close element.  Element kinds are
+ * one byte each:
+ *
+ *   TB_LEAF = 0        a leaf with a box
+ *   TB_OPEN_CLIP = 1   opens a clip node; its box clips every descendant
+ *   TB_OPEN_BLEND = 2  opens a blend node; its own box is ignored
+ *   TB_CLOSE = 3       closes the innermost open node
+ *
+ * A box is four floats (x0, y0, x1, y1), 16 bytes, 16-byte aligned.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ *  - Pointers named kind, box, parent, match, box_out, in, out, local,
+ *    grad_world, grad_local, offsets, ws and d_status are DEVICE pointers
+ *    owned by the caller.  The library allocates nothing and frees nothing.
+ *  - kind and ws must be 16-byte aligned; float/float4 arrays must be
+ *    16-byte aligned; int32 arrays 4-byte aligned.  Outputs must not alias
+ *    inputs.
+ *  - n < 2^31 (indices are int32).
+ *  - stream is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  All work is enqueued on it, nothing is synchronised, and a
+ *    call can be captured into a CUDA graph.
+ *  - ws is scratch of at least tb_workspace_size(op, n, num_scenes) bytes;
+ *    its contents on entry do not matter.
+ *  - d_status is one device int32.  The call first writes TB_OK to it in
+ *    stream order, then kernels write the first data error they find
+ *    (TB_ERR_UNBALANCED, TB_ERR_BAD_KIND or TB_ERR_TIMEOUT).  Read it after
+ *    synchronising the stream.  When it is not TB_OK the outputs are
+ *    unspecified, but every memory access stays inside the buffers above.
+ *  - The return value reports argument errors found on the host before any
+ *    work is enqueued (TB_ERR_INVALID_ARG, TB_ERR_WORKSPACE) or a failed
+ *    launch (TB_ERR_CUDA).  n == 0 enqueues only the status write.
+ */
+#ifndef TB_H
+#define TB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TB_OK = 0,
+  TB_ERR_INVALID_ARG = 1, /* null pointer, n < 0 or too large, misalignment */
+  TB_ERR_UNBALANCED = 2,  /* depth below 0 somewhere, or not 0 at the end  */
+  TB_ERR_BAD_KIND = 3,    /* a kind byte above 3                           */
+  TB_ERR_WORKSPACE = 4,   /* ws_bytes below tb_workspace_size()            */
+  TB_ERR_TIMEOUT = 5,     /* a bounded cross-block wait gave up            */
+  TB_ERR_CUDA = 6         /* a CUDA launch or memset failed                */
+} tb_status;
+
+enum { TB_LEAF = 0, TB_OPEN_CLIP = 1, TB_OPEN_BLEND = 2, TB_CLOSE = 3 };
+
+/* Operations, for tb_workspace_size(). */
+enum {
+  TB_OP_MATCH_PARENS = 0,
+  TB_OP_BBOXES = 1,
+  TB_OP_BBOXES_BATCHED = 2
+};
+
+/* Bytes of scratch the operation needs for n elements (num_scenes is used
+ * by TB_OP_BBOXES_BATCHED only).  Never fails; 0 for n == 0. */
+size_t tb_workspace_size(int op, int64_t n, int64_t num_scenes);
+
+/* Parentheses matching, strong form (Sec. 2, Fig. 1).
+ *   parent[i] = the stack top before element i is processed: the
+ *               innermost enclosing open for a leaf or an open, the matching
+ *               open for a close, -1 at the root.
+ *   match[i]  = the matching close of an open, the matching open of a close,
+ *               -1 for a leaf.
+ * Computed with the bicyclic semigroup (Sec. 3) and stack slices (Sec. 4,
+ * Sec. 7) in a single pass over the kind stream plus a tile-level resolve. */
+tb_status tb_match_parens(const uint8_t* kind, int64_t n, int32_t* parent,
+                          int32_t* match, void* ws, size_t ws_bytes,
+                          int32_t* d_status, void* stream);
+
+/* Bounding boxes over the tree (Sec. 1, Sec. 6, Sec. 9).
+ *   leaf:  box_out = its box intersected with the box of every OPEN_CLIP
+ *          ancestor; empty (x0 >= x1 or y0 >= y1) results are written as the
+ *          canonical empty box (+inf, +inf, -inf, -inf).
+ *   open and its close: box_out = union of the canonical clipped boxes of all
+ *          descendant leaves (the canonical empty box if there are none).
+ * parent and match are as in tb_match_parens and may be NULL to skip them.
+ * box is read for LEAF and OPEN_CLIP elements only. */
+tb_status tb_bboxes(const uint8_t* kind, const float* box, int64_t n,
+                    int32_t* parent, int32_t* match, float* box_out, void* ws,
+                    size_t ws_bytes, int32_t* d_status, void* stream);
+
+/* tb_bboxes over num_scenes independent scenes laid end to end: scene s is
+ * elements [offsets[s], offsets[s+1]) with offsets[0] = 0 and
+ * offsets[num_scenes] = n_total, non-decreasing (device int64 array of
+ * num_scenes + 1 entries).  Matching never crosses a scene boundary: each
+ * scene must be balanced on its own (TB_ERR_UNBALANCED otherwise), and
+ * parent and match are scene-local indices with -1 at each scene's roots.
+ * One set of launches covers all scenes. */
+tb_status tb_bboxes_batched(const uint8_t* kind, const float* box,
+                            const int64_t* offsets, int64_t num_scenes,
+                            int64_t n_total, int32_t* parent, int32_t* match,
+                            float* box_out, void* ws, size_t ws_bytes,
+                            int32_t* d_status, void* stream);
+
+/* Tracing hook.  After tb_set_phase_events(events, 5) every later call of
+ * tb_match_parens / tb_bboxes / tb_bboxes_batched records, on its own
+ * stream, events[0] before the tile-summary pass, events[1] before the
+ * tile-level resolve, events[2] before the main tile pass, events[3] before
+ * the cross-tile union step and events[4] at the end.  events holds
+ * cudaEvent_t handles created by the caller; tb_set_phase_events(NULL, 0)
+ * turns the hook off.  The setting is per host thread. */
+tb_status tb_set_phase_events(void* const* events, int num_events);
+
+/* Library version string. */
+const char* tb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TB_H */

@@ -1,0 +1,11 @@
+"""GB300 (sm_103a) implementation of the data-parallel core of Levien,
+"Fast GPU bounding boxes on tree-structured scenes" (arXiv 2205.11659).
+
+``binding`` wraps the C ABI of ``include/tb.h`` (CUDA kernels in ``csrc/``,
+built into ``_build/libtb.so`` by ``_build.build()``); ``inputs`` draws the
+seeded synthetic scenes and skeletons.
+"""
+from .binding import (  # noqa: F401
+    TBError, bboxes, bboxes_batched, match_parens, tb_bboxes, tb_bboxes_batched,
+    tb_match_parens, tb_set_phase_events, tb_version, tb_workspace_size,
+)

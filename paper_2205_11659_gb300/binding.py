@@ -1,0 +1,282 @@
+"""Python binding of the C ABI declared in ``include/tb.h``.
+
+Argument marshalling only: torch tensors supply device memory and the
+current CUDA stream, every step of the computation runs in the CUDA kernels
+of ``_build/libtb.so``.  There is no CPU implementation behind these calls:
+if the library is not built, or a tensor is not on a CUDA device, they raise.
+
+The ``tb_*`` functions mirror the C entry points one to one.  ``match_parens``,
+``bboxes`` and ``bboxes_batched`` are conveniences that allocate outputs and
+workspace with torch, check the device status word and raise on errors.
+"""
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import _build
+
+TB_OK = 0
+TB_ERR_INVALID_ARG = 1
+TB_ERR_UNBALANCED = 2
+TB_ERR_BAD_KIND = 3
+TB_ERR_WORKSPACE = 4
+TB_ERR_TIMEOUT = 5
+TB_ERR_CUDA = 6
+STATUS_NAMES = {0: "TB_OK", 1: "TB_ERR_INVALID_ARG", 2: "TB_ERR_UNBALANCED",
+                3: "TB_ERR_BAD_KIND", 4: "TB_ERR_WORKSPACE", 5: "TB_ERR_TIMEOUT",
+                6: "TB_ERR_CUDA"}
+
+TB_OP_MATCH_PARENS = 0
+TB_OP_BBOXES = 1
+TB_OP_BBOXES_BATCHED = 2
+
+LEAF, OPEN_CLIP, OPEN_BLEND, CLOSE = 0, 1, 2, 3
+
+
+class TBError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__("%s: %s" % (where, STATUS_NAMES.get(code, str(code))))
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """The loaded libtb.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError("libtb.so is not built (%s); run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+            L = ctypes.CDLL(path)
+            p, i64, sz, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t, ctypes.c_int
+            L.tb_workspace_size.argtypes = [i32, i64, i64]
+            L.tb_workspace_size.restype = sz
+            L.tb_match_parens.argtypes = [p, i64, p, p, p, sz, p, p]
+            L.tb_bboxes.argtypes = [p, p, i64, p, p, p, p, sz, p, p]
+            L.tb_bboxes_batched.argtypes = [p, p, p, i64, i64, p, p, p, p, sz, p, p]
+            L.tb_set_phase_events.argtypes = [p, i32]
+            for f in (L.tb_match_parens, L.tb_bboxes, L.tb_bboxes_batched, L.tb_set_phase_events):
+                f.restype = i32
+            L.tb_version.argtypes = []
+            L.tb_version.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _check(code, where):
+    if code != TB_OK:
+        raise TBError(code, where)
+
+
+# --------------------------------------------------------- raw entry points
+def tb_version():
+    return lib().tb_version().decode()
+
+
+def tb_workspace_size(op, n, num_scenes=0):
+    return int(lib().tb_workspace_size(int(op), int(n), int(num_scenes)))
+
+
+def tb_match_parens(kind, n, parent, match, ws, ws_bytes, d_status, stream=None):
+    return lib().tb_match_parens(_ptr(kind), int(n), _ptr(parent), _ptr(match), _ptr(ws),
+                                 int(ws_bytes), _ptr(d_status), _stream(stream))
+
+
+def tb_bboxes(kind, box, n, parent, match, box_out, ws, ws_bytes, d_status, stream=None):
+    return lib().tb_bboxes(_ptr(kind), _ptr(box), int(n), _ptr(parent), _ptr(match),
+                           _ptr(box_out), _ptr(ws), int(ws_bytes), _ptr(d_status),
+                           _stream(stream))
+
+
+def tb_bboxes_batched(kind, box, offsets, num_scenes, n_total, parent, match, box_out, ws,
+                      ws_bytes, d_status, stream=None):
+    return lib().tb_bboxes_batched(_ptr(kind), _ptr(box), _ptr(offsets), int(num_scenes),
+                                   int(n_total), _ptr(parent), _ptr(match), _ptr(box_out),
+                                   _ptr(ws), int(ws_bytes), _ptr(d_status), _stream(stream))
+
+
+def tb_set_phase_events(events):
+    """events: five recorded torch.cuda.Event objects, or None to disable."""
+    if events is None:
+        return lib().tb_set_phase_events(None, 0)
+    arr = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
+    return lib().tb_set_phase_events(arr, len(events))
+
+
+# ------------------------------------------------------------ conveniences
+class Workspace:
+    """Grow-only device scratch buffer (one per device), plus a status word."""
+
+    def __init__(self, device):
+        self.device = torch.device(device)
+        self.buf = torch.empty(0, dtype=torch.uint8, device=self.device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    def get(self, nbytes):
+        if self.buf.numel() < nbytes:
+            self.buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+_ws = {}
+
+
+def workspace(device):
+    d = torch.device(device)
+    key = (d.type, d.index if d.index is not None else torch.cuda.current_device())
+    if key not in _ws:
+        _ws[key] = Workspace(torch.device("cuda", key[1]))
+    return _ws[key]
+
+
+def _on_device(t, dtype, name, device):
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(t)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if t.device.type != "cuda":
+        t = t.to(device, non_blocking=True)
+    return t.contiguous()
+
+
+def check_status(ws, where):
+    code = int(ws.status.item())
+    _check(code, where)
+
+
+def match_parens(kind, check=True):
+    """(parent, match) int32 tensors for a uint8 kind tensor."""
+    dev = kind.device if kind.is_cuda else torch.device("cuda", torch.cuda.current_device())
+    k = _on_device(kind, torch.uint8, "kind", dev)
+    n = k.numel()
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+    match = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = workspace(dev)
+    nb = tb_workspace_size(TB_OP_MATCH_PARENS, n)
+    _check(tb_match_parens(k, n, parent, match, ws.get(nb), nb, ws.status), "tb_match_parens")
+    if check:
+        check_status(ws, "tb_match_parens")
+    if not kind.is_cuda:
+        return parent.cpu(), match.cpu()
+    return parent, match
+
+
+def bboxes(kind, box, want_indices=True, check=True, out=None):
+    """(parent, match, box_out) for a scene; box is float32 (n, 4).
+
+    Device tensors in, device tensors out.  Host tensors are copied to the
+    current device and the results copied back (pinned host memory makes the
+    copies asynchronous)."""
+    host = not kind.is_cuda
+    dev = torch.device("cuda", torch.cuda.current_device()) if host else kind.device
+    k = _on_device(kind, torch.uint8, "kind", dev)
+    b = _on_device(box, torch.float32, "box", dev).reshape(-1, 4)
+    n = k.numel()
+    if b.shape[0] != n:
+        raise ValueError("box must have shape (n, 4)")
+    if out is None:
+        parent = torch.empty(n, dtype=torch.int32, device=dev) if want_indices else None
+        match = torch.empty(n, dtype=torch.int32, device=dev) if want_indices else None
+        box_out = torch.empty(n, 4, dtype=torch.float32, device=dev)
+    else:
+        parent, match, box_out = out
+    ws = workspace(dev)
+    nb = tb_workspace_size(TB_OP_BBOXES, n)
+    _check(tb_bboxes(k, b, n, parent, match, box_out, ws.get(nb), nb, ws.status), "tb_bboxes")
+    if check:
+        check_status(ws, "tb_bboxes")
+    if host:
+        return tuple(None if t is None else t.cpu() for t in (parent, match, box_out))
+    return parent, match, box_out
+
+
+def bboxes_batched(kind, box, offsets, want_indices=True, check=True):
+    """Per-scene (parent, match, box_out) for scenes laid end to end;
+    offsets is int64 of length num_scenes + 1; indices are scene-local."""
+    host = not kind.is_cuda
+    dev = torch.device("cuda", torch.cuda.current_device()) if host else kind.device
+    k = _on_device(kind, torch.uint8, "kind", dev)
+    b = _on_device(box, torch.float32, "box", dev).reshape(-1, 4)
+    off = _on_device(offsets, torch.int64, "offsets", dev)
+    n = k.numel()
+    S = off.numel() - 1
+    parent = torch.empty(n, dtype=torch.int32, device=dev) if want_indices else None
+    match = torch.empty(n, dtype=torch.int32, device=dev) if want_indices else None
+    box_out = torch.empty(n, 4, dtype=torch.float32, device=dev)
+    ws = workspace(dev)
+    nb = tb_workspace_size(TB_OP_BBOXES_BATCHED, n, S)
+    _check(tb_bboxes_batched(k, b, off, S, n, parent, match, box_out, ws.get(nb), nb, ws.status),
+           "tb_bboxes_batched")
+    if check:
+        check_status(ws, "tb_bboxes_batched")
+    if host:
+        return tuple(None if t is None else t.cpu() for t in (parent, match, box_out))
+    return parent, match, box_out
+
+
+def _host_call(fn_name, host_inputs, out_h, extra):
+    """Pinned host inputs in, pinned host outputs filled: the H2D copies, the
+    C-ABI call and the D2H copies are enqueued on the current stream, which is
+    then synchronised and the status word checked."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    d_in = [t.to(dev, non_blocking=True) for t in host_inputs]
+    parent_h, match_h, box_h = out_h
+    n = d_in[0].numel()
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+    match = torch.empty(n, dtype=torch.int32, device=dev)
+    box_out = torch.empty(n, 4, dtype=torch.float32, device=dev)
+    ws = workspace(dev)
+    if fn_name == "tb_bboxes":
+        nb = tb_workspace_size(TB_OP_BBOXES, n)
+        rc = tb_bboxes(d_in[0], d_in[1], n, parent, match, box_out, ws.get(nb), nb, ws.status, stream)
+    else:
+        S = d_in[2].numel() - 1
+        nb = tb_workspace_size(TB_OP_BBOXES_BATCHED, n, S)
+        rc = tb_bboxes_batched(d_in[0], d_in[1], d_in[2], S, n, parent, match, box_out,
+                               ws.get(nb), nb, ws.status, stream)
+    _check(rc, fn_name)
+    parent_h.copy_(parent, non_blocking=True)
+    match_h.copy_(match, non_blocking=True)
+    box_h.copy_(box_out, non_blocking=True)
+    stream.synchronize()
+    check_status(ws, fn_name)
+    return out_h
+
+
+def bboxes_host(kind, box, out):
+    """bboxes() for pinned host tensors: fills out = (parent, match, box_out),
+    pinned host tensors of shapes (n,), (n,), (n, 4)."""
+    return _host_call("tb_bboxes", [kind, box.reshape(-1, 4)], out, None)
+
+
+def bboxes_batched_host(kind, box, offsets, out):
+    """bboxes_batched() for pinned host tensors, filling ``out``."""
+    return _host_call("tb_bboxes_batched", [kind, box.reshape(-1, 4), offsets], out, None)

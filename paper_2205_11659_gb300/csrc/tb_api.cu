@@ -1,0 +1,239 @@
+// tb_api.cu -- the C ABI of include/tb.h: argument checks, workspace
+// layout and the launch sequence of each operation.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "tb.h"
+#include "tb_scene_kernels.cuh"
+
+namespace {
+
+using namespace tb;
+
+constexpr int64_t kMaxN = (int64_t)INT_MAX - TILE;
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// Workspace carving shared by tb_workspace_size and the launches.  The
+// look-back words and the tile counter come first so one memset clears
+// both.
+struct Layout {
+  size_t lb, counter, t_a, t_b, t_dstart, t_lo, t_ps, t_q, lo_tree, t_link0, t_link1, t_val0,
+      t_val1, t_B, t_uall, uall_tree, slice_pos, slice_rel, usuf, upre, cpos, total;
+  int T, P;
+};
+
+Layout scene_layout(int64_t n, bool has_box) {
+  Layout L{};
+  const int T = (int)((n + TILE - 1) / TILE);
+  const int P = next_pow2(T > 0 ? T : 1);
+  L.T = T;
+  L.P = P;
+  const size_t t4 = (size_t)T * 4, t16 = (size_t)T * 16, slots = (size_t)T * TILE;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  L.lb = take((size_t)T * 8);
+  L.counter = take(16);
+  L.t_a = take(t4);
+  L.t_b = take(t4);
+  L.t_dstart = take(t4);
+  L.t_lo = take(t4);
+  L.t_ps = take(t4);
+  L.t_q = take(t4);
+  L.lo_tree = take((size_t)2 * P * 4);
+  L.slice_pos = take(slots * 4);
+  if (has_box) {
+    L.t_link0 = take(t4);
+    L.t_link1 = take(t4);
+    L.t_val0 = take(t16);
+    L.t_val1 = take(t16);
+    L.t_B = take(t16);
+    L.t_uall = take(t16);
+    L.uall_tree = take((size_t)2 * P * 16);
+    L.slice_rel = take(slots * 16);
+    L.usuf = take(slots * 16);
+    L.upre = take(slots * 16);
+    L.cpos = take(slots * 4);
+  }
+  L.total = n > 0 ? o : 0;
+  return L;
+}
+
+SceneWs scene_ws(const Layout& L, void* ws, bool has_box) {
+  unsigned char* b = static_cast<unsigned char*>(ws);
+  SceneWs w{};
+  w.lb = reinterpret_cast<unsigned long long*>(b + L.lb);
+  w.counter = reinterpret_cast<unsigned*>(b + L.counter);
+  w.t_a = reinterpret_cast<int*>(b + L.t_a);
+  w.t_b = reinterpret_cast<int*>(b + L.t_b);
+  w.t_dstart = reinterpret_cast<int*>(b + L.t_dstart);
+  w.t_lo = reinterpret_cast<int*>(b + L.t_lo);
+  w.t_ps = reinterpret_cast<int*>(b + L.t_ps);
+  w.t_q = reinterpret_cast<int*>(b + L.t_q);
+  w.lo_tree = reinterpret_cast<int*>(b + L.lo_tree);
+  w.slice_pos = reinterpret_cast<int*>(b + L.slice_pos);
+  if (has_box) {
+    w.t_link[0] = reinterpret_cast<int*>(b + L.t_link0);
+    w.t_link[1] = reinterpret_cast<int*>(b + L.t_link1);
+    w.t_val[0] = reinterpret_cast<float4*>(b + L.t_val0);
+    w.t_val[1] = reinterpret_cast<float4*>(b + L.t_val1);
+    w.t_B = reinterpret_cast<float4*>(b + L.t_B);
+    w.t_uall = reinterpret_cast<float4*>(b + L.t_uall);
+    w.uall_tree = reinterpret_cast<float4*>(b + L.uall_tree);
+    w.slice_rel = reinterpret_cast<float4*>(b + L.slice_rel);
+    w.usuf = reinterpret_cast<float4*>(b + L.usuf);
+    w.upre = reinterpret_cast<float4*>(b + L.upre);
+    w.cpos = reinterpret_cast<int*>(b + L.cpos);
+  }
+  w.T = L.T;
+  w.P = L.P;
+  return w;
+}
+
+// Caller-owned events recorded between the phases of a scene call.
+thread_local cudaEvent_t g_phase_events[5];
+thread_local bool g_phase_on = false;
+
+inline void phase_mark(int i, cudaStream_t s) {
+  if (g_phase_on) cudaEventRecord(g_phase_events[i], s);
+}
+
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+template <bool HAS_BOX, bool BATCHED>
+cudaError_t launch_k3(const K3Args& a, int T, cudaStream_t s) {
+  static bool attr_set = false;
+  constexpr int smem = k3_smem_bytes(HAS_BOX);
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k3_tile<HAS_BOX, BATCHED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k3_tile<HAS_BOX, BATCHED><<<T, NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// The whole matching / bounding-box pass over one stream (a single scene
+// or a batch laid end to end).
+template <bool HAS_BOX>
+tb_status run_scene(const uint8_t* kind, const float* box, int64_t n, int32_t* parent,
+                    int32_t* match, float* box_out, const int64_t* offsets, int64_t num_scenes,
+                    void* ws, size_t ws_bytes, int32_t* d_status, void* stream,
+                    int withhold_tile) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n < 0 || n > kMaxN || d_status == nullptr) return TB_ERR_INVALID_ARG;
+  if (!aligned(d_status, 4)) return TB_ERR_INVALID_ARG;
+  if (n > 0) {
+    if (kind == nullptr || ws == nullptr) return TB_ERR_INVALID_ARG;
+    if (!aligned(kind, 16) || !aligned(ws, 16)) return TB_ERR_INVALID_ARG;
+    if (HAS_BOX && (box == nullptr || box_out == nullptr || !aligned(box, 16) ||
+                    !aligned(box_out, 16)))
+      return TB_ERR_INVALID_ARG;
+    if (!HAS_BOX && (parent == nullptr || match == nullptr)) return TB_ERR_INVALID_ARG;
+    if ((parent && !aligned(parent, 4)) || (match && !aligned(match, 4))) return TB_ERR_INVALID_ARG;
+    if (offsets != nullptr && (num_scenes < 1 || num_scenes > INT_MAX - 1 || !aligned(offsets, 8)))
+      return TB_ERR_INVALID_ARG;
+  }
+  const Layout L = scene_layout(n, HAS_BOX);
+  if (n > 0 && ws_bytes < L.total) return TB_ERR_WORKSPACE;
+  if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return TB_ERR_CUDA;
+  if (n == 0) return TB_OK;
+
+  const SceneWs w = scene_ws(L, ws, HAS_BOX);
+  if (cudaMemsetAsync(ws, 0, L.t_a, s) != cudaSuccess) return TB_ERR_CUDA;
+
+  phase_mark(0, s);
+  K1Args a1{kind, reinterpret_cast<const float4*>(box), (int)n, w, d_status, withhold_tile};
+  k1_tile_summary<HAS_BOX><<<L.T, NT, 0, s>>>(a1);
+  if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
+  phase_mark(1, s);
+  k2_tile_resolve<HAS_BOX><<<1, NT2, 0, s>>>(w);
+  if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
+
+  phase_mark(2, s);
+  K3Args a3{kind, reinterpret_cast<const float4*>(box), (int)n, parent, match,
+            reinterpret_cast<float4*>(box_out), offsets, (int)num_scenes, w, d_status};
+  cudaError_t e = offsets ? launch_k3<HAS_BOX, true>(a3, L.T, s) : launch_k3<HAS_BOX, false>(a3, L.T, s);
+  if (e != cudaSuccess) return TB_ERR_CUDA;
+  phase_mark(3, s);
+  if (HAS_BOX) {
+    k4_union_tree<<<1, NT2, 0, s>>>(w);
+    if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
+    K4Args a4{reinterpret_cast<float4*>(box_out), w};
+    k4_cross_tile_unions<<<L.T, NT, 0, s>>>(a4);
+    if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
+  }
+  phase_mark(4, s);
+  return TB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t tb_workspace_size(int op, int64_t n, int64_t num_scenes) {
+  (void)num_scenes;
+  if (n <= 0) return 0;
+  switch (op) {
+    case TB_OP_MATCH_PARENS:
+      return scene_layout(n, false).total;
+    case TB_OP_BBOXES:
+    case TB_OP_BBOXES_BATCHED:
+      return scene_layout(n, true).total;
+    default:
+      return 0;
+  }
+}
+
+tb_status tb_match_parens(const uint8_t* kind, int64_t n, int32_t* parent, int32_t* match, void* ws,
+                          size_t ws_bytes, int32_t* d_status, void* stream) {
+  return run_scene<false>(kind, nullptr, n, parent, match, nullptr, nullptr, 0, ws, ws_bytes,
+                          d_status, stream, -1);
+}
+
+tb_status tb_bboxes(const uint8_t* kind, const float* box, int64_t n, int32_t* parent,
+                    int32_t* match, float* box_out, void* ws, size_t ws_bytes, int32_t* d_status,
+                    void* stream) {
+  return run_scene<true>(kind, box, n, parent, match, box_out, nullptr, 0, ws, ws_bytes, d_status,
+                         stream, -1);
+}
+
+tb_status tb_bboxes_batched(const uint8_t* kind, const float* box, const int64_t* offsets,
+                            int64_t num_scenes, int64_t n_total, int32_t* parent, int32_t* match,
+                            float* box_out, void* ws, size_t ws_bytes, int32_t* d_status,
+                            void* stream) {
+  if (offsets == nullptr || num_scenes < 1) return TB_ERR_INVALID_ARG;
+  return run_scene<true>(kind, box, n_total, parent, match, box_out, offsets, num_scenes, ws,
+                         ws_bytes, d_status, stream, -1);
+}
+
+tb_status tb_set_phase_events(void* const* events, int num_events) {
+  if (events == nullptr) {
+    g_phase_on = false;
+    return TB_OK;
+  }
+  if (num_events != 5) return TB_ERR_INVALID_ARG;
+  for (int i = 0; i < 5; ++i) {
+    if (events[i] == nullptr) return TB_ERR_INVALID_ARG;
+    g_phase_events[i] = static_cast<cudaEvent_t>(events[i]);
+  }
+  g_phase_on = true;
+  return TB_OK;
+}
+
+const char* tb_version(void) { return "treebox-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

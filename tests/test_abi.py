@@ -1,0 +1,75 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads
+and exports every entry point declared in include/tb.h; workspace sizing;
+argument errors are reported before any work is enqueued."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(tb_[a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2205_11659_gb300 import _build, binding
+    _build.build()
+    return binding.lib()
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for n in ("tb_workspace_size", "tb_match_parens", "tb_bboxes", "tb_bboxes_batched",
+              "tb_set_phase_events", "tb_version"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    from paper_2205_11659_gb300 import binding
+    assert "sm_103a" in binding.tb_version()
+
+
+def test_workspace_size(lib):
+    from paper_2205_11659_gb300 import binding as b
+    assert b.tb_workspace_size(b.TB_OP_BBOXES, 0) == 0
+    s1 = b.tb_workspace_size(b.TB_OP_BBOXES, 1)
+    s2 = b.tb_workspace_size(b.TB_OP_BBOXES, 1 << 20)
+    m2 = b.tb_workspace_size(b.TB_OP_MATCH_PARENS, 1 << 20)
+    assert 0 < s1 < s2 and 0 < m2 < s2
+    assert b.tb_workspace_size(b.TB_OP_BBOXES_BATCHED, 1 << 20, 7) == s2
+    # workspace grows linearly in the number of tiles
+    assert b.tb_workspace_size(b.TB_OP_BBOXES, 1 << 22) < 4.5 * s2
+
+
+def test_argument_errors_before_any_launch(lib):
+    # These are rejected by host checks before any CUDA call is made.
+    from paper_2205_11659_gb300 import binding as b
+    p = ctypes.c_void_p
+    fake = 1 << 20          # never dereferenced: the checks fail first
+    assert lib.tb_bboxes(p(fake), p(fake), -1, None, None, p(fake), p(fake), 1 << 30, p(fake), None) \
+        == b.TB_ERR_INVALID_ARG
+    assert lib.tb_bboxes(None, p(fake), 10, None, None, p(fake), p(fake), 1 << 30, p(fake), None) \
+        == b.TB_ERR_INVALID_ARG
+    assert lib.tb_bboxes(p(fake + 1), p(fake), 10, None, None, p(fake), p(fake), 1 << 30, p(fake),
+                         None) == b.TB_ERR_INVALID_ARG
+    assert lib.tb_bboxes(p(fake), p(fake), 10, None, None, p(fake), p(fake), 16, p(fake), None) \
+        == b.TB_ERR_WORKSPACE
+    assert lib.tb_match_parens(p(fake), 10, None, p(fake), p(fake), 1 << 30, p(fake), None) \
+        == b.TB_ERR_INVALID_ARG
+    assert lib.tb_bboxes_batched(p(fake), p(fake), None, 1, 10, None, None, p(fake), p(fake),
+                                 1 << 30, p(fake), None) == b.TB_ERR_INVALID_ARG
+    assert lib.tb_bboxes(p(fake), p(fake), 1 << 31, None, None, p(fake), p(fake), 1 << 40, p(fake),
+                         None) == b.TB_ERR_INVALID_ARG
+    assert lib.tb_set_phase_events(None, 0) == b.TB_OK
