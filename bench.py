@@ -41,7 +41,11 @@ WORKLOADS = {
 # DRAM bytes per launch of the main tile pass measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the
 # kernel sources they were taken on; a changed kernel reports null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # first walk: 697.0 MB per 2^24 launch (profiles/k3_tile_bbox_rw24.md); the
+    # 2^26 entry scales it by the element count (traffic tracks the 41 B/elem).
+    "1f1c2eead17b4786": {"rw24": 697.0e6, "rw26": 697.0e6 * 4},
+}
 
 
 def make_workload(name, seed=0):
