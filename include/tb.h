@@ -116,6 +116,31 @@ tb_status tb_bboxes_batched(const uint8_t* kind, const float* box,
  * turns the hook off.  The setting is per host thread. */
 tb_status tb_set_phase_events(void* const* events, int num_events);
 
+/* Allocation-free form of tb_bboxes, for callers that cannot allocate
+ * device memory: code that must not call cudaMalloc while it runs (a
+ * renderer's per-frame path or a real-time loop with a fixed memory budget,
+ * a plug-in whose host application owns all device memory, work issued
+ * where allocation would synchronise the device).  The paper has no
+ * counterpart; it is an interface convenience.
+ *
+ * Same results as tb_bboxes, but the scratch is a file-scope device array of
+ * the library (7.5 MiB, held by every GPU that loads the library until the
+ * process exits), so there is no ws argument.  The caller still passes the
+ * inputs and outputs (d_status included).
+ *  - n may be at most TB_STATIC_WS_MAX_N; larger n returns TB_ERR_WORKSPACE
+ *    without enqueuing anything.
+ *  - The first call on each device looks up that device's address of the
+ *    array (cudaGetSymbolAddress, with that device current); make that first
+ *    call before any stream capture.  It allocates nothing, now or later.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind; each call clears what must start at zero.  Calls whose work
+ *    overlaps on the GPU (other streams, other host threads) race on the
+ *    array and give wrong results: keep them ordered on one stream. */
+#define TB_STATIC_WS_MAX_N (1 << 17)
+tb_status tb_bboxes_static_ws(const uint8_t* kind, const float* box, int64_t n,
+                              int32_t* parent, int32_t* match, float* box_out,
+                              int32_t* d_status, void* stream);
+
 /* Library version string. */
 const char* tb_version(void);
 

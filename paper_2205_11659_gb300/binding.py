@@ -66,7 +66,9 @@ def lib():
             L.tb_bboxes.argtypes = [p, p, i64, p, p, p, p, sz, p, p]
             L.tb_bboxes_batched.argtypes = [p, p, p, i64, i64, p, p, p, p, sz, p, p]
             L.tb_set_phase_events.argtypes = [p, i32]
-            for f in (L.tb_match_parens, L.tb_bboxes, L.tb_bboxes_batched, L.tb_set_phase_events):
+            L.tb_bboxes_static_ws.argtypes = [p, p, i64, p, p, p, p, p]
+            for f in (L.tb_match_parens, L.tb_bboxes, L.tb_bboxes_batched, L.tb_set_phase_events,
+                      L.tb_bboxes_static_ws):
                 f.restype = i32
             L.tb_version.argtypes = []
             L.tb_version.restype = ctypes.c_char_p
@@ -120,6 +122,16 @@ def tb_bboxes_batched(kind, box, offsets, num_scenes, n_total, parent, match, bo
     return lib().tb_bboxes_batched(_ptr(kind), _ptr(box), _ptr(offsets), int(num_scenes),
                                    int(n_total), _ptr(parent), _ptr(match), _ptr(box_out),
                                    _ptr(ws), int(ws_bytes), _ptr(d_status), _stream(stream))
+
+
+def tb_bboxes_static_ws(kind, box, n, parent, match, box_out, d_status, stream=None):
+    """tb_bboxes with the library's own fixed scratch: no workspace argument,
+    nothing allocated (n <= TB_STATIC_WS_MAX_N)."""
+    return lib().tb_bboxes_static_ws(_ptr(kind), _ptr(box), int(n), _ptr(parent), _ptr(match),
+                                     _ptr(box_out), _ptr(d_status), _stream(stream))
+
+
+TB_STATIC_WS_MAX_N = 1 << 17
 
 
 def tb_set_phase_events(events):

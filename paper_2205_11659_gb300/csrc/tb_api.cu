@@ -4,6 +4,7 @@
 
 #include <climits>
 #include <cstdint>
+#include <mutex>
 
 #include "tb.h"
 #include "tb_scene_kernels.cuh"
@@ -235,5 +236,55 @@ tb_status tb_set_phase_events(void* const* events, int num_events) {
 }
 
 const char* tb_version(void) { return "treebox-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of tb_bboxes.  Its scratch is this file-scope
+// device array, so a caller needs no workspace at all.  The array is part of
+// the module image: every GPU that loads the library holds it until exit.
+namespace {
+
+constexpr size_t kStaticWsBytes = (size_t)15 << 19;  // 7.5 MiB
+static_assert(TB_STATIC_WS_MAX_N == (1 << 17), "limit and array size go together");
+
+__device__ __align__(256) unsigned char g_tb_static_ws[kStaticWsBytes];
+
+// Device address of g_tb_static_ws per device ordinal, looked up once with that
+// device current (host code cannot use the symbol itself as an address).
+constexpr int kMaxDevices = 64;
+void* g_static_ws_ptr[kMaxDevices] = {};
+std::mutex g_static_ws_mu;
+
+tb_status static_ws_for_current_device(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TB_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_static_ws_mu);
+  if (g_static_ws_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_tb_static_ws) != cudaSuccess || p == nullptr) return TB_ERR_CUDA;
+    g_static_ws_ptr[dev] = p;
+  }
+  *out = g_static_ws_ptr[dev];
+  return TB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tb_status tb_bboxes_static_ws(const uint8_t* kind, const float* box, int64_t n, int32_t* parent,
+                              int32_t* match, float* box_out, int32_t* d_status, void* stream) {
+  if (n < 0 || n > TB_STATIC_WS_MAX_N) return TB_ERR_WORKSPACE;
+  const Layout L = scene_layout(n, true);
+  if (L.total > kStaticWsBytes) return TB_ERR_WORKSPACE;
+  void* ws = nullptr;
+  const tb_status st = static_ws_for_current_device(&ws);
+  if (st != TB_OK) return st;
+  // run_scene clears the look-back words and the tile counter of the scratch
+  // on every call; everything else in it is written before it is read.
+  return run_scene<true>(kind, box, n, parent, match, box_out, nullptr, 0, ws, kStaticWsBytes,
+                         d_status, stream, -1);
+}
 
 }  // extern "C"
