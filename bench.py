@@ -42,9 +42,9 @@ WORKLOADS = {
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the
 # kernel sources they were taken on; a changed kernel reports null.
 NCU_TRAFFIC = {
-    # first walk: 697.0 MB per 2^24 launch (profiles/k3_tile_bbox_rw24.md); the
-    # 2^26 entry scales it by the element count (traffic tracks the 41 B/elem).
-    "1f1c2eead17b4786": {"rw24": 697.0e6, "rw26": 697.0e6 * 4},
+    # 652.8 MB per 2^24 launch (profiles/k3_tile_bbox_rw24.md); the 2^26
+    # entry scales it by the element count (traffic tracks the 41 B/elem).
+    "b338706b08696cb9": {"rw24": 652.8e6, "rw26": 652.8e6 * 4},
 }
 
 

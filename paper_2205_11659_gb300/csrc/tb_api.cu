@@ -15,9 +15,9 @@ using namespace tb;
 
 constexpr int64_t kMaxN = (int64_t)INT_MAX - TILE;
 
-size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int next_pow2(int x) {
+constexpr int next_pow2(int x) {
   int p = 1;
   while (p < x) p <<= 1;
   return p;
@@ -28,11 +28,12 @@ int next_pow2(int x) {
 // both.
 struct Layout {
   size_t lb, counter, t_a, t_b, t_dstart, t_lo, t_ps, t_q, lo_tree, t_link0, t_link1, t_val0,
-      t_val1, t_B, t_uall, uall_tree, slice_pos, slice_rel, usuf, upre, cpos, total;
+      t_val1, t_B, t_uall, uall_tree, slice_pos, slice_rel, usuf, upre, cpos, cval, t_seg, t_nseg,
+      t_cont, ctx_src, total;
   int T, P;
 };
 
-Layout scene_layout(int64_t n, bool has_box) {
+constexpr Layout scene_layout(int64_t n, bool has_box) {
   Layout L{};
   const int T = (int)((n + TILE - 1) / TILE);
   const int P = next_pow2(T > 0 ? T : 1);
@@ -40,8 +41,8 @@ Layout scene_layout(int64_t n, bool has_box) {
   L.P = P;
   const size_t t4 = (size_t)T * 4, t16 = (size_t)T * 16, slots = (size_t)T * TILE;
   size_t o = 0;
-  auto take = [&](size_t bytes) {
-    size_t at = o;
+  auto take = [&o](size_t bytes) {
+    const size_t at = o;
     o = align_up(o + bytes);
     return at;
   };
@@ -55,6 +56,12 @@ Layout scene_layout(int64_t n, bool has_box) {
   L.t_q = take(t4);
   L.lo_tree = take((size_t)2 * P * 4);
   L.slice_pos = take(slots * 4);
+  L.cpos = take(slots * 4);
+  L.cval = take(slots * 4);
+  L.t_seg = take((size_t)T * SEGK * 16);
+  L.t_nseg = take(t4);
+  L.t_cont = take((size_t)T * 8);
+  L.ctx_src = take((size_t)T * (TILE + 1) * 4);
   if (has_box) {
     L.t_link0 = take(t4);
     L.t_link1 = take(t4);
@@ -66,7 +73,6 @@ Layout scene_layout(int64_t n, bool has_box) {
     L.slice_rel = take(slots * 16);
     L.usuf = take(slots * 16);
     L.upre = take(slots * 16);
-    L.cpos = take(slots * 4);
   }
   L.total = n > 0 ? o : 0;
   return L;
@@ -85,6 +91,12 @@ SceneWs scene_ws(const Layout& L, void* ws, bool has_box) {
   w.t_q = reinterpret_cast<int*>(b + L.t_q);
   w.lo_tree = reinterpret_cast<int*>(b + L.lo_tree);
   w.slice_pos = reinterpret_cast<int*>(b + L.slice_pos);
+  w.cpos = reinterpret_cast<int*>(b + L.cpos);
+  w.cval = reinterpret_cast<int*>(b + L.cval);
+  w.t_seg = reinterpret_cast<int4*>(b + L.t_seg);
+  w.t_nseg = reinterpret_cast<int*>(b + L.t_nseg);
+  w.t_cont = reinterpret_cast<int2*>(b + L.t_cont);
+  w.ctx_src = reinterpret_cast<int*>(b + L.ctx_src);
   if (has_box) {
     w.t_link[0] = reinterpret_cast<int*>(b + L.t_link0);
     w.t_link[1] = reinterpret_cast<int*>(b + L.t_link1);
@@ -96,7 +108,6 @@ SceneWs scene_ws(const Layout& L, void* ws, bool has_box) {
     w.slice_rel = reinterpret_cast<float4*>(b + L.slice_rel);
     w.usuf = reinterpret_cast<float4*>(b + L.usuf);
     w.upre = reinterpret_cast<float4*>(b + L.upre);
-    w.cpos = reinterpret_cast<int*>(b + L.cpos);
   }
   w.T = L.T;
   w.P = L.P;
@@ -124,6 +135,28 @@ cudaError_t launch_k3(const K3Args& a, int T, cudaStream_t s) {
     attr_set = true;
   }
   k3_tile<HAS_BOX, BATCHED><<<T, NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// The tile-level resolve keeps its tree and links in shared memory when they
+// fit, else works on the copies in the workspace.
+constexpr size_t kK2SmemMax = 200 * 1024;
+
+template <bool HAS_BOX>
+cudaError_t launch_k2(const SceneWs& w, cudaStream_t s) {
+  const size_t smem = k2_smem_bytes(w.T, w.P);
+  if (smem <= kK2SmemMax) {
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(k2_tile_resolve<HAS_BOX, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kK2SmemMax);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    k2_tile_resolve<HAS_BOX, true><<<1, NT2, smem, s>>>(w);
+  } else {
+    k2_tile_resolve<HAS_BOX, false><<<1, NT2, 0, s>>>(w);
+  }
   return cudaGetLastError();
 }
 
@@ -161,22 +194,22 @@ tb_status run_scene(const uint8_t* kind, const float* box, int64_t n, int32_t* p
   k1_tile_summary<HAS_BOX><<<L.T, NT, 0, s>>>(a1);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   phase_mark(1, s);
-  k2_tile_resolve<HAS_BOX><<<1, NT2, 0, s>>>(w);
-  if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
+  if (launch_k2<HAS_BOX>(w, s) != cudaSuccess) return TB_ERR_CUDA;
 
   phase_mark(2, s);
+  const int vec_out = (!parent || aligned(parent, 16)) && (!match || aligned(match, 16));
   K3Args a3{kind, reinterpret_cast<const float4*>(box), (int)n, parent, match,
-            reinterpret_cast<float4*>(box_out), offsets, (int)num_scenes, w, d_status};
+            reinterpret_cast<float4*>(box_out), offsets, (int)num_scenes, vec_out, w, d_status};
   cudaError_t e = offsets ? launch_k3<HAS_BOX, true>(a3, L.T, s) : launch_k3<HAS_BOX, false>(a3, L.T, s);
   if (e != cudaSuccess) return TB_ERR_CUDA;
   phase_mark(3, s);
   if (HAS_BOX) {
     k4_union_tree<<<1, NT2, 0, s>>>(w);
     if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
-    K4Args a4{reinterpret_cast<float4*>(box_out), w};
-    k4_cross_tile_unions<<<L.T, NT, 0, s>>>(a4);
-    if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   }
+  K4Args a4{reinterpret_cast<float4*>(box_out), match, w};
+  k4_cross_tile_unions<HAS_BOX><<<L.T, NT, 0, s>>>(a4);
+  if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   phase_mark(4, s);
   return TB_OK;
 }
@@ -245,8 +278,9 @@ const char* tb_version(void) { return "treebox-gb300 0.1 (sm_103a)"; }
 // the module image: every GPU that loads the library holds it until exit.
 namespace {
 
-constexpr size_t kStaticWsBytes = (size_t)15 << 19;  // 7.5 MiB
-static_assert(TB_STATIC_WS_MAX_N == (1 << 17), "limit and array size go together");
+constexpr size_t kStaticWsBytes = (size_t)9 << 20;  // 9 MiB
+static_assert(scene_layout(TB_STATIC_WS_MAX_N, true).total <= kStaticWsBytes,
+              "the static scratch must hold the workspace of TB_STATIC_WS_MAX_N elements");
 
 __device__ __align__(256) unsigned char g_tb_static_ws[kStaticWsBytes];
 

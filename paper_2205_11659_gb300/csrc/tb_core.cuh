@@ -66,6 +66,9 @@ struct OpMin { __device__ int operator()(int a, int b) const { return a < b ? a 
 struct OpIsect { __device__ float4 operator()(float4 a, float4 b) const { return box_isect(a, b); } };
 struct OpUnite { __device__ float4 operator()(float4 a, float4 b) const { return box_unite(a, b); } };
 
+__device__ __forceinline__ float4 shfl_xor(float4 v, int m) {
+  return make_float4(shfl_xor(v.x, m), shfl_xor(v.y, m), shfl_xor(v.z, m), shfl_xor(v.w, m));
+}
 __device__ __forceinline__ float4 shfl_up(float4 v, int d) {
   return make_float4(shfl_up(v.x, d), shfl_up(v.y, d), shfl_up(v.z, d), shfl_up(v.w, d));
 }
@@ -226,9 +229,20 @@ struct SceneWs {
   float4* usuf;
   float4* upre;
   int* cpos;
+  int* cval;         // per tile and m: value match[open] receives (scene-local close)
+  int4* t_seg;       // per tile SEGK owner segments of the stack at its start
+  int* t_nseg;       // segment count, or SEGK + 1 when the chain continues
+  int2* t_cont;      // continuation (owner, depth) when t_nseg = SEGK + 1
+  int* ctx_src;      // per tile (TILE + 1): context sources, for tiles whose chain overflows
   int T;
   int P;
 };
+
+// Owner segments precomputed per tile by the tile-level resolve: segment j
+// of tile t is {owner tile u (-1 below the root), u's lowest depth, lowest
+// and highest global depth covered}; together they cover depths
+// t_dstart - 1 - t_a .. t_dstart - 1 of the stack at the tile start.
+constexpr int SEGK = 8;
 
 // Owner segments of the stack at a tile start.  Collected by one thread, a
 // bounded number at a time: segment i covers global depths
@@ -271,6 +285,12 @@ __device__ __forceinline__ void seg_collect(SegState& S, const int* t_ps, const 
 
 // Segment of the current batch holding global depth d (segments are in
 // decreasing depth order); -1 if outside the batch.
+__device__ __forceinline__ int segk_find(const int4* seg, int n, int d) {
+  for (int i = 0; i < n; ++i)
+    if (d >= seg[i].z && d <= seg[i].w) return i;
+  return -1;
+}
+
 __device__ __forceinline__ int seg_find(const SegState& S, int d) {
   for (int i = 0; i < S.n; ++i)
     if (d >= S.seg_lo[i] && d <= S.seg_hi[i]) return i;

@@ -19,7 +19,11 @@ __device__ __forceinline__ int shfl_down(int v, int d) { return __shfl_down_sync
 __device__ __forceinline__ int shfl_idx(int v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ __forceinline__ float shfl_up(float v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
 __device__ __forceinline__ float shfl_down(float v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ int shfl_xor(int v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ float shfl_xor(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 __device__ __forceinline__ unsigned ballot(bool p) { return __ballot_sync(0xffffffffu, p); }
+__device__ __forceinline__ int popc(unsigned x) { return __popc(x); }
+__device__ __forceinline__ int lowest_set(unsigned x) { return __ffs(x) - 1; }  // -1 if none
 __device__ __forceinline__ bool block_or(bool p) { return __syncthreads_or(p) != 0; }
 
 // Acquire load / release store at GPU scope: a block that observes another
@@ -48,6 +52,15 @@ __device__ __forceinline__ void poll_backoff(unsigned it) {
 
 __device__ __forceinline__ unsigned atomic_add_u32(unsigned* p, unsigned v) { return atomicAdd(p, v); }
 __device__ __forceinline__ int atomic_cas_i32(int* p, int cmp, int v) { return atomicCAS(p, cmp, v); }
+
+// 16-byte asynchronous global -> shared copy (cp.async.cg, bypassing L1),
+// committed as one group and awaited with cp_async_wait_all.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // 128-bit read-only loads of input streams (ld.global.nc.v4).
 __device__ __forceinline__ uint4 ld_nc_u4(const void* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }

@@ -12,7 +12,8 @@
 //   k2_tile_resolve  the tile-level tree: for every tile the owner of the
 //                    depth just below its slice (ps) and of the depth just
 //                    below its start (q), found by the up/down tree search
-//                    of Fig. "core" over a tree of tile minima; then the
+//                    of Fig. "core" over a tree of tile minima; the owner
+//                    segments of the stack at every tile start; then the
 //                    clip in force below each slice by pointer jumping over
 //                    the ps links (Sec. 6.1).
 //   k3_tile          the main pass: reads kinds and boxes once, resolves
@@ -66,6 +67,12 @@ __device__ __forceinline__ unsigned long long lb_pack(unsigned flag, int v) {
   return ((unsigned long long)flag << 32) | (unsigned long long)(unsigned)v;
 }
 
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) v += shfl_xor(v, m);
+  return v;
+}
+
 // ------------------------------------------------------------------- K1
 struct K1Args {
   const uint8_t* kind;
@@ -80,7 +87,7 @@ template <bool HAS_BOX>
 __global__ void __launch_bounds__(NT) k1_tile_summary(K1Args a) {
   __shared__ int s_scr[NW + 1];
   __shared__ float4 s_fscr[NW + 1];
-  __shared__ int s_t, s_excl;
+  __shared__ int s_t;
   const int tid = threadIdx.x;
   // Tiles are numbered in the order blocks start, so every tile a block
   // waits for belongs to a block that is already running.
@@ -112,35 +119,51 @@ __global__ void __launch_bounds__(NT) k1_tile_summary(K1Args a) {
   const int suf_after = block_excl_suffix_min(ds + mn_after, s_scr);
 
   // Decoupled look-back (single pass) for the global depth at the tile
-  // start: publish this tile's depth delta, then add predecessors' deltas
-  // until one that already knows its inclusive prefix.
-  if (tid == 0) {
+  // start: publish this tile's depth delta, then warp 0 adds predecessors'
+  // deltas 32 tiles per poll until one that knows its inclusive prefix.
+  if (warp_id() == 0) {
+    const int lane = lane_id();
     unsigned long long* lb = a.ws.lb;
-    if (t != a.withhold) st_release_u64(lb + t, lb_pack(1u, tot));
+    if (lane == 0 && t != a.withhold) st_release_u64(lb + t, lb_pack(1u, tot));
     int excl = 0;
     bool timed_out = false;
-    for (int j = t - 1; j >= 0; --j) {
-      unsigned long long w;
-      unsigned it = 0;
-      for (;;) {
-        w = ld_acquire_u64(lb + j);
-        if ((w >> 32) != 0) break;
-        if (++it >= SPIN_LIMIT) { timed_out = true; break; }
-        poll_backoff(it);
+    for (int hi = t - 1; hi >= 0; hi -= 32) {
+      const int j = hi - lane;
+      unsigned flag = 2u;  // before tile 0: inclusive prefix 0
+      int val = 0;
+      if (j >= 0) {
+        unsigned long long w = 0;
+        unsigned it = 0;
+        for (;;) {
+          w = ld_acquire_u64(lb + j);
+          if ((w >> 32) != 0) break;
+          if (++it >= SPIN_LIMIT) break;
+          poll_backoff(it);
+        }
+        flag = (unsigned)(w >> 32);
+        val = (int)(unsigned)(w & 0xffffffffull);
+        if (flag == 0u) {
+          timed_out = true;
+          flag = 2u;
+          val = 0;
+        }
       }
-      if (timed_out) break;
-      excl += (int)(unsigned)(w & 0xffffffffull);
-      if ((w >> 32) == 2ull) break;
+      const unsigned incl = ballot(flag == 2u);
+      if (incl != 0u && lane > lowest_set(incl)) val = 0;
+      excl += warp_sum(val);
+      if (incl != 0u) break;
     }
-    if (timed_out) atomic_cas_i32(a.status, ST_OK, ST_TIMEOUT);
-    if (t != a.withhold) st_release_u64(lb + t, lb_pack(2u, excl + tot));
-    s_excl = excl;
-    a.ws.t_a[t] = a_t;
-    a.ws.t_b[t] = b_t;
-    a.ws.t_dstart[t] = excl;
-    a.ws.t_lo[t] = excl - a_t;
-    if (excl - a_t < 0) atomic_cas_i32(a.status, ST_OK, ST_UNBALANCED);
-    if (t == a.ws.T - 1 && excl + tot != 0) atomic_cas_i32(a.status, ST_OK, ST_UNBALANCED);
+    const bool any_timeout = ballot(timed_out) != 0u;
+    if (lane == 0) {
+      if (any_timeout) atomic_cas_i32(a.status, ST_OK, ST_TIMEOUT);
+      if (t != a.withhold) st_release_u64(lb + t, lb_pack(2u, excl + tot));
+      a.ws.t_a[t] = a_t;
+      a.ws.t_b[t] = b_t;
+      a.ws.t_dstart[t] = excl;
+      a.ws.t_lo[t] = excl - a_t;
+      if (excl - a_t < 0) atomic_cas_i32(a.status, ST_OK, ST_UNBALANCED);
+      if (t == a.ws.T - 1 && excl + tot != 0) atomic_cas_i32(a.status, ST_OK, ST_UNBALANCED);
+    }
   }
 
   // The tile's stack slice: an open is unmatched in the tile when the depth
@@ -184,10 +207,16 @@ __global__ void __launch_bounds__(NT) k1_tile_summary(K1Args a) {
 // ------------------------------------------------------------------- K2
 constexpr int NT2 = 1024;
 
-template <bool HAS_BOX>
+// Dynamic shared memory of k2_tile_resolve when the tile tree and the ps
+// links live in shared memory.
+__host__ __device__ constexpr size_t k2_smem_bytes(int T, int P) { return (size_t)(2 * P + T) * 4; }
+
+template <bool HAS_BOX, bool SMEM>
 __global__ void __launch_bounds__(NT2) k2_tile_resolve(SceneWs ws) {
+  TB_DYNAMIC_SMEM(smem);
   const int T = ws.T, P = ws.P, tid = threadIdx.x;
-  int* tree = ws.lo_tree;
+  int* tree = SMEM ? reinterpret_cast<int*>(smem) : ws.lo_tree;
+  int* ps = SMEM ? tree + 2 * P : ws.t_ps;
   for (int u = tid; u < P; u += NT2) tree[P + u] = u < T ? ws.t_lo[u] : INT_MAX;
   __syncthreads();
   for (int h = P >> 1; h >= 1; h >>= 1) {
@@ -198,21 +227,52 @@ __global__ void __launch_bounds__(NT2) k2_tile_resolve(SceneWs ws) {
     __syncthreads();
   }
   for (int u = tid; u < T; u += NT2) {
-    const int lo = ws.t_lo[u], ds = ws.t_dstart[u];
-    ws.t_ps[u] = lo - 1 >= 0 ? tree_last_le(tree, P, u, lo - 1) : -1;
+    const int lo = tree[P + u], ds = ws.t_dstart[u];
+    const int p = lo - 1 >= 0 ? tree_last_le(tree, P, u, lo - 1) : -1;
+    ps[u] = p;
+    if (SMEM) ws.t_ps[u] = p;
     ws.t_q[u] = ds - 1 >= 0 ? tree_last_le(tree, P, u, ds - 1) : -1;
   }
-  if (!HAS_BOX) return;
   __syncthreads();
+  // Owner segments of the stack at each tile start, depths ds-1 .. ds-1-a:
+  // from the owner q of depth ds-1, each owner covers down to its lowest
+  // depth and hands over to its ps.
+  for (int u = tid; u < T; u += NT2) {
+    const int ds = ws.t_dstart[u];
+    int dtop = ds - 1;
+    const int dbot = ds - 1 - ws.t_a[u];
+    int own = ws.t_q[u];
+    int n = 0;
+    int4* seg = ws.t_seg + (size_t)u * SEGK;
+    while (dtop >= dbot && n < SEGK) {
+      if (dtop < 0 || own < 0) {
+        seg[n++] = make_int4(-1, 0, dbot, dtop);
+        dtop = dbot - 1;
+        break;
+      }
+      const int lo_o = tree[P + own];
+      const int lo_s = lo_o > dbot ? lo_o : dbot;
+      seg[n++] = make_int4(own, lo_o, lo_s, dtop);
+      dtop = lo_s - 1;
+      own = ps[own];
+    }
+    if (dtop >= dbot) {
+      ws.t_nseg[u] = SEGK + 1;
+      ws.t_cont[u] = make_int2(own, dtop);
+    } else {
+      ws.t_nseg[u] = n;
+    }
+  }
+  if constexpr (HAS_BOX) {
   // v(u): relative clip of the ps tile's slice entry at depth lo(u)-1;
   // B(u) = B(ps(u)) * v(u) is then a fold along the ps chain, done by
   // pointer jumping: each round doubles the covered chain length.
   for (int u = tid; u < T; u += NT2) {
-    const int lo = ws.t_lo[u], p = ws.t_ps[u];
+    const int lo = tree[P + u], p = ps[u];
     float4 v = box_universe();
     int l = -1;
     if (lo - 1 >= 0 && p >= 0) {
-      v = ws.slice_rel[(size_t)p * TILE + (lo - 1 - ws.t_lo[p])];
+      v = ws.slice_rel[(size_t)p * TILE + (lo - 1 - tree[P + p])];
       l = p;
     }
     ws.t_val[0][u] = v;
@@ -239,6 +299,82 @@ __global__ void __launch_bounds__(NT2) k2_tile_resolve(SceneWs ws) {
     if (!any) break;
   }
   for (int u = tid; u < T; u += NT2) ws.t_B[u] = ws.t_val[cur][u];
+  }
+}
+
+// ----------------------------------------------------- tile context helpers
+// Source slot (tile * TILE + slot) of the stack entry at global depth gd,
+// m = dstart - 1 - gd, at the start of tile t; -1 below the root.
+__device__ __forceinline__ int ctx_src_of(const SceneWs& ws, int t, bool ovf, const int4* seg,
+                                          int nseg, int gd, int m) {
+  if (ovf) return (m >= 0 && m <= TILE) ? ws.ctx_src[(size_t)t * (TILE + 1) + m] : -1;
+  const int s = segk_find(seg, nseg, gd);
+  if (s < 0 || seg[s].x < 0) return -1;
+  return seg[s].x * TILE + (gd - seg[s].y);
+}
+
+// For a tile whose owner chain has more than SEGK segments: writes the
+// context sources of all `count` depths below the tile start into the
+// tile's ctx_src row (the precomputed segments first, then the rest of the
+// chain collected SEG_CAP segments at a time).
+__device__ __forceinline__ void fill_ctx_overflow(SegState& S, const SceneWs& ws, int t,
+                                                  int dstart, int count, const int4* seg) {
+  const int tid = threadIdx.x;
+  int* row = ws.ctx_src + (size_t)t * (TILE + 1);
+  const int covered_lo = seg[SEGK - 1].z;
+  for (int m = tid; m < count; m += NT) {
+    const int d = dstart - 1 - m;
+    if (d >= covered_lo) {
+      const int s = segk_find(seg, SEGK, d);
+      row[m] = (s >= 0 && seg[s].x >= 0) ? seg[s].x * TILE + (d - seg[s].y) : -1;
+    }
+  }
+  if (tid == 0) {
+    const int2 c = ws.t_cont[t];
+    S.u = c.x;
+    S.dtop = c.y;
+    S.dbot = dstart - count;
+  }
+  __syncthreads();
+  for (;;) {
+    if (tid == 0) seg_collect(S, ws.t_ps, ws.t_lo);
+    __syncthreads();
+    const int hi = S.seg_hi[0], lo = S.seg_lo[S.n - 1];
+    for (int m = dstart - 1 - hi + tid; m <= dstart - 1 - lo; m += NT) {
+      const int d = dstart - 1 - m;
+      const int s = seg_find(S, d);
+      const int u = s >= 0 ? S.seg_u[s] : -1;
+      row[m] = u >= 0 ? u * TILE + (d - S.seg_ulo[s]) : -1;
+    }
+    const bool done = S.done;
+    __syncthreads();
+    if (done) break;
+  }
+}
+
+// Min tree (or union tree) over the NT chunks, leaves at [NT, 2NT): the five
+// lowest levels inside each warp by shuffles, the rest by warp 0.
+template <class T, class Op>
+__device__ __forceinline__ void build_chunk_tree(T* tree, T leaf, Op op) {
+  const int tid = threadIdx.x, lane = lane_id();
+  T v = leaf;
+  tree[NT + tid] = v;
+#pragma unroll
+  for (int g = 2; g <= 32; g <<= 1) {
+    v = op(v, shfl_xor(v, g >> 1));
+    if ((lane & (g - 1)) == 0) tree[NT / g + tid / g] = v;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    // NW warp nodes at [NW, 2NW): reduce them the same way
+    T w = tid < NW ? tree[NW + tid] : tree[NW];
+#pragma unroll
+    for (int g = 2; g <= NW; g <<= 1) {
+      w = op(w, shfl_xor(w, g >> 1));
+      if (tid < NW && (tid & (g - 1)) == 0) tree[NW / g + tid / g] = w;
+    }
+  }
+  __syncthreads();
 }
 
 // ------------------------------------------------------------------- K3
@@ -251,49 +387,99 @@ struct K3Args {
   float4* box_out;
   const int64_t* offsets;  // batched: scene offsets (num_scenes + 1)
   int num_scenes;
+  int vec_out;             // parent/match are 16-byte aligned
   SceneWs ws;
   int* status;
 };
 
+constexpr int CTXC = 32;      // top entries of the tile context cached in shared memory
+constexpr int SOFF_CAP = 64;  // scene offsets of one tile staged in shared memory
+
 // Dynamic shared memory of k3_tile.
 __host__ __device__ constexpr int k3_smem_bytes(bool has_box) {
-  return (has_box ? (BOX_SMEM_LEN * 16 + 2 * NT * 16) : 0) + TILE * 2 + (TILE + 4) * 4 +
-         NT * 4 + 2 * NT * 4 + NT * 4 + 2 * NT * 4;
+  return (has_box ? (BOX_SMEM_LEN * 16 + 2 * NT * 16 + NT * 16) : 0) + TILE * 2 + NT * 4 +
+         2 * NT * 4 + NT * 4 + 2 * NT * 4;
 }
 
-// Fills s_ctx[m], m = 0 .. count-1, with the workspace slot (tile * TILE +
-// slot) of the stack entry at global depth dstart-1-m in the stack at the
-// start of tile t, or -1 below the root.
-__device__ __forceinline__ void fill_tile_ctx(SegState& S, const SceneWs& ws, int t, int dstart,
-                                              int count, int* s_ctx) {
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    S.u = ws.t_q[t];
-    S.dtop = dstart - 1;
-    S.dbot = dstart - count;
-  }
-  __syncthreads();
-  for (;;) {
-    if (tid == 0) seg_collect(S, ws.t_ps, ws.t_lo);
-    __syncthreads();
-    const int hi = S.seg_hi[0], lo = S.seg_lo[S.n - 1];
-    for (int m = dstart - 1 - hi + tid; m <= dstart - 1 - lo; m += NT) {
-      const int d = dstart - 1 - m;
-      const int s = seg_find(S, d);
-      const int u = s >= 0 ? S.seg_u[s] : -1;
-      s_ctx[m] = u >= 0 ? u * TILE + (d - S.seg_ulo[s]) : -1;
+// Fold of chunk-tree leaves l..r (inclusive); the loop has a fixed trip
+// count and addresses that do not depend on loaded values.
+template <class T, class Op>
+__device__ __forceinline__ T chunk_range(const T* tree, int l, int r, T ident, Op op) {
+  T left = ident, right = ident;
+  if (l <= r) {
+    l += NT;
+    r += NT + 1;
+#pragma unroll
+    for (int lev = 0; lev <= 8; ++lev) {
+      if (l < r) {
+        if (l & 1) left = op(left, tree[l++]);
+        if (r & 1) right = op(tree[--r], right);
+      }
+      l >>= 1;
+      r >>= 1;
     }
-    const bool done = S.done;
-    __syncthreads();
-    if (done) break;
   }
+  return op(left, right);
+}
+
+// Where the stack entries below a chunk's own elements live: an earlier
+// chunk of the tile (its slice in shared memory) or the tile context.
+struct OutCtx {
+  const int* s_lo;
+  const int* s_cps;
+  const uint16_t* s_spos;
+  const float4* s_B;
+  const float4* s_box;
+  const int* s_cidx;
+  const float4* s_cclip;
+  const int4* s_seg;
+  int nseg, ovf, t, dstart_t, base;
+};
+struct OutRes {
+  int own, par;
+  float4 cx;
+};
+
+// The entry at tile-relative depth dd of the stack at the start of the
+// calling chunk: its global index and (want_clip) the clip in force there.
+// `own` is the chunk cursor (owner of the previous, higher depth).
+template <bool HAS_BOX>
+__device__ __noinline__ OutRes out_lookup(const OutCtx& c, const SceneWs& ws, int dd, int want_clip,
+                                          int own) {
+  OutRes r;
+  r.cx = box_universe();
+  while (own >= 0 && c.s_lo[own] > dd) own = c.s_cps[own];
+  r.own = own;
+  if (own >= 0) {
+    const int op = c.s_spos[own * KPT + (dd - c.s_lo[own])];
+    r.par = c.base + op;
+    if (HAS_BOX && want_clip) r.cx = box_isect(c.s_B[own], c.s_box[box_slot(op)]);
+  } else {
+    const int m = -1 - dd;
+    if (m < CTXC) {
+      r.par = c.s_cidx[m];
+      if (HAS_BOX && want_clip) r.cx = c.s_cclip[m];
+    } else {
+      const int src = ctx_src_of(ws, c.t, c.ovf != 0, c.s_seg, c.nseg, c.dstart_t - 1 - m, m);
+      r.par = src >= 0 ? ws.slice_pos[src] : -1;
+      if (HAS_BOX && want_clip && src >= 0)
+        r.cx = box_isect(ws.t_B[src / TILE], ws.slice_rel[src]);
+    }
+  }
+  return r;
 }
 
 template <bool HAS_BOX, bool BATCHED>
 __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
   TB_DYNAMIC_SMEM(smem);
   __shared__ int s_scr[NW + 1];
+  __shared__ int4 s_seg[SEGK];
+  __shared__ int s_info[3];
+  __shared__ int s_cidx[CTXC];
+  __shared__ float4 s_cclip[CTXC];
   __shared__ SegState S;
+  __shared__ long long s_soff[SOFF_CAP + 1];
+  __shared__ int s_sc[2];
 
   const int tid = threadIdx.x;
   const int t = blockIdx.x;
@@ -305,11 +491,10 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
   unsigned char* sp = smem;
   float4* s_box = reinterpret_cast<float4*>(sp);
   float4* s_val = s_box + BOX_SMEM_LEN;  // 2*NT: pointer jumping, then the union tree
-  if (HAS_BOX) sp += BOX_SMEM_LEN * 16 + 2 * NT * 16;
+  float4* s_span = s_val + 2 * NT;       // NT: union of the chunks skipped by each cps link
+  if (HAS_BOX) sp += BOX_SMEM_LEN * 16 + 2 * NT * 16 + NT * 16;
   uint16_t* s_spos = reinterpret_cast<uint16_t*>(sp);
   sp += TILE * 2;
-  int* s_ctx = reinterpret_cast<int*>(sp);
-  sp += (TILE + 4) * 4;
   int* s_lo = reinterpret_cast<int*>(sp);
   sp += NT * 4;
   int* s_tree = reinterpret_cast<int*>(sp);
@@ -318,55 +503,132 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
   sp += NT * 4;
   int* s_link = reinterpret_cast<int*>(sp);
 
-  // ---- stage: kinds into registers, boxes into shared memory (coalesced)
+  // ---- stage: tile info, kinds into registers, boxes into shared memory
+  if (tid == 0) {
+    s_info[0] = ws.t_a[t];
+    s_info[1] = ws.t_dstart[t];
+    s_info[2] = ws.t_nseg[t];
+  }
+  if (tid < SEGK) s_seg[tid] = ws.t_seg[(size_t)t * SEGK + tid];
+  if (BATCHED && tid < 2) {
+    // scene of the tile's first (tid 0) and last (tid 1) element
+    const int64_t e = base + (tid == 0 ? 0 : cnt - 1);
+    int lo = 0, hi = a.num_scenes;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.offsets[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    s_sc[tid] = lo < a.num_scenes ? lo : a.num_scenes - 1;
+  }
   uint8_t kk[KPT];
   load_kinds(a.kind, a.n, base + p0, kk);  // bad kinds were reported by k1
   if (HAS_BOX) {
+    // asynchronous global -> shared copies; the kinds-only work below runs
+    // while they are in flight
 #pragma unroll 4
     for (int i = 0; i < KPT; ++i) {
       const int p = i * NT + tid;
-      if (p < cnt) s_box[box_slot(p)] = ld_nc_f4(a.box + base + p);
+      if (p < cnt) cp_async16(&s_box[box_slot(p)], a.box + base + p);
     }
+    cp_async_commit();
   }
-  const int a_t = ws.t_a[t];
-  const int dstart_t = ws.t_dstart[t];
 
-  // ---- chunk summaries: Bic(chunk) = (a_j, b_j) and depth at chunk start
-  int r = 0, mn = 0;
-#pragma unroll
-  for (int i = 0; i < KPT; ++i) {
-    r += kind_delta(kk[i]);
-    mn = mn < r ? mn : r;
-  }
-  const int a_j = -mn;
-  int tot;
-  const int ds = block_excl_scan(r, 0, OpAdd(), s_scr, &tot);  // tile-relative
-  const int lo_j = ds - a_j;
-  s_lo[tid] = lo_j;
-  s_tree[NT + tid] = lo_j;
-
-  // Chunk stack slice: the chunk's unmatched opens, slot = depth - lo_j.
-  unsigned um = 0;
+  // ---- in-chunk structure from the kinds alone (register stack of
+  // 4-bit positions): parent position, partner position, masks.
+  unsigned long long lpar = 0, lmate = 0;
+  unsigned inside = 0, pairm = 0, openm = 0, closem = 0, leafm = 0;
   {
-    int rr[KPT];
-    int x = 0;
+    unsigned long long stk = 0;
+    int spn = 0;
 #pragma unroll
     for (int i = 0; i < KPT; ++i) {
-      x += kind_delta(kk[i]);
-      rr[i] = x;
-    }
-    int suf = INT_MAX;
-#pragma unroll
-    for (int i = KPT - 1; i >= 0; --i) {
-      suf = suf < rr[i] ? suf : rr[i];
-      if (kind_open(kk[i]) && rr[i] <= suf) {
-        um |= 1u << i;
-        s_spos[p0 + rr[i] - 1 + a_j] = (uint16_t)(p0 + i);
+      const int k = kk[i];
+      if (spn > 0) {
+        inside |= 1u << i;
+        lpar |= (stk & 15ull) << (4 * i);
+      }
+      if (k == K_CLIP || k == K_BLEND) {
+        openm |= 1u << i;
+        stk = (stk << 4) | (unsigned long long)i;
+        ++spn;
+      } else if (k == K_CLOSE) {
+        closem |= 1u << i;
+        if (spn > 0) {
+          const int o = (int)(stk & 15ull);
+          stk >>= 4;
+          --spn;
+          pairm |= (1u << i) | (1u << o);
+          lmate |= ((unsigned long long)o << (4 * i)) | ((unsigned long long)i << (4 * o));
+        }
+      } else if (k == K_LEAF) {
+        leafm |= 1u << i;
       }
     }
   }
-  __syncthreads();
+  const unsigned um = openm & ~pairm;   // the chunk's slice: opens unmatched in the chunk
+  const unsigned xcl = closem & ~pairm;  // closes matching an open before the chunk
+  const int a_j = popc(xcl);
+  int tot;
+  const int ds = block_excl_scan(popc(openm) - popc(closem), 0, OpAdd(), s_scr, &tot);
+  const int lo_j = ds - a_j;
+  s_lo[tid] = lo_j;
+  // Chunk stack slice: the k-th unmatched open sits at depth lo_j + k.
+  {
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+      if ((um >> i) & 1u) s_spos[p0 + k++] = (uint16_t)(p0 + i);
+  }
+  const int a_t = s_info[0], dstart_t = s_info[1], nseg = s_info[2];
+  const bool ovf = nseg > SEGK;
+
+  // ---- tile context: the top CTXC entries of the stack below the tile
+  // start, fetched now so that their latency overlaps the work below
+  if (ovf) fill_ctx_overflow(S, ws, t, dstart_t, a_t + 1, s_seg);
+  if (tid < CTXC && tid <= a_t) {
+    const int src = ctx_src_of(ws, t, ovf, s_seg, nseg, dstart_t - 1 - tid, tid);
+    s_cidx[tid] = src >= 0 ? ws.slice_pos[src] : -1;
+    if (HAS_BOX)
+      s_cclip[tid] = src >= 0 ? box_isect(ws.t_B[src / TILE], ws.slice_rel[src]) : box_universe();
+  }
+
+  // ---- per-element lookups for the walk, from the chunk structure alone
+  //   parpair: the parent is an in-chunk open whose close is also in the chunk
+  //   for such an open with such a parent, lA = the parent's close slot (the
+  //   parent's partial union is parked there while the child is open)
+  //   for an in-chunk close: lA = gp, its open's parent; lB = gp's close
+  //   slot; whether gp is in the chunk (cl_gin), matched in it (cl_gpair),
+  //   or one of its unmatched opens (cl_gum)
+  unsigned long long kpack = 0;  // kinds, 4 bits per element, for the rolled walk
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) kpack |= (unsigned long long)kk[i] << (4 * i);
+  unsigned parpair = 0, savem = 0, cl_gin = 0, cl_gpair = 0, cl_gum = 0;
+  unsigned long long lA = 0, lB = 0;
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) {
+    const unsigned bit = 1u << i;
+    const int lp = (int)((lpar >> (4 * i)) & 15ull);
+    const bool pp = (inside & bit) && ((pairm >> lp) & 1u);
+    if (pp) parpair |= bit;
+    if ((openm & pairm & bit) && pp) {
+      savem |= bit;
+      lA |= ((lmate >> (4 * lp)) & 15ull) << (4 * i);
+    }
+    if ((closem & inside & bit) && ((inside >> lp) & 1u)) {
+      const int gp = (int)((lpar >> (4 * lp)) & 15ull);
+      cl_gin |= bit;
+      lA |= (unsigned long long)gp << (4 * i);
+      if ((pairm >> gp) & 1u) {
+        cl_gpair |= bit;
+        lB |= ((lmate >> (4 * gp)) & 15ull) << (4 * i);
+      }
+      if ((um >> gp) & 1u) cl_gum |= bit;
+    }
+  }
+
   if (HAS_BOX) {
+    cp_async_wait_all();
+    __syncthreads();
     // Relative clip of each chunk-slice entry (intersection of the chunk's
     // unmatched clip boxes up to it), stored over that open's staged box.
     float4 acc = box_universe();
@@ -379,17 +641,17 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
       }
     }
   }
-  // Min tree over the chunks' lowest depths.
-  for (int h = NT >> 1; h >= 1; h >>= 1) {
-    if (tid < h) {
-      const int l = s_tree[2 * (h + tid)], rgt = s_tree[2 * (h + tid) + 1];
-      s_tree[h + tid] = l < rgt ? l : rgt;
-    }
-    __syncthreads();
-  }
+  build_chunk_tree(s_tree, lo_j, OpMin());
 
-  // ---- tile context: sources of the top a_t + 1 stack entries
-  fill_tile_ctx(S, ws, t, dstart_t, a_t + 1, s_ctx);
+  // scene offsets of the tile
+  int sc0 = 0;
+  bool soff_smem = false;
+  if (BATCHED) {
+    sc0 = s_sc[0];
+    const int nsc = s_sc[1] - s_sc[0] + 2;
+    soff_smem = nsc <= SOFF_CAP + 1;
+    if (soff_smem && tid < nsc) s_soff[tid] = a.offsets[sc0 + tid];
+  }
 
   // ---- chunk links: cps = owner of depth lo_j - 1, cq = owner of ds - 1.
   // A tile-relative depth is owned by the last earlier chunk reaching down to
@@ -398,6 +660,21 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
   const int cps = tree_last_le(s_tree, NT, tid, lo_j - 1);
   const int cq = tree_last_le(s_tree, NT, tid, ds - 1);
   s_cps[tid] = cps;
+  __syncthreads();
+
+  OutCtx oc;
+  oc.s_lo = s_lo;
+  oc.s_cps = s_cps;
+  oc.s_spos = s_spos;
+  oc.s_box = s_box;
+  oc.s_cidx = s_cidx;
+  oc.s_cclip = s_cclip;
+  oc.s_seg = s_seg;
+  oc.nseg = nseg;
+  oc.ovf = ovf;
+  oc.t = t;
+  oc.dstart_t = dstart_t;
+  oc.base = base;
 
   int cur = 0;
   float4 Bx = box_universe();
@@ -406,14 +683,17 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
     // by pointer jumping (Sec. 6.1) with the tile context at the roots.
     float4 v;
     int link;
-    const int dl = lo_j - 1;
     if (cps >= 0) {
-      const int slot = dl - s_lo[cps];
-      v = s_box[box_slot(s_spos[cps * KPT + slot])];
+      v = s_box[box_slot(s_spos[cps * KPT + (lo_j - 1 - s_lo[cps])])];
       link = cps;
     } else {
-      const int src = s_ctx[-1 - dl];
-      v = src >= 0 ? box_isect(ws.t_B[src / TILE], ws.slice_rel[src]) : box_universe();
+      const int m = -lo_j;
+      if (m < CTXC) {
+        v = s_cclip[m];
+      } else {
+        const int src = ctx_src_of(ws, t, ovf, s_seg, nseg, dstart_t - 1 - m, m);
+        v = src >= 0 ? box_isect(ws.t_B[src / TILE], ws.slice_rel[src]) : box_universe();
+      }
       link = -1;
     }
     s_val[tid] = v;
@@ -434,194 +714,269 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
       if (!any) break;
     }
     Bx = s_val[cur * NT + tid];
-  } else {
-    __syncthreads();
   }
-  const float4* s_B = s_val + cur * NT;
+  oc.s_B = s_val + cur * NT;
 
-  // ---- scene bookkeeping (batched): scene of the chunk's first element
+  // ---- scene of the chunk's first element (batched)
   int64_t sc_start = 0, sc_next = INT64_MAX;
   int sc = 0;
   if (BATCHED) {
     const int64_t e0 = base + p0;
-    int lo = 0, hi = a.num_scenes;  // last s with offsets[s] <= e0
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (a.offsets[mid] <= e0) lo = mid; else hi = mid - 1;
+    if (soff_smem) {
+      int lo = 0, hi = s_sc[1] - sc0;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_soff[mid] <= e0) lo = mid; else hi = mid - 1;
+      }
+      sc = sc0 + lo;
+    } else {
+      int lo = 0, hi = a.num_scenes;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.offsets[mid] <= e0) lo = mid; else hi = mid - 1;
+      }
+      sc = lo < a.num_scenes ? lo : a.num_scenes - 1;
     }
-    sc = lo < a.num_scenes ? lo : a.num_scenes - 1;
     sc_start = a.offsets[sc];
     sc_next = a.offsets[sc + 1];
   }
+  const int64_t sc_start0 = sc_start, sc_next0 = sc_next;
+  const int sc0c = sc;
 
-  // ---- the walk: one pass over the chunk with a local stack
-  int D = ds;          // tile-relative depth before the current element
-  int own = cq;        // chunk owning depth D-1 while the local stack is empty
-  uint8_t st_pos[KPT];
-  float4 st_acc[KPT];
-  int sp_n = 0;
+  // ---- the walk over the chunk's elements.  The clip of the innermost
+  // open is kept in top_clip; shared memory is written for later readers and
+  // read back only when a close returns to an older open.  Element i+1's box
+  // is loaded during element i: no store of element i can target slot i+1
+  // (a parked union goes to a close beyond the current open's own close).
+  float4 bcur = box_universe();
+  if (HAS_BOX) bcur = s_box[box_slot(p0)];
+  int D = ds;     // tile-relative depth before the current element
+  int own = cq;   // chunk owning depth D-1 when the parent is outside the chunk
+  float4 cur_acc = box_empty();  // union so far of the innermost in-chunk pair
+  float4 pre = box_empty();      // union of the chunk's leaves so far
   float4 top_clip = box_universe();
-  float4 cur_acc = box_empty();
-  float4 run = box_empty();  // union of all leaf boxes of the chunk so far
-  uint8_t xc_i[KPT];
-  int xc_d[KPT];
-  int nxc = 0;
-  int32_t* const parent = a.parent;
-  int32_t* const match = a.match;
-
+  int o_dd = INT_MIN, o_par = -1;  // last looked-up outside parent (depth, index, clip)
+  float4 o_cx = box_universe();
+  int4 pg = make_int4(-1, -1, -1, -1), mg = make_int4(-1, -1, -1, -1);
+#pragma unroll 1
   for (int i = 0; i < KPT; ++i) {
-    const int k = kk[i];
-    if (k == K_PAD) break;
+    const int k = (int)((kpack >> (4 * i)) & 15ull);
+    const unsigned bit = 1u << i;
     const int p = p0 + i;
     const int e = base + p;
-    if (BATCHED) {
-      while (e >= sc_next) {
-        ++sc;
-        sc_start = a.offsets[sc];
-        sc_next = a.offsets[sc + 1];
+    float4 bnext = bcur;
+    if (HAS_BOX && i + 1 < KPT) bnext = s_box[box_slot(p + 1)];
+    int par_i = -1, mat_i = -1;
+    if (k != K_PAD) {
+      if (BATCHED) {
+        while (e >= sc_next && sc < a.num_scenes - 1) {
+          ++sc;
+          sc_start = a.offsets[sc];
+          sc_next = a.offsets[sc + 1];
+        }
+        if (e == sc_start && dstart_t + D != 0) atomic_cas_i32(a.status, ST_OK, ST_UNBALANCED);
       }
-      if (e == sc_start && dstart_t + D != 0) atomic_cas_i32(a.status, ST_OK, ST_UNBALANCED);
-    }
-    // Parent and clip context: the local top, else the entry at depth D-1
-    // of the stack at the chunk start.
-    int par;
-    float4 ctx = box_universe();
-    if (sp_n > 0) {
-      par = base + p0 + st_pos[sp_n - 1];
-      ctx = top_clip;
-    } else {
-      const int dd = D - 1;
-      while (own >= 0 && s_lo[own] > dd) own = s_cps[own];
-      if (own >= 0) {
-        const int op = s_spos[own * KPT + (dd - s_lo[own])];
-        par = base + op;
-        if (HAS_BOX) ctx = box_isect(s_B[own], s_box[box_slot(op)]);
-      } else {
-        const int src = s_ctx[-1 - dd];
-        par = src >= 0 ? ws.slice_pos[src] : -1;
-        if (HAS_BOX && src >= 0) ctx = box_isect(ws.t_B[src / TILE], ws.slice_rel[src]);
+      const int lp = (int)((lpar >> (4 * i)) & 15ull);
+      int par = base + p0 + lp;
+      float4 cx = top_clip;
+      if (!(inside & bit)) {
+        // Parent is the entry at depth D-1 of the stack at the chunk start.
+        // Consecutive elements at the chunk's base level share it, so the
+        // last one looked up is kept; a close needs only its index.
+        const int dd = D - 1;
+        if (dd != o_dd) {
+          const int want_clip = HAS_BOX && k != K_CLOSE;
+          const OutRes r = out_lookup<HAS_BOX>(oc, ws, dd, want_clip, own);
+          own = r.own;
+          o_par = r.par;
+          o_cx = r.cx;
+          o_dd = (want_clip || !HAS_BOX) ? dd : INT_MIN;
+        }
+        par = o_par;
+        cx = o_cx;
       }
-    }
-    const int par_out = (BATCHED && par >= 0) ? (int)(par - sc_start) : par;
-    const int e_out = BATCHED ? (int)(e - sc_start) : e;
-    if (k == K_LEAF) {
-      if (parent) parent[e] = par_out;
-      if (match) match[e] = -1;
+      par_i = par;
+      if (pairm & bit) mat_i = base + p0 + (int)((lmate >> (4 * i)) & 15ull);
+      else if (k == K_CLOSE) mat_i = par;
       if (HAS_BOX) {
         float4* b = &s_box[box_slot(p)];
-        const float4 out = box_canon(box_isect(*b, ctx));
-        *b = out;
-        run = box_unite(run, out);
-        if (sp_n > 0) cur_acc = box_unite(cur_acc, out);
-      }
-    } else if (k == K_CLIP || k == K_BLEND) {
-      if (parent) parent[e] = par_out;
-      float4 clip = ctx;
-      if (HAS_BOX) {
-        float4* b = &s_box[box_slot(p)];
-        if ((um >> i) & 1u) {
-          clip = box_isect(Bx, *b);  // chunk-slice entry: B(j) * relative clip
-        } else {
-          if (k == K_CLIP) clip = box_isect(ctx, *b);
-          *b = clip;  // kept for when this open is the top again
-        }
-      }
-      if (sp_n > 0) st_acc[sp_n - 1] = cur_acc;
-      st_pos[sp_n++] = (uint8_t)i;
-      cur_acc = box_empty();
-      top_clip = clip;
-      ++D;
-    } else {  // close
-      if (sp_n > 0) {
-        const int oi = st_pos[--sp_n];
-        const int o = base + p0 + oi;
-        const int o_out = BATCHED ? (int)(o - sc_start) : o;
-        if (parent) parent[e] = o_out;
-        if (match) {
-          match[e] = o_out;
-          match[o] = e_out;
-        }
-        if (HAS_BOX) {
-          const float4 U = cur_acc;
-          s_box[box_slot(p0 + oi)] = U;
-          s_box[box_slot(p)] = U;
-          if (sp_n > 0) {
-            cur_acc = box_unite(st_acc[sp_n - 1], U);
-            const int ti = st_pos[sp_n - 1];
-            const float4 tb = s_box[box_slot(p0 + ti)];
-            top_clip = ((um >> ti) & 1u) ? box_isect(Bx, tb) : tb;
-          } else {
+        const float4 iv = box_isect(bcur, cx);
+        if (k == K_LEAF) {
+          const float4 out = box_canon(iv);
+          *b = out;
+          pre = box_unite(pre, out);
+          if (parpair & bit) cur_acc = box_unite(cur_acc, out);
+        } else if (k == K_CLOSE) {
+          if (inside & bit) {
+            // in-chunk pair: write its union at both ends, return to the
+            // enclosing open's clip and partial union
+            const float4 U = cur_acc;
+            s_box[box_slot(p0 + lp)] = U;
+            *b = U;
             cur_acc = box_empty();
+            if (cl_gin & bit) {
+              const int gp = (int)((lA >> (4 * i)) & 15ull);
+              const float4 g = s_box[box_slot(p0 + gp)];
+              top_clip = (cl_gum & bit) ? box_isect(Bx, g) : g;
+              if (cl_gpair & bit)
+                cur_acc = box_unite(s_box[box_slot(p0 + (int)((lB >> (4 * i)) & 15ull))], U);
+            }
+          } else {
+            *b = pre;  // matches an open before the chunk: everything before it is inside
+          }
+        } else {  // open
+          float4 clip;
+          if (um & bit) {
+            clip = box_isect(Bx, bcur);  // chunk-slice entry: B(j) * relative clip
+          } else {
+            clip = (k == K_CLIP) ? iv : cx;
+            *b = clip;  // read back when a close returns to this open
+          }
+          top_clip = clip;
+          if (savem & bit) s_box[box_slot(p0 + (int)((lA >> (4 * i)) & 15ull))] = cur_acc;
+          if (pairm & bit) cur_acc = box_empty();
+        }
+      }
+      if (BATCHED) {
+        if (par_i >= 0) par_i = (int)(par_i - sc_start);
+        if (mat_i >= 0) mat_i = (int)(mat_i - sc_start);
+      }
+      D += kind_delta(k);
+    }
+    bcur = bnext;
+    const int q = i & 3;
+    pg.x = q == 0 ? par_i : pg.x;
+    pg.y = q == 1 ? par_i : pg.y;
+    pg.z = q == 2 ? par_i : pg.z;
+    pg.w = q == 3 ? par_i : pg.w;
+    mg.x = q == 0 ? mat_i : mg.x;
+    mg.y = q == 1 ? mat_i : mg.y;
+    mg.z = q == 2 ? mat_i : mg.z;
+    mg.w = q == 3 ? mat_i : mg.w;
+    if (q == 3) {
+      // parent / match of four elements (opens matched outside the chunk get
+      // -1 here; their close writes the real value later)
+      const int e4 = e - 3;
+      if (a.vec_out && e4 + 4 <= a.n) {
+        if (a.parent) *reinterpret_cast<int4*>(a.parent + e4) = pg;
+        if (a.match) *reinterpret_cast<int4*>(a.match + e4) = mg;
+      } else {
+        const int pa[4] = {pg.x, pg.y, pg.z, pg.w};
+        const int ma[4] = {mg.x, mg.y, mg.z, mg.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          if (e4 + r < a.n) {
+            if (a.parent) a.parent[e4 + r] = pa[r];
+            if (a.match) a.match[e4 + r] = ma[r];
           }
         }
-      } else {
-        // Matches an open before the chunk: the context entry at depth D-1.
-        if (parent) parent[e] = par_out;
-        if (match) {
-          match[e] = par_out;
-          if (par >= 0) match[par] = e_out;
-        }
-        if (HAS_BOX) s_box[box_slot(p)] = run;  // leaves of the chunk before it
-        xc_i[nxc] = (uint8_t)i;
-        xc_d[nxc] = D - 1;
-        ++nxc;
       }
-      --D;
     }
   }
+  __syncthreads();  // every walk has finished; relative clips are no longer read
 
-  if (!HAS_BOX) return;
-
-  // Unions of the opens still on the local stack over the rest of the
-  // chunk: fold from the top down.
-  {
-    float4 u = box_empty();
-    for (int s = sp_n - 1; s >= 0; --s) {
-      const float4 acc_s = (s == sp_n - 1) ? cur_acc : st_acc[s];
-      u = box_unite(acc_s, u);
-      st_acc[s] = u;
-    }
-  }
-  __syncthreads();  // every walk has finished reading relative clips
-  for (int s = 0; s < sp_n; ++s) s_box[box_slot(p0 + st_pos[s])] = st_acc[s];
-  float4* s_ut = s_val;  // union tree over the chunks' leaf unions
-  s_ut[NT + tid] = run;
-  __syncthreads();
-  for (int h = NT >> 1; h >= 1; h >>= 1) {
-    if (tid < h) s_ut[h + tid] = box_unite(s_ut[2 * (h + tid)], s_ut[2 * (h + tid) + 1]);
-    __syncthreads();
-  }
-
-  // Closes matching an open of an earlier chunk: union = the open's chunk
-  // after it + whole chunks in between + this chunk before the close.
-  {
+  if (!HAS_BOX) {
+    // Closes matching an open of an earlier chunk of this tile write that
+    // open's match (after the owner's vector store above); closes matching an
+    // open of an earlier tile leave it to the cross-tile pass.
     int u = cq;
-    for (int c = 0; c < nxc; ++c) {
-      const int cp = p0 + xc_i[c];
-      const int dd = xc_d[c];
-      const float4 upre = s_box[box_slot(cp)];
+    int64_t scs = sc_start0, scn = sc_next0;
+    int scx = sc0c;
+    unsigned m = xcl;
+    while (m) {
+      const int i = lowest_set(m);
+      m &= m - 1;
+      const unsigned below = (1u << i) - 1u;
+      const int dd = ds + popc(openm & below) - popc(closem & below) - 1;
+      const int e = base + p0 + i;
+      if (BATCHED) {
+        while (e >= scn && scx < a.num_scenes - 1) {
+          ++scx;
+          scs = a.offsets[scx];
+          scn = a.offsets[scx + 1];
+        }
+      }
+      const int eo = BATCHED ? (int)(e - scs) : e;
       while (u >= 0 && s_lo[u] > dd) u = s_cps[u];
       if (u >= 0) {
+        if (a.match) a.match[base + s_spos[u * KPT + (dd - s_lo[u])]] = eo;
+      } else {
+        ws.cpos[(size_t)t * TILE + (-1 - dd)] = e;
+        ws.cval[(size_t)t * TILE + (-1 - dd)] = eo;
+      }
+    }
+    return;
+  }
+
+  // ---- unions across chunks (and the partial unions of cross-tile pairs)
+  // Union of the chunk's leaves after each unmatched open: everything after
+  // it in the chunk is inside it.
+  float4 run = box_empty();
+#pragma unroll
+  for (int i = KPT - 1; i >= 0; --i) {
+    if ((leafm >> i) & 1u) run = box_unite(run, s_box[box_slot(p0 + i)]);
+    if ((um >> i) & 1u) s_box[box_slot(p0 + i)] = run;
+  }
+  const int later_lo = block_excl_suffix_min(lo_j, s_scr);
+  float4* s_ut = s_val;  // union tree over the chunks' leaf unions
+  build_chunk_tree(s_ut, run, OpUnite());
+  // span(x) = union of the chunks (cps(x), x]: what a close gains when its
+  // open's owner moves one cps link down
+  s_span[tid] = chunk_range(s_ut, cps + 1, tid, box_empty(), OpUnite());
+  float4 mid = chunk_range(s_ut, cq + 1, tid - 1, box_empty(), OpUnite());
+  const float4 rest = chunk_range(s_ut, tid + 1, NT - 1, box_empty(), OpUnite());
+  __syncthreads();
+  {
+    // Closes matching an open of an earlier chunk: union = the open's chunk
+    // after it + whole chunks in between + this chunk before the close.
+    int u = cq;
+    int64_t scs = sc_start0, scn = sc_next0;
+    int scx = sc0c;
+    unsigned m = xcl;
+    while (m) {
+      const int i = lowest_set(m);
+      m &= m - 1;
+      const unsigned below = (1u << i) - 1u;
+      const int dd = ds + popc(openm & below) - popc(closem & below) - 1;
+      const int cp = p0 + i;
+      const int e = base + cp;
+      if (BATCHED) {
+        while (e >= scn && scx < a.num_scenes - 1) {
+          ++scx;
+          scs = a.offsets[scx];
+          scn = a.offsets[scx + 1];
+        }
+      }
+      const int eo = BATCHED ? (int)(e - scs) : e;
+      const float4 upre = s_box[box_slot(cp)];
+      while (u >= 0 && s_lo[u] > dd) {
+        mid = box_unite(mid, s_span[u]);
+        u = s_cps[u];
+      }
+      if (u >= 0) {
         const int op = s_spos[u * KPT + (dd - s_lo[u])];
-        const float4 mid = tree_range(s_ut, NT, u + 1, tid - 1, box_empty(), OpUnite());
         const float4 U = box_unite(box_unite(s_box[box_slot(op)], mid), upre);
         s_box[box_slot(op)] = U;
         s_box[box_slot(cp)] = U;
+        if (a.match) a.match[base + op] = eo;
       } else {
-        const int m = -1 - dd;
-        const float4 mid = tree_range(s_ut, NT, 0, tid - 1, box_empty(), OpUnite());
-        ws.upre[(size_t)t * TILE + m] = box_unite(mid, upre);
-        ws.cpos[(size_t)t * TILE + m] = base + cp;
+        const int mm = -1 - dd;
+        ws.upre[(size_t)t * TILE + mm] = box_unite(mid, upre);
+        ws.cpos[(size_t)t * TILE + mm] = e;
+        ws.cval[(size_t)t * TILE + mm] = eo;
       }
     }
   }
   // Opens left unmatched at the tile end: union over the rest of the tile.
-  if (sp_n > 0) {
-    const int later_lo = tree_range(s_tree, NT, tid + 1, NT - 1, INT_MAX, OpMin());
-    const float4 rest = tree_range(s_ut, NT, tid + 1, NT - 1, box_empty(), OpUnite());
-    for (int s = 0; s < sp_n; ++s) {
-      const int dd = lo_j + s;
-      if (dd < later_lo) ws.usuf[(size_t)t * TILE + dd + a_t] = box_unite(st_acc[s], rest);
+  {
+    unsigned m = um;
+    int dd = lo_j;
+    while (m) {
+      const int i = lowest_set(m);
+      m &= m - 1;
+      if (dd < later_lo)
+        ws.usuf[(size_t)t * TILE + dd + a_t] = box_unite(s_box[box_slot(p0 + i)], rest);
+      ++dd;
     }
   }
   if (tid == 0) ws.t_uall[t] = s_ut[1];
@@ -647,48 +1002,57 @@ __global__ void __launch_bounds__(NT2) k4_union_tree(SceneWs ws) {
 
 struct K4Args {
   float4* box_out;
+  int32_t* match;
   SceneWs ws;
 };
 
+// One block per tile with closes matching opens of earlier tiles: writes
+// match[open] and, with boxes, the union at both ends of the pair.
+template <bool HAS_BOX>
 __global__ void __launch_bounds__(NT) k4_cross_tile_unions(K4Args a) {
-  __shared__ SegState S;
-  __shared__ float4 s_mid[SEG_CAP];
+  __shared__ int4 s_seg[SEGK];
+  __shared__ float4 s_mid[SEGK];
+  __shared__ int s_nseg;
   const SceneWs& ws = a.ws;
   const int t = blockIdx.x, tid = threadIdx.x;
   const int a_t = ws.t_a[t];
   if (a_t == 0) return;
   const int dstart = ws.t_dstart[t];
-  if (tid == 0) {
-    S.u = ws.t_q[t];
-    S.dtop = dstart - 1;
-    S.dbot = dstart - a_t;
+  if (tid == 0) s_nseg = ws.t_nseg[t];
+  if (tid < SEGK) {
+    const int4 sg = ws.t_seg[(size_t)t * SEGK + tid];
+    s_seg[tid] = sg;
   }
   __syncthreads();
-  for (;;) {
-    if (tid == 0) seg_collect(S, ws.t_ps, ws.t_lo);
-    __syncthreads();
-    if (tid < S.n) {
-      const int u = S.seg_u[tid];
-      s_mid[tid] = u >= 0 ? tree_range(ws.uall_tree, ws.P, u + 1, t - 1, box_empty(), OpUnite())
-                          : box_empty();
+  const int nseg = s_nseg;
+  const bool ovf = nseg > SEGK;
+  if (HAS_BOX && !ovf && tid < nseg) {
+    const int u = s_seg[tid].x;
+    s_mid[tid] = u >= 0 ? tree_range(ws.uall_tree, ws.P, u + 1, t - 1, box_empty(), OpUnite())
+                        : box_empty();
+  }
+  __syncthreads();
+  for (int m = tid; m < a_t; m += NT) {
+    const int d = dstart - 1 - m;
+    int src, s = -1;
+    if (ovf) {
+      src = ws.ctx_src[(size_t)t * (TILE + 1) + m];
+    } else {
+      s = segk_find(s_seg, nseg, d);
+      src = (s >= 0 && s_seg[s].x >= 0) ? s_seg[s].x * TILE + (d - s_seg[s].y) : -1;
     }
-    __syncthreads();
-    const int hi = S.seg_hi[0], lo = S.seg_lo[S.n - 1];
-    for (int m = dstart - 1 - hi + tid; m <= dstart - 1 - lo; m += NT) {
-      const int d = dstart - 1 - m;
-      const int s = seg_find(S, d);
-      const int u = s >= 0 ? S.seg_u[s] : -1;
-      if (u < 0) continue;
-      const int src = u * TILE + (d - S.seg_ulo[s]);
-      const int o = ws.slice_pos[src];
+    if (src < 0) continue;  // unbalanced input
+    const int o = ws.slice_pos[src];
+    if (a.match) a.match[o] = ws.cval[(size_t)t * TILE + m];
+    if (HAS_BOX) {
+      const int u = src / TILE;
+      const float4 mid = ovf ? tree_range(ws.uall_tree, ws.P, u + 1, t - 1, box_empty(), OpUnite())
+                             : s_mid[s];
       const int c = ws.cpos[(size_t)t * TILE + m];
-      const float4 U = box_unite(box_unite(ws.usuf[src], s_mid[s]), ws.upre[(size_t)t * TILE + m]);
+      const float4 U = box_unite(box_unite(ws.usuf[src], mid), ws.upre[(size_t)t * TILE + m]);
       a.box_out[o] = U;
       a.box_out[c] = U;
     }
-    const bool done = S.done;
-    __syncthreads();
-    if (done) break;
   }
 }
 
