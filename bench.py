@@ -1,13 +1,16 @@
-"""Benchmark of the bounding-box + parentheses-matching pass on GB300.
+"""Benchmark of the bounding-box + parentheses-matching pass and of the
+differentiable transform tree scan on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload rw26|chain24|flat24|batched|rw24|rw16]
+                    [--workload rw26|chain24|flat24|batched|rw24|rw16|skel20|skel20s|skelbatch]
 
-One step = one full pass (tile summaries with look-back, tile-level
-resolve, main tile pass, cross-tile unions) over one synthetic scene already
-resident in HBM.  Prints one JSON line (rank 0).  With N > 1 (torchrun), each
-rank runs its own replica of the workload on its own GPU (independent scenes,
-no collective on the data path) and the value is the whole-job throughput.
+Scene workloads: one step = one full pass (tile summaries with look-back,
+tile-level resolve, main tile pass, cross-tile unions) over one synthetic
+scene already resident in HBM.  Skeleton workloads: one step = the affine
+DOWN scan (forward) plus its adjoint (backward) over the joint stream.
+Prints one JSON line (rank 0).  With N > 1 (torchrun), each rank runs its own
+replica of the workload on its own GPU (independent scenes, no collective on
+the data path) and the value is the whole-job throughput.
 
 ``--impl reference`` times the sequential CPU oracle (the checker) on the
 same workload on the host cores instead.
@@ -36,7 +39,14 @@ WORKLOADS = {
     "batched": "bbox+paren pass, 4096 random-walk scenes with N_s = round(2^U[8,18]), one batched call",
     "rw16": "bbox+paren pass, one random-walk scene, N=2^16 (L2-resident)",
     "rw24": "bbox+paren pass, one random-walk scene, N=2^24 (profiling size)",
+    "skel20": "affine tree scan forward + adjoint, one skeleton of J=2^20 joints (N=2J), depth <= 64",
+    "skel20s": "affine tree scan forward + adjoint, one skeleton of J=2^18 joints (profiling size)",
+    "skelbatch": "affine tree scan forward + adjoint through TreeTransform, 256 skeletons with "
+                 "J_s = round(2^U[10,16]), one CUDA graph per step",
 }
+TREE_WORKLOADS = ("skel20", "skel20s", "skelbatch")
+FWD_BYTES_PER_JOINT = 98   # 2 kinds + 48 local read, 48 world written
+BWD_BYTES_PER_JOINT = 146  # 2 kinds + 48 local + 48 grad_world read, 48 grad_local written
 
 # DRAM bytes per launch of the main tile pass measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the
@@ -67,6 +77,14 @@ def make_workload(name, seed=0):
         return k, b, None
     if name == "batched":
         return inputs.batched_scenes(4096, seed)
+    if name == "skel20":
+        k, L, W = inputs.skeleton(1 << 20, seed)
+        return k, L, W, None, None
+    if name == "skel20s":
+        k, L, W = inputs.skeleton(1 << 18, seed)
+        return k, L, W, None, None
+    if name == "skelbatch":
+        return inputs.batched_skeletons(256, seed)
     raise ValueError(name)
 
 
@@ -159,10 +177,26 @@ def time_oracle(kind, box, offsets, budget_s=12.0, min_runs=1, max_runs=50):
             return kind.size * runs / el / 1e9, runs, el
 
 
+def time_oracle_tree(kind, L, W, budget_s=12.0, max_runs=50):
+    import oracle
+    oracle.build()
+    L64, W64 = L.astype(np.float64), W.astype(np.float64)
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        assert oracle.affine_forward(kind, L64)[0] == oracle.OK
+        assert oracle.affine_backward(kind, L64, W64)[0] == oracle.OK
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or runs >= max_runs:
+            return kind.size * runs / el / 1e9, runs, el
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
+    if args.workload in TREE_WORKLOADS:
+        return run_reference_tree(args, world)
     kind, box, offsets = make_workload(args.workload)
     import oracle
     oracle.build()
@@ -192,6 +226,251 @@ def run_reference(args):
     return 0
 
 
+def run_reference_tree(args, world):
+    kind, L, W = make_workload(args.workload)[:3]
+    import oracle
+    oracle.build()
+    L64, W64 = L.astype(np.float64), W.astype(np.float64)
+
+    def once():
+        assert oracle.affine_forward(kind, L64)[0] == oracle.OK
+        assert oracle.affine_backward(kind, L64, W64)[0] == oracle.OK
+    for _ in range(args.warmup):
+        once()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        once()
+    el = time.perf_counter() - t0
+    value = kind.size * args.steps / el / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Gelem/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "n": int(kind.size),
+                       "joints": int(L.shape[0]), "seed": 0},
+            "cpu_baseline": {"value": round(value, 4), "unit": "Gelem/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": "full workload (%d elements) forward + backward per step, "
+                                       "single thread, fp64" % kind.size},
+            "e2e": {"value": round(value, 4), "unit": "Gelem/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_tree(args, torch, world, rank, dev):
+    """Skeleton workloads: forward (affine DOWN scan) + adjoint per step."""
+    from paper_2205_11659_gb300 import binding
+    kind, L, W, eoff, joff = make_workload(args.workload, seed=0)
+    n, J = int(kind.size), int(L.shape[0])
+    k_d = torch.from_numpy(kind).to(dev)
+    L_d = torch.from_numpy(L).to(dev)
+    W_d = torch.from_numpy(W).to(dev)
+    world_d = torch.empty_like(L_d)
+    grad_d = torch.empty_like(L_d)
+    nb = binding.tb_workspace_size(binding.TB_OP_TREE_BACKWARD, n)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    batched = eoff is not None
+
+    def fwd():
+        rc = binding.tb_tree_scan(binding.TB_MONOID_AFFINE3X4_F32, binding.TB_DOWN, k_d, n, J, L_d,
+                                  world_d, ws, nb, status, stream)
+        if rc != binding.TB_OK:
+            raise binding.TBError(rc, "forward")
+
+    def bwd():
+        rc = binding.tb_tree_scan_affine_backward(k_d, n, J, L_d, W_d, grad_d, ws, nb, status,
+                                                  stream)
+        if rc != binding.TB_OK:
+            raise binding.TBError(rc, "backward")
+
+    graph = None
+    if batched:
+        # forward + backward through the autograd function, one graph
+        bws = binding.workspace(dev)
+        bws.reserve(binding.TB_OP_TREE_BACKWARD, n)
+        local = L_d.clone().requires_grad_(True)
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                local.grad = None
+                (binding.TreeTransform.apply(k_d, local, False) * W_d).sum().backward()
+        stream.wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        local.grad = None
+        with torch.cuda.graph(graph):
+            (binding.TreeTransform.apply(k_d, local, False) * W_d).sum().backward()
+
+    for _ in range(max(args.warmup, 3)):
+        fwd()
+        bwd()
+        if graph is not None:
+            graph.replay()
+    torch.cuda.synchronize()
+    assert int(status.item()) == binding.TB_OK, int(status.item())
+    if graph is not None:
+        assert int(binding.workspace(dev).status.item()) == binding.TB_OK
+
+    K = args.steps
+    nf, nbk = 11, 15
+    ev_f = [[torch.cuda.Event(enable_timing=True) for _ in range(nf)] for _ in range(K)]
+    ev_b = [[torch.cuda.Event(enable_timing=True) for _ in range(nbk)] for _ in range(K)]
+    for evs in ev_f + ev_b:
+        for e in evs:
+            e.record(stream)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    for i in range(K):
+        if graph is not None:
+            graph.replay()
+        else:
+            binding.tb_set_phase_events(ev_f[i])
+            fwd()
+            binding.tb_set_phase_events(ev_b[i])
+            bwd()
+    ev1.record(stream)
+    binding.tb_set_phase_events(None)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / K
+    value = world * n / (ms_step * 1e-3) / 1e9
+
+    # per-kernel times of the plain calls (event pairs in launch order)
+    fnames = ["k1", "k2", "k3", "k4", "memset", "rank", "joint", "down_chain", "down_tiles",
+              "down_tile"]
+    bnames = fnames + ["up_tile", "up_tiles", "up_cross", "bwd_final"]
+    if graph is not None:
+        for i in range(K):
+            binding.tb_set_phase_events(ev_f[i])
+            fwd()
+            binding.tb_set_phase_events(ev_b[i])
+            bwd()
+        binding.tb_set_phase_events(None)
+        torch.cuda.synchronize()
+
+    def spans(evs, names):
+        return {nm: statistics.mean(evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(K))
+                for j, nm in enumerate(names)}
+    fph = spans(ev_f, fnames)
+    bph = spans(ev_b, bnames)
+    fwd_ms = statistics.mean(ev_f[i][0].elapsed_time(ev_f[i][nf - 1]) for i in range(K))
+    bwd_ms = statistics.mean(ev_b[i][0].elapsed_time(ev_b[i][nbk - 1]) for i in range(K))
+
+    per_scene = None
+    if batched:
+        # the same skeletons as 256 separate plain forward + backward calls
+        S = len(eoff) - 1
+        parts = []
+        for sidx in range(S):
+            e0, e1, j0, j1 = int(eoff[sidx]), int(eoff[sidx + 1]), int(joff[sidx]), int(joff[sidx + 1])
+            parts.append((k_d[e0:e1].clone(), L_d[j0:j1].clone(), W_d[j0:j1].clone(),
+                          torch.empty_like(L_d[j0:j1]), torch.empty_like(L_d[j0:j1])))
+
+        def per_scene_step():
+            for kk, ll, wg, wo, go in parts:
+                ns, js = kk.numel(), ll.shape[0]
+                binding.tb_tree_scan(binding.TB_MONOID_AFFINE3X4_F32, binding.TB_DOWN, kk, ns, js, ll,
+                                     wo, ws, nb, status, stream)
+                binding.tb_tree_scan_affine_backward(kk, ns, js, ll, wg, go, ws, nb, status, stream)
+        per_scene_step()
+        torch.cuda.synchronize()
+        reps = max(2, min(K, 5))
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(reps):
+            per_scene_step()
+        p1.record(stream)
+        torch.cuda.synchronize()
+        ps_ms = p0.elapsed_time(p1) / reps
+        assert int(status.item()) == binding.TB_OK
+        per_scene = {"value": round(n / (ps_ms * 1e-3) / 1e9, 3), "unit": "Gelem/s",
+                     "ms_per_step": round(ps_ms, 4), "launches": "%d x (forward + backward) plain calls" % S,
+                     "batched_over_per_scene": round(ps_ms / ms_step, 2)}
+
+    # end to end through the public API with pinned host buffers
+    kind_h = torch.from_numpy(kind).pin_memory()
+    L_h = torch.from_numpy(L).pin_memory()
+    W_h = torch.from_numpy(W).pin_memory()
+    world_h = torch.empty_like(L_h).pin_memory()
+    grad_h = torch.empty_like(L_h).pin_memory()
+
+    def e2e_step():
+        kd = kind_h.to(dev, non_blocking=True)
+        ld = L_h.to(dev, non_blocking=True)
+        wd = W_h.to(dev, non_blocking=True)
+        wo = binding.tree_scan(binding.TB_MONOID_AFFINE3X4_F32, binding.TB_DOWN, kd, ld, check=False)
+        go = binding.affine_backward(kd, ld, wd, check=False)
+        world_h.copy_(wo, non_blocking=True)
+        grad_h.copy_(go, non_blocking=True)
+        stream.synchronize()
+        binding.check_status(binding.workspace(dev), "e2e")
+    e2e_step()
+    e2e_steps = max(2, min(K, 5))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+
+    peak, peak_src = measured_peaks()
+    bwd_alg = BWD_BYTES_PER_JOINT * J
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, runs, el = time_oracle_tree(kind, L, W)
+        cpu = {"value": round(v, 4), "unit": "Gelem/s", "cores": 1, "kind": "oracle",
+               "sample": "the full workload (%d elements) forward + backward x %d runs, %.1f s, "
+                         "single thread, fp64" % (n, runs, el)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "Gelem/s", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "n": n, "joints": J, "seed": 0,
+                       "gjoint_per_s": round(world * J / (ms_step * 1e-3) / 1e9, 3),
+                       "step": "one CUDA graph of TreeTransform forward + backward" if batched
+                               else "tb_tree_scan (affine DOWN) + tb_tree_scan_affine_backward",
+                       "l2": "inputs larger than L2, no flush" if 98 * J > 130e6 else
+                             "inputs (%.0f MB) L2-resident, no flush" % (98 * J / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "kernel": "tb_tree_scan_affine_backward (all its launches)",
+                         "achieved": round(bwd_alg / (bwd_ms * 1e-3) / 1e9, 1), "peak": peak,
+                         "peak_source": peak_src, "unit": "GB/s",
+                         "frac": round(bwd_alg / (bwd_ms * 1e-3) / 1e9 / peak, 4), "traffic": None,
+                         "algorithmic_bytes_per_launch": bwd_alg},
+            "forward_roofline_frac": round(FWD_BYTES_PER_JOINT * J / (fwd_ms * 1e-3) / 1e9 / peak, 4),
+            "forward_ms": round(fwd_ms, 4), "backward_ms": round(bwd_ms, 4),
+            "backward_gjoint_per_s": round(J / (bwd_ms * 1e-3) / 1e9, 3),
+            "phases_ms": {"forward": {k: round(v, 4) for k, v in fph.items()},
+                          "backward": {k: round(v, 4) for k, v in bph.items()}},
+            "per_scene": per_scene,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(world * n / e2e_s / 1e9, 3), "unit": "Gelem/s",
+                    "h2d_bytes_per_step": int(kind.nbytes + L.nbytes + W.nbytes),
+                    "d2h_bytes_per_step": int(2 * L.nbytes)},
+            "gpu_launches": (9 + 13) * K,
+            "clocks": clk,
+            "kernel_hash": kernel_hash(),
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup()
@@ -204,6 +483,12 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     from paper_2205_11659_gb300 import _build, binding
     _build.build()
+    if args.workload in TREE_WORKLOADS:
+        rc = run_tree(args, torch, world, rank, dev)
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return rc
 
     kind, box, offsets = make_workload(args.workload, seed=0)
     n = int(kind.size)

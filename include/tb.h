@@ -63,8 +63,24 @@ enum { TB_LEAF = 0, TB_OPEN_CLIP = 1, TB_OPEN_BLEND = 2, TB_CLOSE = 3 };
 enum {
   TB_OP_MATCH_PARENS = 0,
   TB_OP_BBOXES = 1,
-  TB_OP_BBOXES_BATCHED = 2
+  TB_OP_BBOXES_BATCHED = 2,
+  TB_OP_TREE_SCAN = 3,
+  TB_OP_TREE_BACKWARD = 4
 };
+
+/* Monoids and directions of tb_tree_scan. */
+typedef enum {
+  TB_MONOID_BBOX_ISECT = 0,   /* float4 boxes, intersection, identity (-inf,-inf,+inf,+inf) */
+  TB_MONOID_BBOX_UNION = 1,   /* float4 boxes, union, identity (+inf,+inf,-inf,-inf) */
+  TB_MONOID_ADD_I32 = 2,      /* int32, addition modulo 2^32, identity 0 */
+  TB_MONOID_AFFINE3X4_F32 = 3 /* 12 floats, row-major [R | t] (x -> R x + t),
+                                 composition A*B = apply B then A, identity [I | 0] */
+} tb_monoid;
+
+typedef enum {
+  TB_DOWN = 0, /* each joint: fold along its root path, the root first */
+  TB_UP = 1    /* each joint: fold over its subtree, in stream order */
+} tb_dir;
 
 /* Bytes of scratch the operation needs for n elements (num_scenes is used
  * by TB_OP_BBOXES_BATCHED only).  Never fails; 0 for n == 0. */
@@ -107,13 +123,53 @@ tb_status tb_bboxes_batched(const uint8_t* kind, const float* box,
                             float* box_out, void* ws, size_t ws_bytes,
                             int32_t* d_status, void* stream);
 
-/* Tracing hook.  After tb_set_phase_events(events, 5) every later call of
- * tb_match_parens / tb_bboxes / tb_bboxes_batched records, on its own
- * stream, events[0] before the tile-summary pass, events[1] before the
- * tile-level resolve, events[2] before the main tile pass, events[3] before
- * the cross-tile union step and events[4] at the end.  events holds
- * cudaEvent_t handles created by the caller; tb_set_phase_events(NULL, 0)
- * turns the hook off.  The setting is per host thread. */
+/* Tree scans: the monoid generalisation of Sec. 1 and Sec. 13 (any
+ * associative operation with an identity, neither commutative nor
+ * idempotent required).  Values belong to the opens ("joints"): joint r is
+ * the r-th open of the stream (pre-order rank), leaves carry none.
+ * num_joints must equal the number of opens (at most n / 2); in and out hold
+ * num_joints values of the monoid's type (4, 16 or 48 bytes each) and must
+ * not overlap.
+ *   TB_DOWN: out[r] = in[root] * ... * in[parent(r)] * in[r]
+ *            (ancestor on the left; for transforms, world = parent world
+ *            times local).
+ *   TB_UP:   out[r] = fold of in[d] over the joints d of r's subtree (r
+ *            itself first), in stream order.
+ * A stream of several trees (a forest, e.g. skeletons laid end to end) is
+ * fine: each tree is scanned on its own.  A wrong num_joints is reported as
+ * TB_ERR_INVALID_ARG in d_status; unbalanced streams and bad kinds as in
+ * tb_match_parens. */
+tb_status tb_tree_scan(int monoid, int dir, const uint8_t* kind, int64_t n,
+                       int64_t num_joints, const void* in, void* out, void* ws,
+                       size_t ws_bytes, int32_t* d_status, void* stream);
+
+/* Adjoint of the affine TB_DOWN scan for the loss sum_r <W_r, world_r>
+ * (Frobenius product of 3x4 matrices), given grad_world[r] = W_r:
+ *   grad_local[r] = d loss / d local[r]
+ * local, grad_world and grad_local hold num_joints 3x4 row-major float
+ * matrices.  The forward transforms are recomputed, not read from a saved
+ * forward pass.  With A_r = sum over r's subtree of W_d (x) world_d^T (the
+ * product of homogeneous 4x4 forms), Gbar_r = A_r world_r^{-T} and
+ * grad_local[r] = R_parent(r)^T Gbar_r (Gbar_r at a root), where R is the
+ * rotation part of the parent's world transform.  Needs invertible local
+ * rotation parts. */
+tb_status tb_tree_scan_affine_backward(const uint8_t* kind, int64_t n,
+                                       int64_t num_joints, const float* local,
+                                       const float* grad_world,
+                                       float* grad_local, void* ws,
+                                       size_t ws_bytes, int32_t* d_status,
+                                       void* stream);
+
+/* Tracing hook.  After tb_set_phase_events(events, k) (1 <= k <= 16) every
+ * later call on this host thread records, on its own stream, events[0],
+ * events[1], ... in launch order: one before each kernel of the call and
+ * one after its last kernel, until the k events run out.  The matching
+ * calls (tb_match_parens, tb_bboxes, tb_bboxes_batched) use five: before the
+ * tile-summary pass, the tile-level resolve, the main tile pass and the
+ * cross-tile union step, and at the end.  The tree scans start with the same
+ * five for their matching pass, then the rank pass, the joint pass and the
+ * scan kernels in order.  events holds cudaEvent_t handles created by the
+ * caller; tb_set_phase_events(NULL, 0) turns the hook off. */
 tb_status tb_set_phase_events(void* const* events, int num_events);
 
 /* Allocation-free form of tb_bboxes, for callers that cannot allocate

@@ -6,8 +6,11 @@ of ``_build/libtb.so``.  There is no CPU implementation behind these calls:
 if the library is not built, or a tensor is not on a CUDA device, they raise.
 
 The ``tb_*`` functions mirror the C entry points one to one.  ``match_parens``,
-``bboxes`` and ``bboxes_batched`` are conveniences that allocate outputs and
-workspace with torch, check the device status word and raise on errors.
+``bboxes``, ``bboxes_batched``, ``tree_scan`` and ``affine_backward`` are
+conveniences that allocate outputs and workspace with torch, check the device
+status word and raise on errors.  ``TreeTransform`` is the autograd function
+of the affine root-path product (forward: DOWN scan, backward: the
+hand-written adjoint).
 """
 import ctypes
 import os
@@ -31,6 +34,15 @@ STATUS_NAMES = {0: "TB_OK", 1: "TB_ERR_INVALID_ARG", 2: "TB_ERR_UNBALANCED",
 TB_OP_MATCH_PARENS = 0
 TB_OP_BBOXES = 1
 TB_OP_BBOXES_BATCHED = 2
+TB_OP_TREE_SCAN = 3
+TB_OP_TREE_BACKWARD = 4
+
+TB_MONOID_BBOX_ISECT = 0
+TB_MONOID_BBOX_UNION = 1
+TB_MONOID_ADD_I32 = 2
+TB_MONOID_AFFINE3X4_F32 = 3
+TB_DOWN = 0
+TB_UP = 1
 
 LEAF, OPEN_CLIP, OPEN_BLEND, CLOSE = 0, 1, 2, 3
 
@@ -67,8 +79,10 @@ def lib():
             L.tb_bboxes_batched.argtypes = [p, p, p, i64, i64, p, p, p, p, sz, p, p]
             L.tb_set_phase_events.argtypes = [p, i32]
             L.tb_bboxes_static_ws.argtypes = [p, p, i64, p, p, p, p, p]
+            L.tb_tree_scan.argtypes = [i32, i32, p, i64, i64, p, p, p, sz, p, p]
+            L.tb_tree_scan_affine_backward.argtypes = [p, i64, i64, p, p, p, p, sz, p, p]
             for f in (L.tb_match_parens, L.tb_bboxes, L.tb_bboxes_batched, L.tb_set_phase_events,
-                      L.tb_bboxes_static_ws):
+                      L.tb_bboxes_static_ws, L.tb_tree_scan, L.tb_tree_scan_affine_backward):
                 f.restype = i32
             L.tb_version.argtypes = []
             L.tb_version.restype = ctypes.c_char_p
@@ -134,8 +148,23 @@ def tb_bboxes_static_ws(kind, box, n, parent, match, box_out, d_status, stream=N
 TB_STATIC_WS_MAX_N = 1 << 17
 
 
+def tb_tree_scan(monoid, direction, kind, n, num_joints, values, out, ws, ws_bytes, d_status,
+                 stream=None):
+    return lib().tb_tree_scan(int(monoid), int(direction), _ptr(kind), int(n), int(num_joints),
+                              _ptr(values), _ptr(out), _ptr(ws), int(ws_bytes), _ptr(d_status),
+                              _stream(stream))
+
+
+def tb_tree_scan_affine_backward(kind, n, num_joints, local, grad_world, grad_local, ws,
+                                 ws_bytes, d_status, stream=None):
+    return lib().tb_tree_scan_affine_backward(_ptr(kind), int(n), int(num_joints), _ptr(local),
+                                              _ptr(grad_world), _ptr(grad_local), _ptr(ws),
+                                              int(ws_bytes), _ptr(d_status), _stream(stream))
+
+
 def tb_set_phase_events(events):
-    """events: five recorded torch.cuda.Event objects, or None to disable."""
+    """events: 1 to 16 torch.cuda.Event objects (recorded in launch order), or
+    None to disable."""
     if events is None:
         return lib().tb_set_phase_events(None, 0)
     arr = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
@@ -155,6 +184,11 @@ class Workspace:
         if self.buf.numel() < nbytes:
             self.buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
         return self.buf
+
+    def reserve(self, op, n, num_scenes=0):
+        """Grow now, so that later calls of up to n elements allocate nothing
+        (needed before capturing calls into a CUDA graph)."""
+        self.get(tb_workspace_size(op, n, num_scenes))
 
 
 _ws = {}
@@ -292,3 +326,79 @@ def bboxes_host(kind, box, out):
 def bboxes_batched_host(kind, box, offsets, out):
     """bboxes_batched() for pinned host tensors, filling ``out``."""
     return _host_call("tb_bboxes_batched", [kind, box.reshape(-1, 4), offsets], out, None)
+
+
+# ------------------------------------------------------------- tree scans
+_VALUE_SHAPE = {TB_MONOID_BBOX_ISECT: ((4,), torch.float32),
+                TB_MONOID_BBOX_UNION: ((4,), torch.float32),
+                TB_MONOID_ADD_I32: ((), torch.int32),
+                TB_MONOID_AFFINE3X4_F32: ((3, 4), torch.float32)}
+
+
+def tree_scan(monoid, direction, kind, values, check=True):
+    """tb_tree_scan on device tensors: values holds one monoid value per open
+    of ``kind`` in stream order ((J, 4) float32 boxes, (J,) int32, or
+    (J, 3, 4) float32 transforms); returns a tensor of the same shape."""
+    shape, dtype = _VALUE_SHAPE[monoid]
+    dev = kind.device
+    if not kind.is_cuda or not values.is_cuda:
+        raise ValueError("tree_scan takes CUDA tensors")
+    k = _on_device(kind, torch.uint8, "kind", dev)
+    v = _on_device(values, dtype, "values", dev)
+    J = v.shape[0] if v.dim() > 0 else 0
+    if tuple(v.shape[1:]) != shape:
+        raise ValueError("values must have shape (J,) + %s" % (shape,))
+    n = k.numel()
+    out = torch.empty_like(v)
+    ws = workspace(dev)
+    nb = tb_workspace_size(TB_OP_TREE_SCAN, n)
+    _check(tb_tree_scan(monoid, direction, k, n, J, v, out, ws.get(nb), nb, ws.status),
+           "tb_tree_scan")
+    if check:
+        check_status(ws, "tb_tree_scan")
+    return out
+
+
+def affine_backward(kind, local, grad_world, check=True):
+    """grad_local of sum_r <grad_world_r, world_r> for world = DOWN affine
+    scan of ``local`` ((J, 3, 4) float32 device tensors)."""
+    dev = kind.device
+    if not kind.is_cuda or not local.is_cuda or not grad_world.is_cuda:
+        raise ValueError("affine_backward takes CUDA tensors")
+    k = _on_device(kind, torch.uint8, "kind", dev)
+    L = _on_device(local, torch.float32, "local", dev)
+    G = _on_device(grad_world, torch.float32, "grad_world", dev)
+    if L.shape != G.shape or tuple(L.shape[1:]) != (3, 4):
+        raise ValueError("local and grad_world must both have shape (J, 3, 4)")
+    n, J = k.numel(), L.shape[0]
+    out = torch.empty_like(L)
+    ws = workspace(dev)
+    nb = tb_workspace_size(TB_OP_TREE_BACKWARD, n)
+    _check(tb_tree_scan_affine_backward(k, n, J, L, G, out, ws.get(nb), nb, ws.status),
+           "tb_tree_scan_affine_backward")
+    if check:
+        check_status(ws, "tb_tree_scan_affine_backward")
+    return out
+
+
+class TreeTransform(torch.autograd.Function):
+    """world = TreeTransform.apply(kind, local[, check]).
+
+    local: (J, 3, 4) float32 local transforms, one per open of ``kind`` in
+    stream order; world[r] = world[parent(r)] * local[r].  The backward pass
+    recomputes world inside the library (nothing but kind and local is saved)
+    and runs the hand-written adjoint.  With check=False no call reads the
+    device status word, so forward and backward can be captured in a CUDA
+    graph (reserve the workspace first)."""
+
+    @staticmethod
+    def forward(ctx, kind, local, check=True):
+        ctx.save_for_backward(kind, local)
+        ctx.check = check
+        return tree_scan(TB_MONOID_AFFINE3X4_F32, TB_DOWN, kind, local.detach(), check=check)
+
+    @staticmethod
+    def backward(ctx, grad_world):
+        kind, local = ctx.saved_tensors
+        g = affine_backward(kind, local, grad_world.contiguous(), check=ctx.check)
+        return None, g, None

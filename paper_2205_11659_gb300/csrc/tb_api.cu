@@ -7,6 +7,7 @@
 #include <mutex>
 
 #include "tb.h"
+#include "tb_internal.h"
 #include "tb_scene_kernels.cuh"
 
 namespace {
@@ -114,12 +115,14 @@ SceneWs scene_ws(const Layout& L, void* ws, bool has_box) {
   return w;
 }
 
-// Caller-owned events recorded between the phases of a scene call.
-thread_local cudaEvent_t g_phase_events[5];
-thread_local bool g_phase_on = false;
+// Caller-owned events recorded between the kernels of a call.
+constexpr int kMaxPhaseEvents = 16;
+thread_local cudaEvent_t g_phase_events[kMaxPhaseEvents];
+thread_local int g_phase_n = 0;
+thread_local int g_phase_next = 0;
 
-inline void phase_mark(int i, cudaStream_t s) {
-  if (g_phase_on) cudaEventRecord(g_phase_events[i], s);
+inline void phase_mark(cudaStream_t s) {
+  if (g_phase_next < g_phase_n) cudaEventRecord(g_phase_events[g_phase_next++], s);
 }
 
 bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
@@ -189,20 +192,20 @@ tb_status run_scene(const uint8_t* kind, const float* box, int64_t n, int32_t* p
   const SceneWs w = scene_ws(L, ws, HAS_BOX);
   if (cudaMemsetAsync(ws, 0, L.t_a, s) != cudaSuccess) return TB_ERR_CUDA;
 
-  phase_mark(0, s);
+  phase_mark(s);
   K1Args a1{kind, reinterpret_cast<const float4*>(box), (int)n, w, d_status, withhold_tile};
   k1_tile_summary<HAS_BOX><<<L.T, NT, 0, s>>>(a1);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
-  phase_mark(1, s);
+  phase_mark(s);
   if (launch_k2<HAS_BOX>(w, s) != cudaSuccess) return TB_ERR_CUDA;
 
-  phase_mark(2, s);
+  phase_mark(s);
   const int vec_out = (!parent || aligned(parent, 16)) && (!match || aligned(match, 16));
   K3Args a3{kind, reinterpret_cast<const float4*>(box), (int)n, parent, match,
             reinterpret_cast<float4*>(box_out), offsets, (int)num_scenes, vec_out, w, d_status};
   cudaError_t e = offsets ? launch_k3<HAS_BOX, true>(a3, L.T, s) : launch_k3<HAS_BOX, false>(a3, L.T, s);
   if (e != cudaSuccess) return TB_ERR_CUDA;
-  phase_mark(3, s);
+  phase_mark(s);
   if (HAS_BOX) {
     k4_union_tree<<<1, NT2, 0, s>>>(w);
     if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
@@ -210,7 +213,7 @@ tb_status run_scene(const uint8_t* kind, const float* box, int64_t n, int32_t* p
   K4Args a4{reinterpret_cast<float4*>(box_out), match, w};
   k4_cross_tile_unions<HAS_BOX><<<L.T, NT, 0, s>>>(a4);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
-  phase_mark(4, s);
+  phase_mark(s);
   return TB_OK;
 }
 
@@ -220,13 +223,16 @@ extern "C" {
 
 size_t tb_workspace_size(int op, int64_t n, int64_t num_scenes) {
   (void)num_scenes;
-  if (n <= 0) return 0;
+  if (n <= 0 || n > kMaxN) return 0;
   switch (op) {
     case TB_OP_MATCH_PARENS:
       return scene_layout(n, false).total;
     case TB_OP_BBOXES:
     case TB_OP_BBOXES_BATCHED:
       return scene_layout(n, true).total;
+    case TB_OP_TREE_SCAN:
+    case TB_OP_TREE_BACKWARD:
+      return tb_internal::tree_ws_bytes(op, n);
     default:
       return 0;
   }
@@ -234,6 +240,7 @@ size_t tb_workspace_size(int op, int64_t n, int64_t num_scenes) {
 
 tb_status tb_match_parens(const uint8_t* kind, int64_t n, int32_t* parent, int32_t* match, void* ws,
                           size_t ws_bytes, int32_t* d_status, void* stream) {
+  g_phase_next = 0;
   return run_scene<false>(kind, nullptr, n, parent, match, nullptr, nullptr, 0, ws, ws_bytes,
                           d_status, stream, -1);
 }
@@ -241,6 +248,7 @@ tb_status tb_match_parens(const uint8_t* kind, int64_t n, int32_t* parent, int32
 tb_status tb_bboxes(const uint8_t* kind, const float* box, int64_t n, int32_t* parent,
                     int32_t* match, float* box_out, void* ws, size_t ws_bytes, int32_t* d_status,
                     void* stream) {
+  g_phase_next = 0;
   return run_scene<true>(kind, box, n, parent, match, box_out, nullptr, 0, ws, ws_bytes, d_status,
                          stream, -1);
 }
@@ -250,27 +258,42 @@ tb_status tb_bboxes_batched(const uint8_t* kind, const float* box, const int64_t
                             float* box_out, void* ws, size_t ws_bytes, int32_t* d_status,
                             void* stream) {
   if (offsets == nullptr || num_scenes < 1) return TB_ERR_INVALID_ARG;
+  g_phase_next = 0;
   return run_scene<true>(kind, box, n_total, parent, match, box_out, offsets, num_scenes, ws,
                          ws_bytes, d_status, stream, -1);
 }
 
 tb_status tb_set_phase_events(void* const* events, int num_events) {
   if (events == nullptr) {
-    g_phase_on = false;
+    g_phase_n = 0;
     return TB_OK;
   }
-  if (num_events != 5) return TB_ERR_INVALID_ARG;
-  for (int i = 0; i < 5; ++i) {
+  if (num_events < 1 || num_events > kMaxPhaseEvents) return TB_ERR_INVALID_ARG;
+  for (int i = 0; i < num_events; ++i)
     if (events[i] == nullptr) return TB_ERR_INVALID_ARG;
-    g_phase_events[i] = static_cast<cudaEvent_t>(events[i]);
-  }
-  g_phase_on = true;
+  for (int i = 0; i < num_events; ++i) g_phase_events[i] = static_cast<cudaEvent_t>(events[i]);
+  g_phase_n = num_events;
   return TB_OK;
 }
 
 const char* tb_version(void) { return "treebox-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+namespace tb_internal {
+
+size_t match_ws_bytes(int64_t n) { return n > 0 && n <= kMaxN ? scene_layout(n, false).total : 0; }
+
+tb_status run_match(const uint8_t* kind, int64_t n, int32_t* parent, int32_t* match, void* ws,
+                    size_t ws_bytes, int32_t* d_status, cudaStream_t s) {
+  return run_scene<false>(kind, nullptr, n, parent, match, nullptr, nullptr, 0, ws, ws_bytes,
+                          d_status, s, -1);
+}
+
+void phase_reset() { g_phase_next = 0; }
+void phase_mark(cudaStream_t s) { ::phase_mark(s); }
+
+}  // namespace tb_internal
 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of tb_bboxes.  Its scratch is this file-scope
@@ -317,6 +340,7 @@ tb_status tb_bboxes_static_ws(const uint8_t* kind, const float* box, int64_t n, 
   if (st != TB_OK) return st;
   // run_scene clears the look-back words and the tile counter of the scratch
   // on every call; everything else in it is written before it is read.
+  g_phase_next = 0;
   return run_scene<true>(kind, box, n, parent, match, box_out, nullptr, 0, ws, kStaticWsBytes,
                          d_status, stream, -1);
 }

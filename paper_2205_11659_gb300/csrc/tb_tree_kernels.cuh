@@ -1,0 +1,726 @@
+// tb_tree_kernels.cuh -- folds of a monoid over the tree (Sec. 1 and Sec. 13:
+// the method works for any associative operation with an identity) and the
+// adjoint of the 3x4 affine root-path product.
+//
+// Values live on the opens ("joints"), joint r being the r-th open of the
+// stream (pre-order).  Given the parent and match of every element from the
+// matching pass, the joint tree is described by
+//   jparent[r]  parent joint (-1 at a root), always < r
+//   jend[r]     one past the last joint of r's subtree, so the subtree of r
+//               is the contiguous range [r, jend[r]) (Sec. 6.2)
+//
+// Joints are processed in tiles of JT = 1024 consecutive joints, one block of
+// NT threads each; thread c owns the chunk of JC = 4 joints [c*JC, c*JC+JC).
+//
+// DOWN (root-path fold, ancestor on the left, Sec. 6.1):
+//   * A joint whose subtree runs past the end of its chunk (or tile) is
+//     "exported" from it.  The exported joints of a chunk or tile form one
+//     parent-child chain, and every other joint's nearest ancestor outside
+//     its chunk is an exported joint of an earlier chunk.
+//   * k_down_chain: per tile, the prefix fold of its exported chain relative
+//     to the chain's base (the parent of its first link), and that base.
+//   * k_down_tiles: pointer jumping over tiles (each tile links to the tile
+//     of its base) gives the fold at every tile's base.
+//   * k_down_tile: in-chunk walk relative to each joint's nearest outside
+//     ancestor, pointer jumping over the chunks of the tile, then every joint
+//     combines its outside ancestor's fold with its own relative fold.
+//
+// UP (subtree fold in stream order):
+//   * k_up_tile: in-chunk subtree folds by walking each joint's children,
+//     folds that leave the chunk completed with a segment tree over the
+//     tile's chunk totals, prefix folds over chunks published per tile.
+//   * k_up_tiles: segment tree over the tiles' totals.
+//   * k_up_cross: completes the folds of subtrees that leave their tile.
+//
+// Affine adjoint (loss = sum_r <W_r, world_r>): world by DOWN, then
+// A_r = sum over the subtree of W_d (x) world_d^T by UP, then
+// Gbar_r = A_r world_r^{-T} and dL_r = R_parent^T Gbar_r (k_bwd_final).
+#ifndef TB_TREE_KERNELS_CUH
+#define TB_TREE_KERNELS_CUH
+
+#include "tb_core.cuh"
+
+namespace tb {
+
+constexpr int JC = 4;          // joints per thread
+constexpr int JT = NT * JC;    // joints per tile
+constexpr int NCH = NT;        // chunks per tile
+constexpr int NO_CHAIN = -2;   // tile without exported joints
+constexpr int kMaxJumpRounds = 40;
+constexpr int ST_INVALID = 1;  // TB_ERR_INVALID_ARG
+
+// ------------------------------------------------------------- monoids
+// A 3x4 affine transform [R | t] acting on column vectors, stored as three
+// rows (R_i0, R_i1, R_i2, t_i).
+struct Aff {
+  float4 r0, r1, r2;
+};
+
+__host__ __device__ __forceinline__ Aff aff_identity() {
+  Aff a;
+  a.r0 = make_float4(1.f, 0.f, 0.f, 0.f);
+  a.r1 = make_float4(0.f, 1.f, 0.f, 0.f);
+  a.r2 = make_float4(0.f, 0.f, 1.f, 0.f);
+  return a;
+}
+__host__ __device__ __forceinline__ Aff aff_zero() {
+  Aff a;
+  a.r0 = a.r1 = a.r2 = make_float4(0.f, 0.f, 0.f, 0.f);
+  return a;
+}
+// Row i of A*B where B is applied first: (A*B)x = A(Bx).
+__host__ __device__ __forceinline__ float4 aff_mul_row(float4 a, const Aff& B) {
+  float4 c;
+  c.x = fmaf(a.x, B.r0.x, fmaf(a.y, B.r1.x, a.z * B.r2.x));
+  c.y = fmaf(a.x, B.r0.y, fmaf(a.y, B.r1.y, a.z * B.r2.y));
+  c.z = fmaf(a.x, B.r0.z, fmaf(a.y, B.r1.z, a.z * B.r2.z));
+  c.w = fmaf(a.x, B.r0.w, fmaf(a.y, B.r1.w, fmaf(a.z, B.r2.w, a.w)));
+  return c;
+}
+__host__ __device__ __forceinline__ Aff aff_mul(const Aff& A, const Aff& B) {
+  Aff C;
+  C.r0 = aff_mul_row(A.r0, B);
+  C.r1 = aff_mul_row(A.r1, B);
+  C.r2 = aff_mul_row(A.r2, B);
+  return C;
+}
+__host__ __device__ __forceinline__ float4 f4_add(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__host__ __device__ __forceinline__ Aff aff_add(const Aff& a, const Aff& b) {
+  Aff c;
+  c.r0 = f4_add(a.r0, b.r0);
+  c.r1 = f4_add(a.r1, b.r1);
+  c.r2 = f4_add(a.r2, b.r2);
+  return c;
+}
+__device__ __forceinline__ Aff shfl_up(const Aff& a, int d) {
+  Aff b;
+  b.r0 = shfl_up(a.r0, d);
+  b.r1 = shfl_up(a.r1, d);
+  b.r2 = shfl_up(a.r2, d);
+  return b;
+}
+__device__ __forceinline__ Aff ld_aff(const void* p, int64_t i) {
+  const float4* q = reinterpret_cast<const float4*>(p) + 3 * i;
+  Aff a;
+  a.r0 = q[0];
+  a.r1 = q[1];
+  a.r2 = q[2];
+  return a;
+}
+__device__ __forceinline__ void st_aff(void* p, int64_t i, const Aff& v) {
+  float4* q = reinterpret_cast<float4*>(p) + 3 * i;
+  q[0] = v.r0;
+  q[1] = v.r1;
+  q[2] = v.r2;
+}
+
+// A monoid: value type, identity, combine (earlier operand on the left) and
+// element access in global memory.
+struct MonoidAddI32 {
+  using V = int;
+  __device__ static V identity() { return 0; }
+  __device__ static V combine(V a, V b) { return (int)((unsigned)a + (unsigned)b); }
+  __device__ static V load(const void* p, int64_t i) { return reinterpret_cast<const int*>(p)[i]; }
+  __device__ static void store(void* p, int64_t i, V v) { reinterpret_cast<int*>(p)[i] = v; }
+};
+struct MonoidIsect {
+  using V = float4;
+  __device__ static V identity() { return box_universe(); }
+  __device__ static V combine(V a, V b) { return box_isect(a, b); }
+  __device__ static V load(const void* p, int64_t i) { return reinterpret_cast<const float4*>(p)[i]; }
+  __device__ static void store(void* p, int64_t i, V v) { reinterpret_cast<float4*>(p)[i] = v; }
+};
+struct MonoidUnion {
+  using V = float4;
+  __device__ static V identity() { return box_empty(); }
+  __device__ static V combine(V a, V b) { return box_unite(a, b); }
+  __device__ static V load(const void* p, int64_t i) { return reinterpret_cast<const float4*>(p)[i]; }
+  __device__ static void store(void* p, int64_t i, V v) { reinterpret_cast<float4*>(p)[i] = v; }
+};
+struct MonoidAffine {
+  using V = Aff;
+  __device__ static V identity() { return aff_identity(); }
+  __device__ static V combine(const V& a, const V& b) { return aff_mul(a, b); }
+  __device__ static V load(const void* p, int64_t i) { return ld_aff(p, i); }
+  __device__ static void store(void* p, int64_t i, const V& v) { st_aff(p, i, v); }
+};
+// Entrywise sum of 3x4 matrices (the adjoint's subtree accumulation).
+struct MonoidAffSum {
+  using V = Aff;
+  __device__ static V identity() { return aff_zero(); }
+  __device__ static V combine(const V& a, const V& b) { return aff_add(a, b); }
+  __device__ static V load(const void* p, int64_t i) { return ld_aff(p, i); }
+  __device__ static void store(void* p, int64_t i, const V& v) { st_aff(p, i, v); }
+};
+
+template <class M>
+struct MonoidOp {
+  __device__ typename M::V operator()(const typename M::V& a, const typename M::V& b) const {
+    return M::combine(a, b);
+  }
+};
+
+// Shared-memory slot of joint k of a tile: one padding value per chunk keeps
+// the JC-strided accesses of a warp on distinct banks.
+__host__ __device__ __forceinline__ int jslot(int k) { return k + k / JC; }
+constexpr int JSLOTS = JT + JT / JC;
+
+// ------------------------------------------------------------- workspace
+struct TreeWs {
+  // element level
+  unsigned long long* lb;  // look-back words of k_rank, one per element tile
+  unsigned* counter;       // tile ticket of k_rank
+  unsigned* xcount;        // number of entries in xlist
+  const int* parent_e;     // parent of every element (matching pass)
+  const int* match_e;      // match of every element (matching pass)
+  int* rank_e;             // opens before each element
+  int* nj;                 // opens counted on the device
+  // joint level
+  int* jpos;     // element position of joint r
+  int* jparent;  // parent joint, -1 at a root
+  int* jend;     // one past the last joint of r's subtree
+  // DOWN
+  void* relT;     // fold of a tile-exported joint relative to its tile's base
+  int* t_base;    // per tile: base joint of the exported chain, -1, or NO_CHAIN
+  int* t_link[2];
+  void* t_val[2];
+  void* t_world;  // per tile: fold at the base joint
+  // UP
+  void* cpre;    // per tile: NCH + 1 prefix folds over its chunks
+  void* t_tree;  // segment tree over the tiles' totals, 2 * PJ values
+  int* xlist;    // joints whose subtree leaves their tile
+  int n;         // elements
+  int J;         // joints (opens) announced by the caller
+  int TE;        // element tiles (TILE elements each)
+  int TJ;        // joint tiles (JT joints each)
+  int PJ;        // next power of two >= TJ
+};
+
+// ------------------------------------------------------------- ranks
+// Exclusive count of opens before every element, by a single pass with a
+// decoupled look-back over the element tiles' open counts, and the element
+// position of every joint.
+__global__ void __launch_bounds__(NT) k_rank(const uint8_t* __restrict__ kind, TreeWs w,
+                                             int* status) {
+  __shared__ int s_scr[NW + 1];
+  __shared__ int s_t, s_excl;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_t = (int)atomic_add_u32(w.counter, 1u);
+  __syncthreads();
+  const int t = s_t;
+  const int64_t e0 = (int64_t)t * TILE + (int64_t)tid * KPT;
+  uint8_t kk[KPT];
+  if (e0 + KPT <= w.n) {
+    const uint4 q = ld_nc_u4(kind + e0);
+    const uint32_t wds[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int i = 0; i < KPT; ++i) kk[i] = (uint8_t)(wds[i >> 2] >> (8 * (i & 3)));
+  } else {
+#pragma unroll
+    for (int i = 0; i < KPT; ++i) kk[i] = e0 + i < w.n ? kind[e0 + i] : (uint8_t)K_PAD;
+  }
+  int cnt = 0;
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) cnt += kind_open(kk[i]) ? 1 : 0;
+  int tot;
+  const int ex = block_excl_scan(cnt, 0, OpAdd(), s_scr, &tot);
+  if (tid == 0) {
+    unsigned long long* lb = w.lb;
+    st_release_u64(lb + t, (1ull << 32) | (unsigned)tot);
+    unsigned excl = 0;
+    bool timed_out = false;
+    for (int j = t - 1; j >= 0; --j) {
+      unsigned long long v;
+      unsigned it = 0;
+      for (;;) {
+        v = ld_acquire_u64(lb + j);
+        if ((v >> 32) != 0) break;
+        if (++it >= SPIN_LIMIT) {
+          timed_out = true;
+          break;
+        }
+        poll_backoff(it);
+      }
+      if (timed_out) break;
+      excl += (unsigned)(v & 0xffffffffull);
+      if ((v >> 32) == 2ull) break;
+    }
+    if (timed_out) atomic_cas_i32(status, ST_OK, ST_TIMEOUT);
+    st_release_u64(lb + t, (2ull << 32) | (excl + (unsigned)tot));
+    s_excl = (int)excl;
+    if (t == w.TE - 1) {
+      const int all = (int)(excl + (unsigned)tot);
+      *w.nj = all;
+      if (all != w.J) atomic_cas_i32(status, ST_OK, ST_INVALID);
+    }
+  }
+  __syncthreads();
+  int r = s_excl + ex;
+  int rk[KPT];
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) {
+    rk[i] = r;
+    if (kind_open(kk[i])) {
+      if (r < w.J) w.jpos[r] = (int)(e0 + i);
+      ++r;
+    }
+  }
+  if (e0 + KPT <= w.n) {
+    int4* dst = reinterpret_cast<int4*>(w.rank_e + e0);
+#pragma unroll
+    for (int i = 0; i < KPT / 4; ++i)
+      dst[i] = make_int4(rk[4 * i], rk[4 * i + 1], rk[4 * i + 2], rk[4 * i + 3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+      if (e0 + i < w.n) w.rank_e[e0 + i] = rk[i];
+  }
+}
+
+// Parent joint and subtree end of every joint.  Values that break
+// -1 <= jparent[r] < r < jend[r] <= J (possible only for input the matching
+// pass already rejected, or a wrong joint count) are replaced so that the
+// later passes stay in bounds, and reported.
+__global__ void k_joint(TreeWs w, int* status) {
+  const int J = w.J;
+  bool bad = false;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < J; r += gridDim.x * blockDim.x) {
+    const int e = w.jpos[r];
+    int jp = -1, je = r + 1;
+    if (e >= 0 && e < w.n) {
+      const int p = w.parent_e[e];
+      const int c = w.match_e[e];
+      if (p >= 0 && p < e) jp = w.rank_e[p];
+      else if (p != -1) bad = true;
+      if (c > e && c < w.n) je = w.rank_e[c];
+      else bad = true;
+    } else {
+      bad = true;
+    }
+    if (jp < -1 || jp >= r) {
+      jp = -1;
+      bad = true;
+    }
+    if (je <= r || je > J) {
+      je = r + 1;
+      bad = true;
+    }
+    w.jparent[r] = jp;
+    w.jend[r] = je;
+  }
+  if (bad) atomic_cas_i32(status, ST_OK, ST_INVALID);
+}
+
+// ------------------------------------------------------------- DOWN
+// Per tile: prefix folds of the exported chain relative to its base.
+template <class M>
+__global__ void __launch_bounds__(NT) k_down_chain(TreeWs w, const void* __restrict__ in) {
+  using V = typename M::V;
+  __shared__ V s_scr[NW + 1];
+  __shared__ int s_first;
+  const int t = blockIdx.x, tid = threadIdx.x;
+  const int R0 = t * JT, R1 = R0 + JT;
+  if (tid == 0) s_first = JT;
+  __syncthreads();
+  unsigned xm = 0;
+  V agg = M::identity();
+#pragma unroll
+  for (int i = 0; i < JC; ++i) {
+    const int r = R0 + tid * JC + i;
+    if (r < w.J && w.jend[r] > R1) {
+      xm |= 1u << i;
+      agg = M::combine(agg, M::load(in, r));
+    }
+  }
+  if (xm) atomicMin(&s_first, tid * JC + lowest_set(xm));
+  V tot;
+  V acc = block_excl_scan(agg, M::identity(), MonoidOp<M>(), s_scr, &tot);
+#pragma unroll
+  for (int i = 0; i < JC; ++i) {
+    if (xm & (1u << i)) {
+      const int r = R0 + tid * JC + i;
+      acc = M::combine(acc, M::load(in, r));
+      M::store(w.relT, r, acc);
+    }
+  }
+  if (tid == 0) w.t_base[t] = s_first < JT ? w.jparent[R0 + s_first] : NO_CHAIN;
+}
+
+// Pointer jumping over the tiles (one block): the fold at each tile's base is
+// the fold at its base's tile base times the base's chain prefix.
+template <class M>
+__global__ void __launch_bounds__(1024) k_down_tiles(TreeWs w, int* status) {
+  using V = typename M::V;
+  const int TJ = w.TJ;
+  bool bad = false;
+  for (int t = threadIdx.x; t < TJ; t += blockDim.x) {
+    const int b = w.t_base[t];
+    int l = -1;
+    V v = M::identity();
+    if (b >= 0) {
+      l = b / JT;
+      if (l >= t) {
+        l = -1;
+        bad = true;
+      } else {
+        v = M::load(w.relT, b);
+      }
+    }
+    w.t_link[0][t] = l;
+    M::store(w.t_val[0], t, v);
+    if (l < 0) M::store(w.t_world, t, v);
+  }
+  if (bad) atomic_cas_i32(status, ST_OK, ST_INVALID);
+  int cur = 0;
+  for (int round = 0; round < kMaxJumpRounds; ++round) {
+    __syncthreads();
+    bool any = false;
+    for (int t = threadIdx.x; t < TJ; t += blockDim.x) {
+      const int l = w.t_link[cur][t];
+      V v = M::load(w.t_val[cur], t);
+      int nl = -1;
+      if (l >= 0) {
+        v = M::combine(M::load(w.t_val[cur], l), v);
+        nl = w.t_link[cur][l];
+        if (nl < 0) M::store(w.t_world, t, v);
+        else any = true;
+      }
+      w.t_link[cur ^ 1][t] = nl;
+      M::store(w.t_val[cur ^ 1], t, v);
+    }
+    cur ^= 1;
+    if (!block_or(any)) break;
+  }
+}
+
+template <class M>
+__device__ __forceinline__ typename M::V fold_outside(const TreeWs& w, int a) {
+  return M::combine(M::load(w.t_world, a / JT), M::load(w.relT, a));
+}
+
+template <class M>
+constexpr size_t down_tile_smem() {
+  return (size_t)JSLOTS * sizeof(typename M::V) + (size_t)NCH * sizeof(typename M::V) +
+         (size_t)JT * sizeof(int) + (size_t)NCH * sizeof(int);
+}
+
+template <class M>
+__global__ void __launch_bounds__(NT, 2) k_down_tile(TreeWs w, const void* __restrict__ in,
+                                                     void* __restrict__ out) {
+  using V = typename M::V;
+  TB_DYNAMIC_SMEM(smem);
+  V* s_val = reinterpret_cast<V*>(smem);
+  V* s_cm = s_val + JSLOTS;
+  int* s_anc = reinterpret_cast<int*>(s_cm + NCH);
+  int* s_cl = s_anc + JT;
+  const int t = blockIdx.x, tid = threadIdx.x;
+  const int R0 = t * JT;
+  const int cnt = min(JT, w.J - R0);
+  for (int k = tid; k < cnt; k += NT) {
+    s_val[jslot(k)] = M::load(in, R0 + k);
+    s_anc[k] = w.jparent[R0 + k];
+  }
+  const int c0 = tid * JC;
+  const int cend = R0 + c0 + JC;  // global end of the chunk
+  unsigned xm = 0;
+#pragma unroll
+  for (int i = 0; i < JC; ++i)
+    if (c0 + i < cnt && w.jend[R0 + c0 + i] > cend) xm |= 1u << i;
+  __syncthreads();
+
+  // In-chunk walk: fold relative to the nearest ancestor outside the chunk.
+#pragma unroll
+  for (int i = 0; i < JC; ++i) {
+    const int k = c0 + i;
+    if (k < cnt) {
+      const int p = s_anc[k];
+      if (p >= R0 + c0) {
+        s_val[jslot(k)] = M::combine(s_val[jslot(p - R0)], s_val[jslot(k)]);
+        s_anc[k] = s_anc[p - R0];
+      }
+    }
+  }
+  __syncthreads();
+
+  // Chunk level: the exported joints of a chunk hang below one base joint,
+  // the nearest outside ancestor of the first of them.
+  int link = -1;
+  V m = M::identity();
+  if (xm) {
+    const int a = s_anc[c0 + lowest_set(xm)];
+    if (a >= R0) {
+      link = (a - R0) / JC;
+      m = s_val[jslot(a - R0)];
+    } else if (a >= 0) {
+      m = fold_outside<M>(w, a);
+    }
+  }
+  s_cm[tid] = m;
+  s_cl[tid] = link;
+  for (int round = 0; round < kMaxJumpRounds; ++round) {
+    if (!block_or(link >= 0)) break;
+    int nl = -1;
+    V nm = m;
+    if (link >= 0) {
+      nm = M::combine(s_cm[link], m);
+      nl = s_cl[link];
+    }
+    __syncthreads();
+    link = nl;
+    m = nm;
+    s_cm[tid] = m;
+    s_cl[tid] = link;
+  }
+  // Exported joints: base fold times the relative fold.
+#pragma unroll
+  for (int i = 0; i < JC; ++i)
+    if (xm & (1u << i)) s_val[jslot(c0 + i)] = M::combine(m, s_val[jslot(c0 + i)]);
+  __syncthreads();
+  // Every other joint: its outside ancestor is an exported joint of an
+  // earlier chunk of this tile (final by now), a joint of an earlier tile, or
+  // none.
+  int last_a = -1;
+  V last_f = M::identity();
+#pragma unroll
+  for (int i = 0; i < JC; ++i) {
+    const int k = c0 + i;
+    if (k < cnt && !(xm & (1u << i))) {
+      const int a = s_anc[k];
+      if (a >= R0) {
+        s_val[jslot(k)] = M::combine(s_val[jslot(a - R0)], s_val[jslot(k)]);
+      } else if (a >= 0) {
+        if (a != last_a) {
+          last_f = fold_outside<M>(w, a);
+          last_a = a;
+        }
+        s_val[jslot(k)] = M::combine(last_f, s_val[jslot(k)]);
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = tid; k < cnt; k += NT) M::store(out, R0 + k, s_val[jslot(k)]);
+}
+
+// ------------------------------------------------------------- UP
+// Fold of leaves l..r (inclusive) of a segment tree with P leaves; node(i)
+// returns node i.
+template <class M, class Node>
+__device__ __forceinline__ typename M::V seg_fold(Node node, int P, int l, int r) {
+  using V = typename M::V;
+  V left = M::identity(), right = M::identity();
+  if (l > r) return left;
+  for (l += P, r += P + 1; l < r; l >>= 1, r >>= 1) {
+    if (l & 1) left = M::combine(left, node(l++));
+    if (r & 1) right = M::combine(node(--r), right);
+  }
+  return M::combine(left, right);
+}
+
+// Values of the UP pass: the caller's input, or the adjoint's
+// X_r = W_r (x) world_r^T = [W^R R^T + W^t t^T | W^t].
+template <class M>
+struct InputValues {
+  const void* in;
+  __device__ typename M::V operator()(int r) const { return M::load(in, r); }
+};
+struct AdjointValues {
+  const void* grad_world;
+  const void* world;
+  __device__ static float4 row(float4 g, const Aff& W) {
+    float4 x;
+    x.x = fmaf(g.x, W.r0.x, fmaf(g.y, W.r0.y, fmaf(g.z, W.r0.z, g.w * W.r0.w)));
+    x.y = fmaf(g.x, W.r1.x, fmaf(g.y, W.r1.y, fmaf(g.z, W.r1.z, g.w * W.r1.w)));
+    x.z = fmaf(g.x, W.r2.x, fmaf(g.y, W.r2.y, fmaf(g.z, W.r2.z, g.w * W.r2.w)));
+    x.w = g.w;
+    return x;
+  }
+  __device__ Aff operator()(int r) const {
+    const Aff G = ld_aff(grad_world, r);
+    const Aff W = ld_aff(world, r);
+    Aff X;
+    X.r0 = row(G.r0, W);
+    X.r1 = row(G.r1, W);
+    X.r2 = row(G.r2, W);
+    return X;
+  }
+};
+
+template <class M>
+constexpr size_t up_tile_smem() {
+  return (size_t)JSLOTS * sizeof(typename M::V) + (size_t)2 * NCH * sizeof(typename M::V) +
+         (size_t)(NW + 1) * sizeof(typename M::V) + (size_t)JT * sizeof(int);
+}
+
+template <class M, class Values>
+__global__ void __launch_bounds__(NT, 2) k_up_tile(TreeWs w, Values values, void* __restrict__ out) {
+  using V = typename M::V;
+  TB_DYNAMIC_SMEM(smem);
+  V* s_val = reinterpret_cast<V*>(smem);
+  V* s_tree = s_val + JSLOTS;  // chunk totals at [NCH, 2 NCH)
+  V* s_scr = s_tree + 2 * NCH;
+  int* s_end = reinterpret_cast<int*>(s_scr + NW + 1);  // local subtree ends
+  const int t = blockIdx.x, tid = threadIdx.x;
+  const int R0 = t * JT;
+  const int cnt = min(JT, w.J - R0);
+  for (int k = tid; k < cnt; k += NT) {
+    s_val[jslot(k)] = values(R0 + k);
+    s_end[k] = w.jend[R0 + k] - R0;
+  }
+  __syncthreads();
+  const int c0 = tid * JC, ce = c0 + JC;
+  const int lim = min(ce, cnt);
+  // Walk the chunk backwards: a joint's fold is its own value followed by its
+  // children's folds; a child leaving the chunk contributes its suffix.
+  for (int k = lim - 1; k >= c0; --k) {
+    V acc = s_val[jslot(k)];
+    const int stop = min(s_end[k], ce);
+    for (int c = k + 1; c < stop; c = s_end[c]) acc = M::combine(acc, s_val[jslot(c)]);
+    s_val[jslot(k)] = acc;
+  }
+  V tot = M::identity();
+  for (int c = c0; c < lim; c = s_end[c]) tot = M::combine(tot, s_val[jslot(c)]);
+  s_tree[NCH + tid] = tot;
+  __syncthreads();
+  for (int h = NCH / 2; h >= 1; h >>= 1) {
+    if (tid < h) s_tree[h + tid] = M::combine(s_tree[2 * (h + tid)], s_tree[2 * (h + tid) + 1]);
+    __syncthreads();
+  }
+  // Joints whose subtree leaves the chunk.
+  auto node = [s_tree](int i) { return s_tree[i]; };
+  for (int k = c0; k < lim; ++k) {
+    const int e = s_end[k];
+    if (e <= ce) continue;
+    V acc = s_val[jslot(k)];
+    if (e <= JT) {
+      const int c2 = e / JC;
+      acc = M::combine(acc, seg_fold<M>(node, NCH, tid + 1, c2 - 1));
+      for (int j = c2 * JC; j < e; j = s_end[j]) acc = M::combine(acc, s_val[jslot(j)]);
+    } else {
+      acc = M::combine(acc, seg_fold<M>(node, NCH, tid + 1, NCH - 1));
+      const unsigned at = atomic_add_u32(w.xcount, 1u);
+      w.xlist[at] = R0 + k;
+    }
+    s_val[jslot(k)] = acc;
+  }
+  // Prefix folds over the chunks, for subtrees of earlier tiles ending here.
+  V all;
+  const V pre = block_excl_scan(tot, M::identity(), MonoidOp<M>(), s_scr, &all);
+  M::store(w.cpre, (int64_t)t * (NCH + 1) + tid, pre);
+  if (tid == 0) M::store(w.cpre, (int64_t)t * (NCH + 1) + NCH, all);
+  for (int k = tid; k < cnt; k += NT) M::store(out, R0 + k, s_val[jslot(k)]);
+}
+
+// Segment tree over the tiles' totals (one block).
+template <class M>
+__global__ void __launch_bounds__(1024) k_up_tiles(TreeWs w) {
+  using V = typename M::V;
+  const int P = w.PJ;
+  for (int t = threadIdx.x; t < P; t += blockDim.x)
+    M::store(w.t_tree, P + t,
+             t < w.TJ ? M::load(w.cpre, (int64_t)t * (NCH + 1) + NCH) : M::identity());
+  for (int h = P / 2; h >= 1; h >>= 1) {
+    __syncthreads();
+    for (int i = h + threadIdx.x; i < 2 * h; i += blockDim.x) {
+      const V v = M::combine(M::load(w.t_tree, 2 * i), M::load(w.t_tree, 2 * i + 1));
+      M::store(w.t_tree, i, v);
+    }
+  }
+}
+
+// Completes the folds of the subtrees that leave their tile: the partial fold
+// written by k_up_tile, the whole tiles in between, and the prefix of the
+// tile where the subtree ends.
+template <class M>
+__global__ void k_up_cross(TreeWs w, void* __restrict__ out) {
+  using V = typename M::V;
+  const int count = (int)*w.xcount;
+  const void* tree = w.t_tree;
+  auto node = [tree](int i) { return M::load(tree, i); };
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const int r = w.xlist[i];
+    const int t = r / JT;
+    const int e = w.jend[r];
+    const int t2 = e / JT;
+    V acc = M::load(out, r);
+    acc = M::combine(acc, seg_fold<M>(node, w.PJ, t + 1, t2 - 1));
+    const int R2 = t2 * JT;
+    if (e > R2) {
+      const int c2 = (e - R2) / JC;
+      acc = M::combine(acc, M::load(w.cpre, (int64_t)t2 * (NCH + 1) + c2));
+      for (int j = R2 + c2 * JC; j < e; j = w.jend[j]) acc = M::combine(acc, M::load(out, j));
+    }
+    M::store(out, r, acc);
+  }
+}
+
+// ------------------------------------------------------------- adjoint
+// Inverse of the 3x3 part (adjugate over determinant).
+__device__ __forceinline__ void inv3(const Aff& a, float m[3][3]) {
+  const float a00 = a.r0.x, a01 = a.r0.y, a02 = a.r0.z;
+  const float a10 = a.r1.x, a11 = a.r1.y, a12 = a.r1.z;
+  const float a20 = a.r2.x, a21 = a.r2.y, a22 = a.r2.z;
+  const float c00 = a11 * a22 - a12 * a21, c01 = a12 * a20 - a10 * a22, c02 = a10 * a21 - a11 * a20;
+  const float id = 1.0f / (a00 * c00 + a01 * c01 + a02 * c02);
+  m[0][0] = c00 * id;
+  m[1][0] = c01 * id;
+  m[2][0] = c02 * id;
+  m[0][1] = (a02 * a21 - a01 * a22) * id;
+  m[1][1] = (a00 * a22 - a02 * a20) * id;
+  m[2][1] = (a01 * a20 - a00 * a21) * id;
+  m[0][2] = (a01 * a12 - a02 * a11) * id;
+  m[1][2] = (a02 * a10 - a00 * a12) * id;
+  m[2][2] = (a00 * a11 - a01 * a10) * id;
+}
+
+// Gbar_r = A_r world_r^{-T} = [(A^R - A^t t^T) R^{-T} | A^t] and
+// dL_r = R_parent^T Gbar_r (Gbar_r itself at a root).
+__global__ void k_bwd_final(TreeWs w, const void* __restrict__ acc, const void* __restrict__ world,
+                            void* __restrict__ grad_local) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < w.J; r += gridDim.x * blockDim.x) {
+    const Aff A = ld_aff(acc, r);
+    const Aff Wr = ld_aff(world, r);
+    float inv[3][3];
+    inv3(Wr, inv);
+    const float tx = Wr.r0.w, ty = Wr.r1.w, tz = Wr.r2.w;
+    const float4 arow[3] = {A.r0, A.r1, A.r2};
+    float4 g[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float4 a = arow[i];
+      const float b0 = a.x - a.w * tx, b1 = a.y - a.w * ty, b2 = a.z - a.w * tz;
+      g[i].x = fmaf(b0, inv[0][0], fmaf(b1, inv[0][1], b2 * inv[0][2]));
+      g[i].y = fmaf(b0, inv[1][0], fmaf(b1, inv[1][1], b2 * inv[1][2]));
+      g[i].z = fmaf(b0, inv[2][0], fmaf(b1, inv[2][1], b2 * inv[2][2]));
+      g[i].w = a.w;
+    }
+    Aff D;
+    const int p = w.jparent[r];
+    if (p >= 0) {
+      const Aff P = ld_aff(world, p);
+      // D = R_p^T Gbar: row i of D is sum_k R_p[k][i] * row k of Gbar.
+      const float q[3][3] = {{P.r0.x, P.r1.x, P.r2.x}, {P.r0.y, P.r1.y, P.r2.y}, {P.r0.z, P.r1.z, P.r2.z}};
+      float4 d[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        d[i].x = fmaf(q[i][0], g[0].x, fmaf(q[i][1], g[1].x, q[i][2] * g[2].x));
+        d[i].y = fmaf(q[i][0], g[0].y, fmaf(q[i][1], g[1].y, q[i][2] * g[2].y));
+        d[i].z = fmaf(q[i][0], g[0].z, fmaf(q[i][1], g[1].z, q[i][2] * g[2].z));
+        d[i].w = fmaf(q[i][0], g[0].w, fmaf(q[i][1], g[1].w, q[i][2] * g[2].w));
+      }
+      D.r0 = d[0];
+      D.r1 = d[1];
+      D.r2 = d[2];
+    } else {
+      D.r0 = g[0];
+      D.r1 = g[1];
+      D.r2 = g[2];
+    }
+    st_aff(grad_local, r, D);
+  }
+}
+
+}  // namespace tb
+
+#endif  // TB_TREE_KERNELS_CUH

@@ -30,7 +30,8 @@ def lib():
 def test_header_declares_entry_points():
     names = declared_functions()
     for n in ("tb_workspace_size", "tb_match_parens", "tb_bboxes", "tb_bboxes_batched",
-              "tb_set_phase_events", "tb_version"):
+              "tb_tree_scan", "tb_tree_scan_affine_backward", "tb_set_phase_events",
+              "tb_version"):
         assert n in names
 
 
@@ -51,6 +52,13 @@ def test_workspace_size(lib):
     assert b.tb_workspace_size(b.TB_OP_BBOXES_BATCHED, 1 << 20, 7) == s2
     # workspace grows linearly in the number of tiles
     assert b.tb_workspace_size(b.TB_OP_BBOXES, 1 << 22) < 4.5 * s2
+    t2 = b.tb_workspace_size(b.TB_OP_TREE_SCAN, 1 << 20)
+    g2 = b.tb_workspace_size(b.TB_OP_TREE_BACKWARD, 1 << 20)
+    assert m2 < t2 < g2
+    # the adjoint adds two transforms per joint (at most n / 2 joints)
+    assert g2 - t2 >= 2 * 48 * (1 << 19)
+    assert b.tb_workspace_size(b.TB_OP_TREE_SCAN, 0) == 0
+    assert b.tb_workspace_size(99, 1 << 20) == 0
 
 
 def test_argument_errors_before_any_launch(lib):
@@ -72,4 +80,45 @@ def test_argument_errors_before_any_launch(lib):
                                  1 << 30, p(fake), None) == b.TB_ERR_INVALID_ARG
     assert lib.tb_bboxes(p(fake), p(fake), 1 << 31, None, None, p(fake), p(fake), 1 << 40, p(fake),
                          None) == b.TB_ERR_INVALID_ARG
+    assert lib.tb_set_phase_events(None, 0) == b.TB_OK
+
+
+def test_tree_scan_argument_errors(lib):
+    from paper_2205_11659_gb300 import binding as b
+    p = ctypes.c_void_p
+    fake, big = 1 << 20, 1 << 40
+    out = fake + (1 << 12)
+
+    def scan(monoid=b.TB_MONOID_ADD_I32, d=b.TB_DOWN, kind=fake, n=10, J=5, vin=fake, vout=out,
+             ws=fake, nb=big):
+        return lib.tb_tree_scan(monoid, d, p(kind), n, J, p(vin), p(vout), p(ws), nb, p(fake), None)
+
+    assert scan(monoid=4) == b.TB_ERR_INVALID_ARG
+    assert scan(monoid=-1) == b.TB_ERR_INVALID_ARG
+    assert scan(d=2) == b.TB_ERR_INVALID_ARG
+    assert scan(J=6) == b.TB_ERR_INVALID_ARG          # more joints than n / 2
+    assert scan(J=-1) == b.TB_ERR_INVALID_ARG
+    assert scan(n=-1, J=0) == b.TB_ERR_INVALID_ARG
+    assert scan(vout=fake) == b.TB_ERR_INVALID_ARG    # in and out alias
+    assert scan(vin=fake + 4) == b.TB_ERR_INVALID_ARG  # misaligned values
+    assert scan(kind=fake + 1) == b.TB_ERR_INVALID_ARG
+    assert scan(nb=16) == b.TB_ERR_WORKSPACE
+    assert lib.tb_tree_scan(0, 0, p(fake), 10, 5, p(fake), p(out), p(fake), big, None, None) \
+        == b.TB_ERR_INVALID_ARG                         # no status word
+
+    def bwd(J=5, local=fake, g=fake + 4096, gl=fake + 8192, nb=big):
+        return lib.tb_tree_scan_affine_backward(p(fake), 10, J, p(local), p(g), p(gl), p(fake), nb,
+                                                p(fake), None)
+
+    assert bwd(J=6) == b.TB_ERR_INVALID_ARG
+    assert bwd(gl=fake) == b.TB_ERR_INVALID_ARG
+    assert bwd(local=fake + 8) == b.TB_ERR_INVALID_ARG
+    assert bwd(nb=1 << 10) == b.TB_ERR_WORKSPACE
+
+
+def test_phase_event_count_limits(lib):
+    from paper_2205_11659_gb300 import binding as b
+    arr = (ctypes.c_void_p * 17)(*([1 << 20] * 17))
+    assert lib.tb_set_phase_events(arr, 17) == b.TB_ERR_INVALID_ARG
+    assert lib.tb_set_phase_events(arr, 0) == b.TB_ERR_INVALID_ARG
     assert lib.tb_set_phase_events(None, 0) == b.TB_OK
