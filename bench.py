@@ -315,7 +315,7 @@ def run_tree(args, torch, world, rank, dev):
         assert int(binding.workspace(dev).status.item()) == binding.TB_OK
 
     K = args.steps
-    nf, nbk = 11, 15
+    nf, nbk = 7, 10
     ev_f = [[torch.cuda.Event(enable_timing=True) for _ in range(nf)] for _ in range(K)]
     ev_b = [[torch.cuda.Event(enable_timing=True) for _ in range(nbk)] for _ in range(K)]
     for evs in ev_f + ev_b:
@@ -351,9 +351,8 @@ def run_tree(args, torch, world, rank, dev):
     value = world * n / (ms_step * 1e-3) / 1e9
 
     # per-kernel times of the plain calls (event pairs in launch order)
-    fnames = ["k1", "k2", "k3", "k4", "memset", "rank", "joint", "down_chain", "down_tiles",
-              "down_tile"]
-    bnames = fnames + ["up_tile", "up_tiles", "up_cross", "bwd_final"]
+    fnames = ["depth", "minmax", "min_tree", "jstruct_chain", "down_tiles", "down_tile"]
+    bnames = fnames + ["up_tile", "up_tiles", "up_cross"]
     if graph is not None:
         for i in range(K):
             binding.tb_set_phase_events(ev_f[i])
@@ -463,7 +462,7 @@ def run_tree(args, torch, world, rank, dev):
             "e2e": {"value": round(world * n / e2e_s / 1e9, 3), "unit": "Gelem/s",
                     "h2d_bytes_per_step": int(kind.nbytes + L.nbytes + W.nbytes),
                     "d2h_bytes_per_step": int(2 * L.nbytes)},
-            "gpu_launches": (9 + 13) * K,
+            "gpu_launches": (6 + 9) * K,
             "clocks": clk,
             "kernel_hash": kernel_hash(),
         }
@@ -553,6 +552,48 @@ def run_ours(args):
               for j, nm in enumerate(names)}
     value = world * n / (ms_step * 1e-3) / 1e9
 
+    # ---- batched: the same scenes as separate plain calls, same outputs
+    per_scene = None
+    if offsets is not None:
+        parent2 = torch.empty_like(parent)
+        match2 = torch.empty_like(match)
+        box2 = torch.empty_like(box_out)
+        calls = []
+        for sidx in range(S):
+            e0, e1 = int(offsets[sidx]), int(offsets[sidx + 1])
+            if e1 > e0:
+                # kind needs 16-byte alignment: a copy per scene; the other
+                # buffers are 16-byte aligned views
+                calls.append((k_d[e0:e1].clone(), b_d[e0:e1], e1 - e0, parent2[e0:e1],
+                              match2[e0:e1], box2[e0:e1]))
+        nb1 = binding.tb_workspace_size(binding.TB_OP_BBOXES, max(c[2] for c in calls))
+
+        def per_scene_step():
+            for kk, bb, ns, pp, mm, oo in calls:
+                rc = binding.tb_bboxes(kk, bb, ns, pp, mm, oo, ws, nb1, status, stream)
+                if rc != binding.TB_OK:
+                    raise binding.TBError(rc, "per-scene step")
+        per_scene_step()
+        torch.cuda.synchronize()
+        assert int(status.item()) == binding.TB_OK
+        same = (torch.equal(parent, parent2) and torch.equal(match, match2) and
+                torch.equal(box_out.view(torch.int32), box2.view(torch.int32)))
+        reps = max(2, min(K, 5))
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(reps):
+            per_scene_step()
+        p1.record(stream)
+        torch.cuda.synchronize()
+        ps_ms = p0.elapsed_time(p1) / reps
+        per_scene = {"value": round(n / (ps_ms * 1e-3) / 1e9, 3), "unit": "Gelem/s",
+                     "ms_per_step": round(ps_ms, 4),
+                     "launches": "%d plain tb_bboxes calls on one stream" % len(calls),
+                     "outputs_identical": bool(same),
+                     "batched_over_per_scene": round(ps_ms / ms_step, 2)}
+        del parent2, match2, box2, calls
+
     # ---- end to end through the public API with host buffers
     kind_h = torch.from_numpy(kind).pin_memory()
     box_h = torch.from_numpy(box).pin_memory()
@@ -606,6 +647,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": BYTES_PER_ELEM * n},
             "step_roofline_frac": round(BYTES_PER_ELEM * n / (ms_step * 1e-3) / 1e9 / peak, 4),
             "phases_ms": {k: round(v, 4) for k, v in phases.items()},
+            "per_scene": per_scene,
             "cpu_baseline": cpu,
             "e2e": {"value": round(world * n / e2e_s / 1e9, 3), "unit": "Gelem/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},

@@ -282,14 +282,6 @@ const char* tb_version(void) { return "treebox-gb300 0.1 (sm_103a)"; }
 
 namespace tb_internal {
 
-size_t match_ws_bytes(int64_t n) { return n > 0 && n <= kMaxN ? scene_layout(n, false).total : 0; }
-
-tb_status run_match(const uint8_t* kind, int64_t n, int32_t* parent, int32_t* match, void* ws,
-                    size_t ws_bytes, int32_t* d_status, cudaStream_t s) {
-  return run_scene<false>(kind, nullptr, n, parent, match, nullptr, nullptr, 0, ws, ws_bytes,
-                          d_status, s, -1);
-}
-
 void phase_reset() { g_phase_next = 0; }
 void phase_mark(cudaStream_t s) { ::phase_mark(s); }
 

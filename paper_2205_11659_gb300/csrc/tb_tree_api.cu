@@ -24,11 +24,11 @@ constexpr int next_pow2(int x) {
   return p;
 }
 
-// The matching pass's scratch comes first; the three counters that must
-// start at zero are adjacent so one memset clears them.
+// The three counters that must start at zero are adjacent so one memset
+// clears them.
 struct TreeLayout {
-  size_t lb, counter, xcount, zero_end, nj, parent_e, match_e, rank_e, jpos, jparent, jend, relT,
-      t_base, t_link0, t_link1, t_val0, t_val1, t_world, cpre, t_tree, xlist, world, acc, total;
+  size_t lb, counter, xcount, zero_end, jdepth, premin, sufmin, jparent, jend, g_tree, relT, t_base,
+      t_link0, t_link1, t_val0, t_val1, t_world, cpre, t_tree, xlist, world, acc, total;
   int TE, TJ, PJ, Jmax;
 };
 
@@ -42,13 +42,13 @@ TreeLayout tree_layout(int64_t n, bool backward) {
   L.TJ = TJ;
   L.PJ = PJ;
   L.Jmax = Jmax;
-  size_t o = align_up(tb_internal::match_ws_bytes(n));
+  size_t o = 0;
   auto take = [&o](size_t bytes) {
     const size_t at = o;
     o = align_up(o + bytes);
     return at;
   };
-  L.lb = o;
+  L.lb = 0;
   o += (size_t)TE * 8;
   L.counter = o;
   o += 4;
@@ -57,13 +57,12 @@ TreeLayout tree_layout(int64_t n, bool backward) {
   L.zero_end = o;
   o = align_up(o);
   const size_t J4 = (size_t)Jmax * 4, JV = (size_t)Jmax * kValBytes;
-  L.nj = take(16);
-  L.parent_e = take((size_t)n * 4);
-  L.match_e = take((size_t)n * 4);
-  L.rank_e = take((size_t)n * 4);
-  L.jpos = take(J4);
+  L.jdepth = take(J4);
+  L.premin = take(J4);
+  L.sufmin = take(J4);
   L.jparent = take(J4);
   L.jend = take(J4);
+  L.g_tree = take((size_t)2 * PJ * 4);
   L.relT = take(JV);
   L.t_base = take((size_t)TJ * 4);
   L.t_link0 = take((size_t)TJ * 4);
@@ -88,13 +87,12 @@ TreeWs tree_ws(const TreeLayout& L, void* ws, int64_t n, int J) {
   w.lb = reinterpret_cast<unsigned long long*>(b + L.lb);
   w.counter = reinterpret_cast<unsigned*>(b + L.counter);
   w.xcount = reinterpret_cast<unsigned*>(b + L.xcount);
-  w.parent_e = reinterpret_cast<const int*>(b + L.parent_e);
-  w.match_e = reinterpret_cast<const int*>(b + L.match_e);
-  w.rank_e = reinterpret_cast<int*>(b + L.rank_e);
-  w.nj = reinterpret_cast<int*>(b + L.nj);
-  w.jpos = reinterpret_cast<int*>(b + L.jpos);
+  w.jdepth = reinterpret_cast<int*>(b + L.jdepth);
+  w.premin = reinterpret_cast<int*>(b + L.premin);
+  w.sufmin = reinterpret_cast<int*>(b + L.sufmin);
   w.jparent = reinterpret_cast<int*>(b + L.jparent);
   w.jend = reinterpret_cast<int*>(b + L.jend);
+  w.g_tree = reinterpret_cast<int*>(b + L.g_tree);
   w.relT = b + L.relT;
   w.t_base = reinterpret_cast<int*>(b + L.t_base);
   w.t_link[0] = reinterpret_cast<int*>(b + L.t_link0);
@@ -125,34 +123,39 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-// Matching pass, ranks and the joint tree.  Returns the workspace view.
+// Status word, joint depths with the stream checks, tile minima.
 tb_status prelude(const uint8_t* kind, int64_t n, int J, const TreeLayout& L, void* ws,
-                  size_t ws_bytes, int32_t* d_status, cudaStream_t s, TreeWs* out) {
+                  int32_t* d_status, cudaStream_t s, TreeWs* out) {
   unsigned char* b = static_cast<unsigned char*>(ws);
-  TreeWs w = tree_ws(L, ws, n, J);
-  tb_status st = tb_internal::run_match(kind, n, reinterpret_cast<int32_t*>(b + L.parent_e),
-                                        reinterpret_cast<int32_t*>(b + L.match_e), ws,
-                                        L.lb, d_status, s);
-  if (st != TB_OK) return st;
-  (void)ws_bytes;
+  const TreeWs w = tree_ws(L, ws, n, J);
+  if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return TB_ERR_CUDA;
   if (cudaMemsetAsync(b + L.lb, 0, L.zero_end - L.lb, s) != cudaSuccess) return TB_ERR_CUDA;
   tb_internal::phase_mark(s);
-  k_rank<<<L.TE, NT, 0, s>>>(kind, w, d_status);
+  k_tdepth<<<L.TE, NT, 0, s>>>(kind, w, d_status);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
-  tb_internal::phase_mark(s);
   if (J > 0) {
-    k_joint<<<grid_for(J, 256), 256, 0, s>>>(w, d_status);
+    tb_internal::phase_mark(s);
+    k_jminmax<<<w.TJ, NT, 0, s>>>(w);
+    if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
+    tb_internal::phase_mark(s);
+    k_jmin_tree<<<1, 1024, 0, s>>>(w);
     if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   }
   *out = w;
   return TB_OK;
 }
 
+template <class M, bool CHAIN>
+tb_status launch_jstruct(const TreeWs& w, const void* in, cudaStream_t s) {
+  tb_internal::phase_mark(s);
+  k_jstruct<M, CHAIN><<<w.TJ, NT, 0, s>>>(w, in);
+  return cudaGetLastError() == cudaSuccess ? TB_OK : TB_ERR_CUDA;
+}
+
 template <class M>
 tb_status launch_down(const TreeWs& w, const void* in, void* out, int32_t* d_status, cudaStream_t s) {
-  tb_internal::phase_mark(s);
-  k_down_chain<M><<<w.TJ, NT, 0, s>>>(w, in);
-  if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
+  tb_status st = launch_jstruct<M, true>(w, in, s);
+  if (st != TB_OK) return st;
   tb_internal::phase_mark(s);
   k_down_tiles<M><<<1, 1024, 0, s>>>(w, d_status);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
@@ -168,22 +171,22 @@ tb_status launch_down(const TreeWs& w, const void* in, void* out, int32_t* d_sta
   return TB_OK;
 }
 
-template <class M, class Values>
-tb_status launch_up(const TreeWs& w, Values values, void* out, cudaStream_t s) {
+template <class M, class Values, class Finish>
+tb_status launch_up(const TreeWs& w, Values values, void* out, Finish fin, cudaStream_t s) {
   tb_internal::phase_mark(s);
   constexpr size_t smem = up_tile_smem<M>();
   static bool attr_set = false;
   if (!attr_set) {
-    if (allow_smem(k_up_tile<M, Values>, smem) != cudaSuccess) return TB_ERR_CUDA;
+    if (allow_smem(k_up_tile<M, Values, Finish>, smem) != cudaSuccess) return TB_ERR_CUDA;
     attr_set = true;
   }
-  k_up_tile<M, Values><<<w.TJ, NT, smem, s>>>(w, values, out);
+  k_up_tile<M, Values, Finish><<<w.TJ, NT, smem, s>>>(w, values, out, fin);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   tb_internal::phase_mark(s);
   k_up_tiles<M><<<1, 1024, 0, s>>>(w);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   tb_internal::phase_mark(s);
-  k_up_cross<M><<<grid_for(w.TJ * 64, 256), 256, 0, s>>>(w, out);
+  k_up_cross<M, Finish><<<grid_for(w.TJ * 64, 256), 256, 0, s>>>(w, out, fin);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   return TB_OK;
 }
@@ -192,7 +195,9 @@ template <class M>
 tb_status scan_dir(int dir, const TreeWs& w, const void* in, void* out, int32_t* d_status,
                    cudaStream_t s) {
   if (dir == TB_DOWN) return launch_down<M>(w, in, out, d_status, s);
-  return launch_up<M>(w, InputValues<M>{in}, out, s);
+  tb_status st = launch_jstruct<M, false>(w, nullptr, s);
+  if (st != TB_OK) return st;
+  return launch_up<M>(w, InputValues<M>{in}, out, NoFinish{}, s);
 }
 
 tb_status check_common(const uint8_t* kind, int64_t n, int64_t num_joints, void* ws,
@@ -232,7 +237,7 @@ tb_status tb_tree_scan(int monoid, int dir, const uint8_t* kind, int64_t n, int6
   if (n > 0 && ws_bytes < L.total) return TB_ERR_WORKSPACE;
   if (n == 0) return cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) == cudaSuccess ? TB_OK : TB_ERR_CUDA;
   TreeWs w;
-  st = prelude(kind, n, (int)num_joints, L, ws, ws_bytes, d_status, s, &w);
+  st = prelude(kind, n, (int)num_joints, L, ws, d_status, s, &w);
   if (st != TB_OK || num_joints == 0) {
     if (st == TB_OK) tb_internal::phase_mark(s);
     return st;
@@ -273,7 +278,7 @@ tb_status tb_tree_scan_affine_backward(const uint8_t* kind, int64_t n, int64_t n
   if (n > 0 && ws_bytes < L.total) return TB_ERR_WORKSPACE;
   if (n == 0) return cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) == cudaSuccess ? TB_OK : TB_ERR_CUDA;
   TreeWs w;
-  st = prelude(kind, n, (int)num_joints, L, ws, ws_bytes, d_status, s, &w);
+  st = prelude(kind, n, (int)num_joints, L, ws, d_status, s, &w);
   if (st != TB_OK || num_joints == 0) {
     if (st == TB_OK) tb_internal::phase_mark(s);
     return st;
@@ -283,11 +288,9 @@ tb_status tb_tree_scan_affine_backward(const uint8_t* kind, int64_t n, int64_t n
   void* acc = b + L.acc;
   st = launch_down<MonoidAffine>(w, local, world, d_status, s);
   if (st != TB_OK) return st;
-  st = launch_up<MonoidAffSum>(w, AdjointValues{grad_world, world}, acc, s);
+  st = launch_up<MonoidAffSum>(w, AdjointValues{grad_world, world}, acc,
+                               AdjointFinish{world, grad_local}, s);
   if (st != TB_OK) return st;
-  tb_internal::phase_mark(s);
-  k_bwd_final<<<grid_for(w.J, 256), 256, 0, s>>>(w, acc, world, grad_local);
-  if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   tb_internal::phase_mark(s);
   return TB_OK;
 }

@@ -3,11 +3,26 @@
 // adjoint of the 3x4 affine root-path product.
 //
 // Values live on the opens ("joints"), joint r being the r-th open of the
-// stream (pre-order).  Given the parent and match of every element from the
-// matching pass, the joint tree is described by
-//   jparent[r]  parent joint (-1 at a root), always < r
-//   jend[r]     one past the last joint of r's subtree, so the subtree of r
+// stream (pre-order).  The joint tree is described by
+//   jdepth[r]   depth of joint r (1 at a root)
+//   jparent[r]  parent joint (-1 at a root): the last joint before r that is
+//               shallower than r, since everything between a parent and its
+//               child lies in the parent's subtree
+//   jend[r]     one past the last joint of r's subtree: the first joint after
+//               r that is not deeper than r (J if none), so the subtree of r
 //               is the contiguous range [r, jend[r]) (Sec. 6.2)
+// Both are nearest-smaller-value searches over jdepth, done with the up/down
+// search of a min tree (Sec. 5, Fig. "core"): inside a tile of joints over a
+// tree in shared memory, across tiles over a tree of tile minima and the
+// tile's monotone prefix / suffix minima.
+//
+//   k_tdepth     one pass over the kinds with a decoupled look-back over the
+//                element tiles' open and close counts: depth of every joint,
+//                balance and kind checks
+//   k_jminmax    per joint tile: prefix and suffix minima of jdepth, tile min
+//   k_jmin_tree  min tree over the tiles (one block)
+//   k_jstruct    per joint tile: jparent and jend; for a DOWN scan also the
+//                prefix folds of the tile's exported chain (below)
 //
 // Joints are processed in tiles of JT = 1024 consecutive joints, one block of
 // NT threads each; thread c owns the chunk of JC = 4 joints [c*JC, c*JC+JC).
@@ -17,8 +32,8 @@
 //     "exported" from it.  The exported joints of a chunk or tile form one
 //     parent-child chain, and every other joint's nearest ancestor outside
 //     its chunk is an exported joint of an earlier chunk.
-//   * k_down_chain: per tile, the prefix fold of its exported chain relative
-//     to the chain's base (the parent of its first link), and that base.
+//   * k_jstruct<CHAIN>: per tile, the prefix fold of its exported chain
+//     relative to the chain's base (the parent of its first link).
 //   * k_down_tiles: pointer jumping over tiles (each tile links to the tile
 //     of its base) gives the fold at every tile's base.
 //   * k_down_tile: in-chunk walk relative to each joint's nearest outside
@@ -33,8 +48,8 @@
 //   * k_up_cross: completes the folds of subtrees that leave their tile.
 //
 // Affine adjoint (loss = sum_r <W_r, world_r>): world by DOWN, then
-// A_r = sum over the subtree of W_d (x) world_d^T by UP, then
-// Gbar_r = A_r world_r^{-T} and dL_r = R_parent^T Gbar_r (k_bwd_final).
+// A_r = sum over the subtree of W_d (x) world_d^T by UP, and in the same
+// kernels Gbar_r = A_r world_r^{-T} and dL_r = R_parent^T Gbar_r.
 #ifndef TB_TREE_KERNELS_CUH
 #define TB_TREE_KERNELS_CUH
 
@@ -170,17 +185,16 @@ constexpr int JSLOTS = JT + JT / JC;
 // ------------------------------------------------------------- workspace
 struct TreeWs {
   // element level
-  unsigned long long* lb;  // look-back words of k_rank, one per element tile
-  unsigned* counter;       // tile ticket of k_rank
+  unsigned long long* lb;  // look-back words of k_tdepth, one per element tile
+  unsigned* counter;       // tile ticket of k_tdepth
   unsigned* xcount;        // number of entries in xlist
-  const int* parent_e;     // parent of every element (matching pass)
-  const int* match_e;      // match of every element (matching pass)
-  int* rank_e;             // opens before each element
-  int* nj;                 // opens counted on the device
   // joint level
-  int* jpos;     // element position of joint r
+  int* jdepth;   // depth of joint r
+  int* premin;   // per joint tile: min of jdepth over the tile up to r
+  int* sufmin;   // per joint tile: min of jdepth over the tile from r on
   int* jparent;  // parent joint, -1 at a root
   int* jend;     // one past the last joint of r's subtree
+  int* g_tree;   // min tree over the joint tiles' minima, 2 * PJ entries
   // DOWN
   void* relT;     // fold of a tile-exported joint relative to its tile's base
   int* t_base;    // per tile: base joint of the exported chain, -1, or NO_CHAIN
@@ -198,14 +212,33 @@ struct TreeWs {
   int PJ;        // next power of two >= TJ
 };
 
-// ------------------------------------------------------------- ranks
-// Exclusive count of opens before every element, by a single pass with a
-// decoupled look-back over the element tiles' open counts, and the element
-// position of every joint.
-__global__ void __launch_bounds__(NT) k_rank(const uint8_t* __restrict__ kind, TreeWs w,
-                                             int* status) {
+// ------------------------------------------------------------- joint tree
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) v += shfl_xor(v, m);
+  return v;
+}
+
+// Look-back word of k_tdepth: flag (2 bits: 1 aggregate, 2 inclusive
+// prefix) | opens (31 bits) | closes (31 bits).
+__device__ __forceinline__ unsigned long long oc_pack(unsigned flag, unsigned opens, unsigned closes) {
+  return ((unsigned long long)flag << 62) | ((unsigned long long)(opens & 0x7fffffffu) << 31) |
+         (unsigned long long)(closes & 0x7fffffffu);
+}
+__device__ __forceinline__ unsigned oc_flag(unsigned long long w) { return (unsigned)(w >> 62); }
+__device__ __forceinline__ unsigned oc_opens(unsigned long long w) { return (unsigned)(w >> 31) & 0x7fffffffu; }
+__device__ __forceinline__ unsigned oc_closes(unsigned long long w) { return (unsigned)w & 0x7fffffffu; }
+
+// Depth of every joint, in one pass over the kinds: open and close counts
+// before each element come from a block scan plus a decoupled look-back over
+// the earlier tiles (warp 0 polls 32 predecessors at a time).  Also checks
+// the kinds, that the depth never drops below 0, that it ends at 0, and that
+// the stream has exactly J opens.
+__global__ void __launch_bounds__(NT) k_tdepth(const uint8_t* __restrict__ kind, TreeWs w,
+                                               int* status) {
   __shared__ int s_scr[NW + 1];
-  __shared__ int s_t, s_excl;
+  __shared__ int s_t;
+  __shared__ unsigned s_o, s_c;
   const int tid = threadIdx.x;
   if (tid == 0) s_t = (int)atomic_add_u32(w.counter, 1u);
   __syncthreads();
@@ -221,133 +254,316 @@ __global__ void __launch_bounds__(NT) k_rank(const uint8_t* __restrict__ kind, T
 #pragma unroll
     for (int i = 0; i < KPT; ++i) kk[i] = e0 + i < w.n ? kind[e0 + i] : (uint8_t)K_PAD;
   }
-  int cnt = 0;
+  int co = 0, cc = 0, run = 0, mn = 0;
+  bool bad = false;
 #pragma unroll
-  for (int i = 0; i < KPT; ++i) cnt += kind_open(kk[i]) ? 1 : 0;
-  int tot;
-  const int ex = block_excl_scan(cnt, 0, OpAdd(), s_scr, &tot);
-  if (tid == 0) {
+  for (int i = 0; i < KPT; ++i) {
+    const int k = kk[i];
+    bad |= k > K_CLOSE && k != K_PAD;
+    co += kind_open(k) ? 1 : 0;
+    cc += k == K_CLOSE ? 1 : 0;
+    run += kind_delta(k);
+    mn = mn < run ? mn : run;
+  }
+  if (bad) atomic_cas_i32(status, ST_OK, ST_BAD_KIND);
+  int tot_o, tot_c, tile_mn;
+  const int ex_o = block_excl_scan(co, 0, OpAdd(), s_scr, &tot_o);
+  const int ex_c = block_excl_scan(cc, 0, OpAdd(), s_scr, &tot_c);
+  block_excl_scan(ex_o - ex_c + mn, INT_MAX, OpMin(), s_scr, &tile_mn);
+  if (warp_id() == 0) {
+    const int lane = lane_id();
     unsigned long long* lb = w.lb;
-    st_release_u64(lb + t, (1ull << 32) | (unsigned)tot);
-    unsigned excl = 0;
+    if (lane == 0) st_release_u64(lb + t, oc_pack(1u, (unsigned)tot_o, (unsigned)tot_c));
+    unsigned xo = 0, xc = 0;
     bool timed_out = false;
-    for (int j = t - 1; j >= 0; --j) {
-      unsigned long long v;
-      unsigned it = 0;
-      for (;;) {
-        v = ld_acquire_u64(lb + j);
-        if ((v >> 32) != 0) break;
-        if (++it >= SPIN_LIMIT) {
-          timed_out = true;
-          break;
+    for (int hi = t - 1; hi >= 0; hi -= 32) {
+      const int j = hi - lane;
+      unsigned flag = 2u;  // before tile 0: inclusive prefix 0
+      unsigned vo = 0, vc = 0;
+      if (j >= 0) {
+        unsigned long long v = 0;
+        unsigned it = 0;
+        for (;;) {
+          v = ld_acquire_u64(lb + j);
+          if (oc_flag(v) != 0) break;
+          if (++it >= SPIN_LIMIT) break;
+          poll_backoff(it);
         }
-        poll_backoff(it);
+        flag = oc_flag(v);
+        vo = oc_opens(v);
+        vc = oc_closes(v);
+        if (flag == 0u) {
+          timed_out = true;
+          flag = 2u;
+          vo = vc = 0;
+        }
       }
-      if (timed_out) break;
-      excl += (unsigned)(v & 0xffffffffull);
-      if ((v >> 32) == 2ull) break;
+      const unsigned incl = ballot(flag == 2u);
+      if (incl != 0u && lane > lowest_set(incl)) vo = vc = 0;
+      xo += (unsigned)warp_sum_i((int)vo);
+      xc += (unsigned)warp_sum_i((int)vc);
+      if (incl != 0u) break;
     }
-    if (timed_out) atomic_cas_i32(status, ST_OK, ST_TIMEOUT);
-    st_release_u64(lb + t, (2ull << 32) | (excl + (unsigned)tot));
-    s_excl = (int)excl;
-    if (t == w.TE - 1) {
-      const int all = (int)(excl + (unsigned)tot);
-      *w.nj = all;
-      if (all != w.J) atomic_cas_i32(status, ST_OK, ST_INVALID);
+    const bool any_timeout = ballot(timed_out) != 0u;
+    if (lane == 0) {
+      if (any_timeout) atomic_cas_i32(status, ST_OK, ST_TIMEOUT);
+      st_release_u64(lb + t, oc_pack(2u, xo + (unsigned)tot_o, xc + (unsigned)tot_c));
+      s_o = xo;
+      s_c = xc;
+      const long long d0 = (long long)xo - (long long)xc;
+      if (d0 + tile_mn < 0) atomic_cas_i32(status, ST_OK, ST_UNBALANCED);
+      if (t == w.TE - 1) {
+        if (d0 + tot_o - tot_c != 0) atomic_cas_i32(status, ST_OK, ST_UNBALANCED);
+        if ((long long)xo + tot_o != (long long)w.J) atomic_cas_i32(status, ST_OK, ST_INVALID);
+      }
     }
   }
   __syncthreads();
-  int r = s_excl + ex;
-  int rk[KPT];
+  int o = (int)s_o + ex_o, c = (int)s_c + ex_c;
 #pragma unroll
   for (int i = 0; i < KPT; ++i) {
-    rk[i] = r;
-    if (kind_open(kk[i])) {
-      if (r < w.J) w.jpos[r] = (int)(e0 + i);
-      ++r;
+    const int k = kk[i];
+    if (kind_open(k)) {
+      if (o < w.J) w.jdepth[o] = o - c + 1;
+      ++o;
+    } else if (k == K_CLOSE) {
+      ++c;
     }
-  }
-  if (e0 + KPT <= w.n) {
-    int4* dst = reinterpret_cast<int4*>(w.rank_e + e0);
-#pragma unroll
-    for (int i = 0; i < KPT / 4; ++i)
-      dst[i] = make_int4(rk[4 * i], rk[4 * i + 1], rk[4 * i + 2], rk[4 * i + 3]);
-  } else {
-#pragma unroll
-    for (int i = 0; i < KPT; ++i)
-      if (e0 + i < w.n) w.rank_e[e0 + i] = rk[i];
   }
 }
 
-// Parent joint and subtree end of every joint.  Values that break
-// -1 <= jparent[r] < r < jend[r] <= J (possible only for input the matching
-// pass already rejected, or a wrong joint count) are replaced so that the
-// later passes stay in bounds, and reported.
-__global__ void k_joint(TreeWs w, int* status) {
-  const int J = w.J;
-  bool bad = false;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < J; r += gridDim.x * blockDim.x) {
-    const int e = w.jpos[r];
-    int jp = -1, je = r + 1;
-    if (e >= 0 && e < w.n) {
-      const int p = w.parent_e[e];
-      const int c = w.match_e[e];
-      if (p >= 0 && p < e) jp = w.rank_e[p];
-      else if (p != -1) bad = true;
-      if (c > e && c < w.n) je = w.rank_e[c];
-      else bad = true;
-    } else {
-      bad = true;
-    }
-    if (jp < -1 || jp >= r) {
-      jp = -1;
-      bad = true;
-    }
-    if (je <= r || je > J) {
-      je = r + 1;
-      bad = true;
-    }
-    w.jparent[r] = jp;
-    w.jend[r] = je;
+// Per joint tile: inclusive prefix and suffix minima of jdepth, tile minimum.
+__global__ void __launch_bounds__(NT) k_jminmax(TreeWs w) {
+  __shared__ int s_scr[NW + 1];
+  const int t = blockIdx.x, tid = threadIdx.x;
+  const int R0 = t * JT, cnt = min(JT, w.J - R0);
+  int d[JC];
+  int mn = INT_MAX;
+#pragma unroll
+  for (int i = 0; i < JC; ++i) {
+    const int k = tid * JC + i;
+    d[i] = k < cnt ? w.jdepth[R0 + k] : INT_MAX;
+    mn = mn < d[i] ? mn : d[i];
   }
-  if (bad) atomic_cas_i32(status, ST_OK, ST_INVALID);
+  int all;
+  int pre = block_excl_scan(mn, INT_MAX, OpMin(), s_scr, &all);
+  int suf = block_excl_suffix_min(mn, s_scr);
+  int sv[JC];
+#pragma unroll
+  for (int i = JC - 1; i >= 0; --i) {
+    suf = suf < d[i] ? suf : d[i];
+    sv[i] = suf;
+  }
+#pragma unroll
+  for (int i = 0; i < JC; ++i) {
+    const int k = tid * JC + i;
+    pre = pre < d[i] ? pre : d[i];
+    if (k < cnt) {
+      w.premin[R0 + k] = pre;
+      w.sufmin[R0 + k] = sv[i];
+    }
+  }
+  if (tid == 0) w.g_tree[w.PJ + t] = all;
 }
 
-// ------------------------------------------------------------- DOWN
-// Per tile: prefix folds of the exported chain relative to its base.
-template <class M>
-__global__ void __launch_bounds__(NT) k_down_chain(TreeWs w, const void* __restrict__ in) {
+// Min tree over the joint tiles (one block); leaves past the last tile hold
+// INT_MAX.
+__global__ void __launch_bounds__(1024) k_jmin_tree(TreeWs w) {
+  const int P = w.PJ;
+  for (int t = w.TJ + threadIdx.x; t < P; t += blockDim.x) w.g_tree[P + t] = INT_MAX;
+  for (int h = P / 2; h >= 1; h >>= 1) {
+    __syncthreads();
+    for (int i = h + threadIdx.x; i < 2 * h; i += blockDim.x) {
+      const int a = w.g_tree[2 * i], b = w.g_tree[2 * i + 1];
+      w.g_tree[i] = a < b ? a : b;
+    }
+  }
+}
+
+// Smallest leaf index u >= x whose value is <= thr, or -1: the mirror of
+// tree_last_le (climb to the first subtree right of the boundary that can
+// hold an answer, then descend into it preferring left).
+__device__ __forceinline__ int tree_first_le(const int* tree, int P, int x, int thr) {
+  if (x >= P) return -1;
+  int node = P + x;
+  for (;;) {
+    if (tree[node] <= thr) break;
+    while (node & 1) {
+      node >>= 1;
+      if (node == 0) return -1;
+    }
+    ++node;
+  }
+  while (node < P) node = (tree[2 * node] <= thr) ? 2 * node : 2 * node + 1;
+  return node - P;
+}
+
+// Parent and subtree end of every joint of the tile; with CHAIN, also the
+// prefix folds of the tile's exported chain (the input of the DOWN scan).
+template <class M, bool CHAIN>
+__global__ void __launch_bounds__(NT) k_jstruct(TreeWs w, const void* __restrict__ in) {
   using V = typename M::V;
+  __shared__ int s_tree[2 * JT];
+  __shared__ int s_rep[JT];
+  __shared__ int s_q[2 * JT];
+  __shared__ int s_nq;
   __shared__ V s_scr[NW + 1];
   __shared__ int s_first;
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT, R1 = R0 + JT;
-  if (tid == 0) s_first = JT;
+  const int cnt = min(JT, w.J - R0);
+  for (int k = tid; k < JT; k += NT) s_tree[JT + k] = k < cnt ? w.jdepth[R0 + k] : INT_MAX;
+  if (tid == 0) {
+    s_first = JT;
+    s_nq = 0;
+  }
+  __syncthreads();
+  for (int h = JT / 2; h >= 1; h >>= 1) {
+    for (int i = h + tid; i < 2 * h; i += NT) {
+      const int a = s_tree[2 * i], b = s_tree[2 * i + 1];
+      s_tree[i] = a < b ? a : b;
+    }
+    __syncthreads();
+  }
+  // In the tile: parent = the previous joint if it is shallower, else the
+  // last shallower joint (tree search); end = the next joint if it is not
+  // deeper, else the first later joint not deeper (tree search).  What the
+  // tile cannot answer goes to a queue served by whole warps below.  All
+  // joints of the tile at depth d whose parent lies before the tile share
+  // that parent (the stack entry at depth d-1 at the tile start), so only
+  // the first joint of the tile at or above depth d (its representative)
+  // queues the question; s_rep maps a representative to its queue slot.
+  int par[JC], end[JC], dep[JC], rep[JC];
+#pragma unroll
+  for (int i = 0; i < JC; ++i) {
+    const int k = tid * JC + i;
+    par[i] = -1;
+    end[i] = -1;
+    rep[i] = -1;
+    dep[i] = k < cnt ? s_tree[JT + k] : INT_MAX;
+    if (k >= cnt) continue;
+    const int d = dep[i];
+    int p;
+    if (k > 0 && s_tree[JT + k - 1] < d) p = k - 1;
+    else p = tree_last_le(s_tree, JT, k, d - 1);
+    if (p >= 0) {
+      par[i] = R0 + p;
+    } else if (d > 1) {
+      rep[i] = tree_first_le(s_tree, JT, 0, d);
+      if (rep[i] == k) s_rep[k] = atomicAdd(&s_nq, 1);
+      if (rep[i] == k) s_q[s_rep[k]] = k;
+    }
+    int e;
+    if (k + 1 < cnt && s_tree[JT + k + 1] <= d) e = k + 1;
+    else e = tree_first_le(s_tree, JT, k + 1, d);
+    if (e >= 0) {
+      end[i] = R0 + e;
+    } else {
+      const int slot = atomicAdd(&s_nq, 1);
+      s_q[slot] = k | (1 << 30);
+      end[i] = -2 - slot;
+    }
+  }
+  __syncthreads();
+  // One question per thread, all in parallel: find the tile (the neighbour
+  // first), then the position in that tile's monotone prefix minima (first
+  // position <= thr) or suffix minima (last position <= thr) by an 8-way
+  // search (eight independent probes per round).
+  for (int qi = tid; qi < s_nq; qi += NT) {
+    const int qv = s_q[qi];
+    const bool is_end = ((qv >> 30) & 1) != 0;
+    const int k = qv & ((1 << 30) - 1);
+    const int d = s_tree[JT + k];
+    const int thr = is_end ? d : d - 1;
+    int tt;
+    if (is_end) {
+      if (t + 1 < w.TJ && w.g_tree[w.PJ + t + 1] <= thr) tt = t + 1;
+      else tt = tree_first_le(w.g_tree, w.PJ, t + 1, thr);
+    } else {
+      if (t > 0 && w.g_tree[w.PJ + t - 1] <= thr) tt = t - 1;
+      else tt = tree_last_le(w.g_tree, w.PJ, t, thr);
+    }
+    int res = is_end ? w.J : -1;
+    if (tt >= 0) {
+      const int len = min(JT, w.J - tt * JT);
+      const int* arr = (is_end ? w.premin : w.sufmin) + (size_t)tt * JT;
+      // first position where the predicate turns true ("<= thr" over the
+      // prefix minima, "> thr" over the suffix minima); len if it never
+      // does.  Positions below lo are false, positions from hi on true.
+      int lo = 0, hi = len;
+      while (lo < hi) {
+        const int step = (hi - lo + 7) >> 3;
+        int v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int pos = lo + j * step;
+          v[j] = pos < hi ? arr[pos] : 0;
+        }
+        int nlo = lo, nhi = hi;
+        bool found = false;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int pos = lo + j * step;
+          if (!found && pos < hi) {
+            if (is_end ? v[j] <= thr : v[j] > thr) {
+              nhi = pos;
+              found = true;
+            } else {
+              nlo = pos + 1;
+            }
+          }
+        }
+        lo = nlo;
+        hi = nhi;
+      }
+      // the end is that position; the parent is the position before it
+      res = tt * JT + (is_end ? lo : lo - 1);
+    }
+    s_q[qi] = res;
+  }
   __syncthreads();
   unsigned xm = 0;
-  V agg = M::identity();
 #pragma unroll
   for (int i = 0; i < JC; ++i) {
-    const int r = R0 + tid * JC + i;
-    if (r < w.J && w.jend[r] > R1) {
-      xm |= 1u << i;
-      agg = M::combine(agg, M::load(in, r));
-    }
+    const int k = tid * JC + i;
+    if (k >= cnt) continue;
+    if (rep[i] >= 0) par[i] = s_q[s_rep[rep[i]]];
+    if (end[i] < -1) end[i] = s_q[-2 - end[i]];
+    w.jparent[R0 + k] = par[i];
+    w.jend[R0 + k] = end[i];
+    if (end[i] > R1) xm |= 1u << i;
   }
-  if (xm) atomicMin(&s_first, tid * JC + lowest_set(xm));
-  V tot;
-  V acc = block_excl_scan(agg, M::identity(), MonoidOp<M>(), s_scr, &tot);
+  if (CHAIN) {
+    V agg = M::identity();
 #pragma unroll
-  for (int i = 0; i < JC; ++i) {
-    if (xm & (1u << i)) {
-      const int r = R0 + tid * JC + i;
-      acc = M::combine(acc, M::load(in, r));
-      M::store(w.relT, r, acc);
+    for (int i = 0; i < JC; ++i)
+      if (xm & (1u << i)) agg = M::combine(agg, M::load(in, R0 + tid * JC + i));
+    if (xm) atomicMin(&s_first, tid * JC + lowest_set(xm));
+    V tot;
+    V acc = block_excl_scan(agg, M::identity(), MonoidOp<M>(), s_scr, &tot);
+#pragma unroll
+    for (int i = 0; i < JC; ++i) {
+      if (xm & (1u << i)) {
+        const int r = R0 + tid * JC + i;
+        acc = M::combine(acc, M::load(in, r));
+        M::store(w.relT, r, acc);
+      }
+    }
+    // block_excl_scan ended with a barrier, so s_first is final
+    const int f = s_first;
+    if (f == JT) {
+      if (tid == 0) w.t_base[t] = NO_CHAIN;
+    } else if (f / JC == tid) {
+      int pv = -1;
+#pragma unroll
+      for (int i = 0; i < JC; ++i)
+        if (i == f % JC) pv = par[i];
+      w.t_base[t] = pv;
     }
   }
-  if (tid == 0) w.t_base[t] = s_first < JT ? w.jparent[R0 + s_first] : NO_CHAIN;
 }
 
+// ------------------------------------------------------------- DOWN
 // Pointer jumping over the tiles (one block): the fold at each tile's base is
 // the fold at its base's tile base times the base's chain prefix.
 template <class M>
@@ -503,6 +719,86 @@ __global__ void __launch_bounds__(NT, 2) k_down_tile(TreeWs w, const void* __res
   for (int k = tid; k < cnt; k += NT) M::store(out, R0 + k, s_val[jslot(k)]);
 }
 
+// ------------------------------------------------------------- adjoint
+// Inverse of the 3x3 part (adjugate over determinant).
+__device__ __forceinline__ void inv3(const Aff& a, float m[3][3]) {
+  const float a00 = a.r0.x, a01 = a.r0.y, a02 = a.r0.z;
+  const float a10 = a.r1.x, a11 = a.r1.y, a12 = a.r1.z;
+  const float a20 = a.r2.x, a21 = a.r2.y, a22 = a.r2.z;
+  const float c00 = a11 * a22 - a12 * a21, c01 = a12 * a20 - a10 * a22, c02 = a10 * a21 - a11 * a20;
+  const float id = 1.0f / (a00 * c00 + a01 * c01 + a02 * c02);
+  m[0][0] = c00 * id;
+  m[1][0] = c01 * id;
+  m[2][0] = c02 * id;
+  m[0][1] = (a02 * a21 - a01 * a22) * id;
+  m[1][1] = (a00 * a22 - a02 * a20) * id;
+  m[2][1] = (a01 * a20 - a00 * a21) * id;
+  m[0][2] = (a01 * a12 - a02 * a11) * id;
+  m[1][2] = (a02 * a10 - a00 * a12) * id;
+  m[2][2] = (a00 * a11 - a01 * a10) * id;
+}
+
+// Gbar_r = A_r world_r^{-T} = [(A^R - A^t t^T) R^{-T} | A^t] and
+// dL_r = R_parent^T Gbar_r (Gbar_r itself at a root).
+__device__ __forceinline__ Aff adjoint_grad(const Aff& A, const Aff& Wr, const Aff* Wp) {
+  float inv[3][3];
+  inv3(Wr, inv);
+  const float tx = Wr.r0.w, ty = Wr.r1.w, tz = Wr.r2.w;
+  const float4 arow[3] = {A.r0, A.r1, A.r2};
+  float4 g[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float4 a = arow[i];
+    const float b0 = a.x - a.w * tx, b1 = a.y - a.w * ty, b2 = a.z - a.w * tz;
+    g[i].x = fmaf(b0, inv[0][0], fmaf(b1, inv[0][1], b2 * inv[0][2]));
+    g[i].y = fmaf(b0, inv[1][0], fmaf(b1, inv[1][1], b2 * inv[1][2]));
+    g[i].z = fmaf(b0, inv[2][0], fmaf(b1, inv[2][1], b2 * inv[2][2]));
+    g[i].w = a.w;
+  }
+  Aff D;
+  if (Wp != nullptr) {
+    const Aff& P = *Wp;
+    // row i of D = sum_k R_p[k][i] * row k of Gbar
+    const float q[3][3] = {{P.r0.x, P.r1.x, P.r2.x}, {P.r0.y, P.r1.y, P.r2.y}, {P.r0.z, P.r1.z, P.r2.z}};
+    float4 d[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      d[i].x = fmaf(q[i][0], g[0].x, fmaf(q[i][1], g[1].x, q[i][2] * g[2].x));
+      d[i].y = fmaf(q[i][0], g[0].y, fmaf(q[i][1], g[1].y, q[i][2] * g[2].y));
+      d[i].z = fmaf(q[i][0], g[0].z, fmaf(q[i][1], g[1].z, q[i][2] * g[2].z));
+      d[i].w = fmaf(q[i][0], g[0].w, fmaf(q[i][1], g[1].w, q[i][2] * g[2].w));
+    }
+    D.r0 = d[0];
+    D.r1 = d[1];
+    D.r2 = d[2];
+  } else {
+    D.r0 = g[0];
+    D.r1 = g[1];
+    D.r2 = g[2];
+  }
+  return D;
+}
+
+// What the UP kernels do with a completed subtree fold besides storing it:
+// nothing, or turn the adjoint's A_r into grad_local[r].
+struct NoFinish {
+  static constexpr bool active = false;
+  template <class V>
+  __device__ void operator()(const TreeWs&, int, const V&) const {}
+};
+struct AdjointFinish {
+  static constexpr bool active = true;
+  const void* world;
+  void* grad_local;
+  __device__ void operator()(const TreeWs& w, int r, const Aff& A) const {
+    const Aff Wr = ld_aff(world, r);
+    const int p = w.jparent[r];
+    Aff Wp;
+    if (p >= 0) Wp = ld_aff(world, p);
+    st_aff(grad_local, r, adjoint_grad(A, Wr, p >= 0 ? &Wp : nullptr));
+  }
+};
+
 // ------------------------------------------------------------- UP
 // Fold of leaves l..r (inclusive) of a segment tree with P leaves; node(i)
 // returns node i.
@@ -553,8 +849,9 @@ constexpr size_t up_tile_smem() {
          (size_t)(NW + 1) * sizeof(typename M::V) + (size_t)JT * sizeof(int);
 }
 
-template <class M, class Values>
-__global__ void __launch_bounds__(NT, 2) k_up_tile(TreeWs w, Values values, void* __restrict__ out) {
+template <class M, class Values, class Finish>
+__global__ void __launch_bounds__(NT, 2) k_up_tile(TreeWs w, Values values, void* __restrict__ out,
+                                                   Finish fin) {
   using V = typename M::V;
   TB_DYNAMIC_SMEM(smem);
   V* s_val = reinterpret_cast<V*>(smem);
@@ -609,7 +906,11 @@ __global__ void __launch_bounds__(NT, 2) k_up_tile(TreeWs w, Values values, void
   const V pre = block_excl_scan(tot, M::identity(), MonoidOp<M>(), s_scr, &all);
   M::store(w.cpre, (int64_t)t * (NCH + 1) + tid, pre);
   if (tid == 0) M::store(w.cpre, (int64_t)t * (NCH + 1) + NCH, all);
-  for (int k = tid; k < cnt; k += NT) M::store(out, R0 + k, s_val[jslot(k)]);
+  for (int k = tid; k < cnt; k += NT) {
+    const V A = s_val[jslot(k)];
+    M::store(out, R0 + k, A);
+    if (Finish::active && s_end[k] <= JT) fin(w, R0 + k, A);
+  }
 }
 
 // Segment tree over the tiles' totals (one block).
@@ -632,8 +933,8 @@ __global__ void __launch_bounds__(1024) k_up_tiles(TreeWs w) {
 // Completes the folds of the subtrees that leave their tile: the partial fold
 // written by k_up_tile, the whole tiles in between, and the prefix of the
 // tile where the subtree ends.
-template <class M>
-__global__ void k_up_cross(TreeWs w, void* __restrict__ out) {
+template <class M, class Finish>
+__global__ void k_up_cross(TreeWs w, void* __restrict__ out, Finish fin) {
   using V = typename M::V;
   const int count = (int)*w.xcount;
   const void* tree = w.t_tree;
@@ -651,73 +952,8 @@ __global__ void k_up_cross(TreeWs w, void* __restrict__ out) {
       acc = M::combine(acc, M::load(w.cpre, (int64_t)t2 * (NCH + 1) + c2));
       for (int j = R2 + c2 * JC; j < e; j = w.jend[j]) acc = M::combine(acc, M::load(out, j));
     }
-    M::store(out, r, acc);
-  }
-}
-
-// ------------------------------------------------------------- adjoint
-// Inverse of the 3x3 part (adjugate over determinant).
-__device__ __forceinline__ void inv3(const Aff& a, float m[3][3]) {
-  const float a00 = a.r0.x, a01 = a.r0.y, a02 = a.r0.z;
-  const float a10 = a.r1.x, a11 = a.r1.y, a12 = a.r1.z;
-  const float a20 = a.r2.x, a21 = a.r2.y, a22 = a.r2.z;
-  const float c00 = a11 * a22 - a12 * a21, c01 = a12 * a20 - a10 * a22, c02 = a10 * a21 - a11 * a20;
-  const float id = 1.0f / (a00 * c00 + a01 * c01 + a02 * c02);
-  m[0][0] = c00 * id;
-  m[1][0] = c01 * id;
-  m[2][0] = c02 * id;
-  m[0][1] = (a02 * a21 - a01 * a22) * id;
-  m[1][1] = (a00 * a22 - a02 * a20) * id;
-  m[2][1] = (a01 * a20 - a00 * a21) * id;
-  m[0][2] = (a01 * a12 - a02 * a11) * id;
-  m[1][2] = (a02 * a10 - a00 * a12) * id;
-  m[2][2] = (a00 * a11 - a01 * a10) * id;
-}
-
-// Gbar_r = A_r world_r^{-T} = [(A^R - A^t t^T) R^{-T} | A^t] and
-// dL_r = R_parent^T Gbar_r (Gbar_r itself at a root).
-__global__ void k_bwd_final(TreeWs w, const void* __restrict__ acc, const void* __restrict__ world,
-                            void* __restrict__ grad_local) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < w.J; r += gridDim.x * blockDim.x) {
-    const Aff A = ld_aff(acc, r);
-    const Aff Wr = ld_aff(world, r);
-    float inv[3][3];
-    inv3(Wr, inv);
-    const float tx = Wr.r0.w, ty = Wr.r1.w, tz = Wr.r2.w;
-    const float4 arow[3] = {A.r0, A.r1, A.r2};
-    float4 g[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const float4 a = arow[i];
-      const float b0 = a.x - a.w * tx, b1 = a.y - a.w * ty, b2 = a.z - a.w * tz;
-      g[i].x = fmaf(b0, inv[0][0], fmaf(b1, inv[0][1], b2 * inv[0][2]));
-      g[i].y = fmaf(b0, inv[1][0], fmaf(b1, inv[1][1], b2 * inv[1][2]));
-      g[i].z = fmaf(b0, inv[2][0], fmaf(b1, inv[2][1], b2 * inv[2][2]));
-      g[i].w = a.w;
-    }
-    Aff D;
-    const int p = w.jparent[r];
-    if (p >= 0) {
-      const Aff P = ld_aff(world, p);
-      // D = R_p^T Gbar: row i of D is sum_k R_p[k][i] * row k of Gbar.
-      const float q[3][3] = {{P.r0.x, P.r1.x, P.r2.x}, {P.r0.y, P.r1.y, P.r2.y}, {P.r0.z, P.r1.z, P.r2.z}};
-      float4 d[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        d[i].x = fmaf(q[i][0], g[0].x, fmaf(q[i][1], g[1].x, q[i][2] * g[2].x));
-        d[i].y = fmaf(q[i][0], g[0].y, fmaf(q[i][1], g[1].y, q[i][2] * g[2].y));
-        d[i].z = fmaf(q[i][0], g[0].z, fmaf(q[i][1], g[1].z, q[i][2] * g[2].z));
-        d[i].w = fmaf(q[i][0], g[0].w, fmaf(q[i][1], g[1].w, q[i][2] * g[2].w));
-      }
-      D.r0 = d[0];
-      D.r1 = d[1];
-      D.r2 = d[2];
-    } else {
-      D.r0 = g[0];
-      D.r1 = g[1];
-      D.r2 = g[2];
-    }
-    st_aff(grad_local, r, D);
+    if (Finish::active) fin(w, r, acc);
+    else M::store(out, r, acc);
   }
 }
 
