@@ -444,7 +444,7 @@ struct OutRes {
 // calling chunk: its global index and (want_clip) the clip in force there.
 // `own` is the chunk cursor (owner of the previous, higher depth).
 template <bool HAS_BOX>
-__device__ __noinline__ OutRes out_lookup(const OutCtx& c, const SceneWs& ws, int dd, int want_clip,
+__device__ __forceinline__ OutRes out_lookup(const OutCtx& c, const SceneWs& ws, int dd, int want_clip,
                                           int own) {
   OutRes r;
   r.cx = box_universe();
