@@ -587,12 +587,31 @@ def run_ours(args):
         p1.record(stream)
         torch.cuda.synchronize()
         ps_ms = p0.elapsed_time(p1) / reps
+        # the batched call captured once in a CUDA graph and replayed
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            rc = binding.tb_bboxes_batched(k_d, b_d, off_d, S, n, parent2, match2, box2, ws, nb,
+                                           status, None)
+        assert rc == binding.TB_OK
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(status.item()) == binding.TB_OK
+        same_graph = (torch.equal(parent, parent2) and torch.equal(match, match2) and
+                      torch.equal(box_out.view(torch.int32), box2.view(torch.int32)))
+        p0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        p1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = p0.elapsed_time(p1) / reps
         per_scene = {"value": round(n / (ps_ms * 1e-3) / 1e9, 3), "unit": "Gelem/s",
                      "ms_per_step": round(ps_ms, 4),
                      "launches": "%d plain tb_bboxes calls on one stream" % len(calls),
                      "outputs_identical": bool(same),
-                     "batched_over_per_scene": round(ps_ms / ms_step, 2)}
-        del parent2, match2, box2, calls
+                     "batched_over_per_scene": round(ps_ms / ms_step, 2),
+                     "graph_ms_per_step": round(graph_ms, 4),
+                     "graph_outputs_identical": bool(same_graph)}
+        del parent2, match2, box2, calls, g
 
     # ---- end to end through the public API with host buffers
     kind_h = torch.from_numpy(kind).pin_memory()

@@ -144,6 +144,35 @@ __device__ __forceinline__ int block_excl_suffix_min(int v, int* s) {
   return r;
 }
 
+// Exclusive suffix fold over the NT threads in thread order: thread j gets
+// v_{j+1} * ... * v_{NT-1} (ident for the last thread).  s holds NW values.
+template <class T, class Op>
+__device__ T block_excl_suffix(T v, T ident, Op op, T* s) {
+  const int lane = lane_id(), w = warp_id();
+  T incl = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T y = shfl_down(incl, d);
+    if (lane + d < 32) incl = op(incl, y);
+  }
+  if (lane == 0) s[w] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T acc = ident;
+    for (int i = NW - 1; i >= 0; --i) {
+      const T x = s[i];
+      s[i] = acc;
+      acc = op(x, acc);
+    }
+  }
+  __syncthreads();
+  T ex = shfl_down(incl, 1);
+  if (lane == 31) ex = ident;
+  const T r = op(ex, s[w]);
+  __syncthreads();
+  return r;
+}
+
 // ----------------------------------------------------------- segment trees
 // Implicit tree over P leaves (P a power of two): leaves at [P, 2P), node i
 // covers its children 2i and 2i+1, the root is node 1.

@@ -477,6 +477,7 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
   __shared__ int s_info[3];
   __shared__ int s_cidx[CTXC];
   __shared__ float4 s_cclip[CTXC];
+  __shared__ float4 s_fscr[NW];
   __shared__ SegState S;
   __shared__ long long s_soff[SOFF_CAP + 1];
   __shared__ int s_sc[2];
@@ -918,13 +919,13 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
     if ((um >> i) & 1u) s_box[box_slot(p0 + i)] = run;
   }
   const int later_lo = block_excl_suffix_min(lo_j, s_scr);
+  const float4 rest = block_excl_suffix(run, box_empty(), OpUnite(), s_fscr);  // later chunks
   float4* s_ut = s_val;  // union tree over the chunks' leaf unions
   build_chunk_tree(s_ut, run, OpUnite());
   // span(x) = union of the chunks (cps(x), x]: what a close gains when its
   // open's owner moves one cps link down
   s_span[tid] = chunk_range(s_ut, cps + 1, tid, box_empty(), OpUnite());
-  float4 mid = chunk_range(s_ut, cq + 1, tid - 1, box_empty(), OpUnite());
-  const float4 rest = chunk_range(s_ut, tid + 1, NT - 1, box_empty(), OpUnite());
+  float4 mid = xcl ? chunk_range(s_ut, cq + 1, tid - 1, box_empty(), OpUnite()) : box_empty();
   __syncthreads();
   {
     // Closes matching an open of an earlier chunk: union = the open's chunk
