@@ -84,7 +84,7 @@ struct K1Args {
 };
 
 template <bool HAS_BOX>
-__global__ void __launch_bounds__(NT) k1_tile_summary(K1Args a) {
+__global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
   __shared__ int s_scr[NW + 1];
   __shared__ float4 s_fscr[NW + 1];
   __shared__ int s_t;
@@ -118,13 +118,55 @@ __global__ void __launch_bounds__(NT) k1_tile_summary(K1Args a) {
   const int b_t = tot + a_t;  // Bic(tile).b: opens left unmatched at the tile end
   const int suf_after = block_excl_suffix_min(ds + mn_after, s_scr);
 
+  // Publish this tile's depth delta at once: later tiles may sum it while
+  // this block is still busy.
+  if (threadIdx.x == 0 && t != a.withhold) st_release_u64(a.ws.lb + t, lb_pack(1u, tot));
+
+  // The tile's stack slice: an open is unmatched in the tile when the depth
+  // never comes back below its level before the tile ends.  Its slot is its
+  // depth relative to the tile's lowest depth (Sec. 7.1).
+  unsigned umt = 0;
+  {
+    int suf = suf_after;
+#pragma unroll
+    for (int i = KPT - 1; i >= 0; --i) {
+      const int A = ds + rr[i];
+      suf = suf < A ? suf : A;
+      if (kind_open(kk[i]) && A <= suf) umt |= 1u << i;
+    }
+  }
+  int* slice_pos = a.ws.slice_pos + (size_t)t * TILE;
+#pragma unroll
+  for (int i = 0; i < KPT; ++i)
+    if ((umt >> i) & 1u) slice_pos[ds + rr[i] - 1 + a_t] = base + p0 + i;
+
+  if (HAS_BOX) {
+    // Running intersection along the slice (Sec. 9: the boxes of a stack
+    // slice are the inclusive intersection scan of its clip boxes).
+    float4 loc = box_universe();
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+      if (((umt >> i) & 1u) && kk[i] == K_CLIP) loc = box_isect(loc, ld_nc_f4(a.box + base + p0 + i));
+    float4 tot4;
+    float4 acc = block_excl_scan(loc, box_universe(), OpIsect(), s_fscr, &tot4);
+    float4* slice_rel = a.ws.slice_rel + (size_t)t * TILE;
+#pragma unroll
+    for (int i = 0; i < KPT; ++i) {
+      if ((umt >> i) & 1u) {
+        if (kk[i] == K_CLIP) acc = box_isect(acc, ld_nc_f4(a.box + base + p0 + i));
+        slice_rel[ds + rr[i] - 1 + a_t] = acc;
+      }
+    }
+  }
+
   // Decoupled look-back (single pass) for the global depth at the tile
-  // start: publish this tile's depth delta, then warp 0 adds predecessors'
-  // deltas 32 tiles per poll until one that knows its inclusive prefix.
+  // start: this tile's depth delta was published above; warp 0 adds
+  // predecessors' deltas 32 tiles per poll until one that knows its
+  // inclusive prefix.  It runs last, after all the tile-local work, so no
+  // barrier of the block waits for it.
   if (warp_id() == 0) {
     const int lane = lane_id();
     unsigned long long* lb = a.ws.lb;
-    if (lane == 0 && t != a.withhold) st_release_u64(lb + t, lb_pack(1u, tot));
     int excl = 0;
     bool timed_out = false;
     for (int hi = t - 1; hi >= 0; hi -= 32) {
@@ -163,43 +205,6 @@ __global__ void __launch_bounds__(NT) k1_tile_summary(K1Args a) {
       a.ws.t_lo[t] = excl - a_t;
       if (excl - a_t < 0) atomic_cas_i32(a.status, ST_OK, ST_UNBALANCED);
       if (t == a.ws.T - 1 && excl + tot != 0) atomic_cas_i32(a.status, ST_OK, ST_UNBALANCED);
-    }
-  }
-
-  // The tile's stack slice: an open is unmatched in the tile when the depth
-  // never comes back below its level before the tile ends.  Its slot is its
-  // depth relative to the tile's lowest depth (Sec. 7.1).
-  unsigned umt = 0;
-  {
-    int suf = suf_after;
-#pragma unroll
-    for (int i = KPT - 1; i >= 0; --i) {
-      const int A = ds + rr[i];
-      suf = suf < A ? suf : A;
-      if (kind_open(kk[i]) && A <= suf) umt |= 1u << i;
-    }
-  }
-  int* slice_pos = a.ws.slice_pos + (size_t)t * TILE;
-#pragma unroll
-  for (int i = 0; i < KPT; ++i)
-    if ((umt >> i) & 1u) slice_pos[ds + rr[i] - 1 + a_t] = base + p0 + i;
-
-  if (HAS_BOX) {
-    // Running intersection along the slice (Sec. 9: the boxes of a stack
-    // slice are the inclusive intersection scan of its clip boxes).
-    float4 loc = box_universe();
-#pragma unroll
-    for (int i = 0; i < KPT; ++i)
-      if (((umt >> i) & 1u) && kk[i] == K_CLIP) loc = box_isect(loc, ld_nc_f4(a.box + base + p0 + i));
-    float4 tot4;
-    float4 acc = block_excl_scan(loc, box_universe(), OpIsect(), s_fscr, &tot4);
-    float4* slice_rel = a.ws.slice_rel + (size_t)t * TILE;
-#pragma unroll
-    for (int i = 0; i < KPT; ++i) {
-      if ((umt >> i) & 1u) {
-        if (kk[i] == K_CLIP) acc = box_isect(acc, ld_nc_f4(a.box + base + p0 + i));
-        slice_rel[ds + rr[i] - 1 + a_t] = acc;
-      }
     }
   }
 }
@@ -584,13 +589,18 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
   const bool ovf = nseg > SEGK;
 
   // ---- tile context: the top CTXC entries of the stack below the tile
-  // start, fetched now so that their latency overlaps the work below
+  // start, loaded into registers now and stored to shared memory after the
+  // register work below, so that their latency overlaps it
   if (ovf) fill_ctx_overflow(S, ws, t, dstart_t, a_t + 1, s_seg);
-  if (tid < CTXC && tid <= a_t) {
+  const bool ctx_mine = tid < CTXC && tid <= a_t;
+  int ctx_i = -1;
+  float4 ctx_c = box_universe();
+  if (ctx_mine) {
     const int src = ctx_src_of(ws, t, ovf, s_seg, nseg, dstart_t - 1 - tid, tid);
-    s_cidx[tid] = src >= 0 ? ws.slice_pos[src] : -1;
-    if (HAS_BOX)
-      s_cclip[tid] = src >= 0 ? box_isect(ws.t_B[src / TILE], ws.slice_rel[src]) : box_universe();
+    if (src >= 0) {
+      ctx_i = ws.slice_pos[src];
+      if (HAS_BOX) ctx_c = box_isect(ws.t_B[src / TILE], ws.slice_rel[src]);
+    }
   }
 
   // ---- per-element lookups for the walk, from the chunk structure alone
@@ -627,6 +637,10 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
     }
   }
 
+  if (ctx_mine) {
+    s_cidx[tid] = ctx_i;
+    if (HAS_BOX) s_cclip[tid] = ctx_c;
+  }
   if (HAS_BOX) {
     cp_async_wait_all();
     __syncthreads();
