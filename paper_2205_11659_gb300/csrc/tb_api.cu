@@ -141,25 +141,12 @@ cudaError_t launch_k3(const K3Args& a, int T, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// The tile-level resolve keeps its tree and links in shared memory when they
-// fit, else works on the copies in the workspace.
-constexpr size_t kK2SmemMax = 200 * 1024;
-
 template <bool HAS_BOX>
 cudaError_t launch_k2(const SceneWs& w, cudaStream_t s) {
-  const size_t smem = k2_smem_bytes(w.T, w.P);
-  if (smem <= kK2SmemMax) {
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaError_t e = cudaFuncSetAttribute(k2_tile_resolve<HAS_BOX, true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kK2SmemMax);
-      if (e != cudaSuccess) return e;
-      attr_set = true;
-    }
-    k2_tile_resolve<HAS_BOX, true><<<1, NT2, smem, s>>>(w);
-  } else {
-    k2_tile_resolve<HAS_BOX, false><<<1, NT2, 0, s>>>(w);
-  }
+  const int g = (w.T + NTR - 1) / NTR;
+  k2_links<<<g, NTR, 0, s>>>(w);
+  k2_segments<HAS_BOX><<<g, NTR, 0, s>>>(w);
+  if (HAS_BOX) k2_jump<<<1, NT2, 0, s>>>(w);
   return cudaGetLastError();
 }
 
@@ -191,6 +178,9 @@ tb_status run_scene(const uint8_t* kind, const float* box, int64_t n, int32_t* p
 
   const SceneWs w = scene_ws(L, ws, HAS_BOX);
   if (cudaMemsetAsync(ws, 0, L.t_a, s) != cudaSuccess) return TB_ERR_CUDA;
+  if (cudaMemsetAsync(static_cast<unsigned char*>(ws) + L.lo_tree, 0x7f, (size_t)2 * L.P * 4, s) !=
+      cudaSuccess)
+    return TB_ERR_CUDA;
 
   phase_mark(s);
   K1Args a1{kind, reinterpret_cast<const float4*>(box), (int)n, w, d_status, withhold_tile};

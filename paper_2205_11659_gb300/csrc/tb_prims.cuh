@@ -52,6 +52,7 @@ __device__ __forceinline__ void poll_backoff(unsigned it) {
 
 __device__ __forceinline__ unsigned atomic_add_u32(unsigned* p, unsigned v) { return atomicAdd(p, v); }
 __device__ __forceinline__ int atomic_cas_i32(int* p, int cmp, int v) { return atomicCAS(p, cmp, v); }
+__device__ __forceinline__ void atomic_min_i32(int* p, int v) { atomicMin(p, v); }
 
 // 16-byte asynchronous global -> shared copy (cp.async.cg, bypassing L1),
 // committed as one group and awaited with cp_async_wait_all.

@@ -203,6 +203,11 @@ __global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
       a.ws.t_b[t] = b_t;
       a.ws.t_dstart[t] = excl;
       a.ws.t_lo[t] = excl - a_t;
+      // min tree over the tiles' lowest depths for the owner searches: this
+      // tile's leaf and the minimum along its path to the root (the tree
+      // starts out filled with 0x7f7f7f7f, above any depth)
+      a.ws.lo_tree[a.ws.P + t] = excl - a_t;
+      for (int i = (a.ws.P + t) >> 1; i >= 1; i >>= 1) atomic_min_i32(&a.ws.lo_tree[i], excl - a_t);
       if (excl - a_t < 0) atomic_cas_i32(a.status, ST_OK, ST_UNBALANCED);
       if (t == a.ws.T - 1 && excl + tot != 0) atomic_cas_i32(a.status, ST_OK, ST_UNBALANCED);
     }
@@ -210,101 +215,110 @@ __global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
 }
 
 // ------------------------------------------------------------------- K2
+// Tile-level resolve, one thread per tile.  lo_tree, the min tree over the
+// tiles' lowest depths, was built by k1_tile_summary.
 constexpr int NT2 = 1024;
+constexpr int NTR = 256;
 
-// Dynamic shared memory of k2_tile_resolve when the tile tree and the ps
-// links live in shared memory.
-__host__ __device__ constexpr size_t k2_smem_bytes(int T, int P) { return (size_t)(2 * P + T) * 4; }
+// Owner links: ps = owner of depth lo - 1 (last earlier tile whose lowest
+// depth is at most lo - 1), q = owner of depth dstart - 1.
+__global__ void __launch_bounds__(NTR) k2_links(SceneWs ws) {
+  const int u = blockIdx.x * NTR + threadIdx.x;
+  if (u >= ws.T) return;
+  const int lo = ws.t_lo[u], ds = ws.t_dstart[u];
+  ws.t_ps[u] = lo - 1 >= 0 ? tree_last_le(ws.lo_tree, ws.P, u, lo - 1) : -1;
+  ws.t_q[u] = ds - 1 >= 0 ? tree_last_le(ws.lo_tree, ws.P, u, ds - 1) : -1;
+}
 
-template <bool HAS_BOX, bool SMEM>
-__global__ void __launch_bounds__(NT2) k2_tile_resolve(SceneWs ws) {
-  TB_DYNAMIC_SMEM(smem);
-  const int T = ws.T, P = ws.P, tid = threadIdx.x;
-  int* tree = SMEM ? reinterpret_cast<int*>(smem) : ws.lo_tree;
-  int* ps = SMEM ? tree + 2 * P : ws.t_ps;
-  for (int u = tid; u < P; u += NT2) tree[P + u] = u < T ? ws.t_lo[u] : INT_MAX;
-  __syncthreads();
-  for (int h = P >> 1; h >= 1; h >>= 1) {
-    for (int i = h + tid; i < 2 * h; i += NT2) {
-      const int l = tree[2 * i], r = tree[2 * i + 1];
-      tree[i] = l < r ? l : r;
+// Owner segments of the stack at each tile start, depths ds-1 .. ds-1-a:
+// from the owner q of depth ds-1, each owner covers down to its lowest depth
+// and hands over to its ps.  With boxes, also the first step of the pointer
+// jumping below: v(u) = relative clip of the ps tile's slice entry at depth
+// lo(u)-1, link(u) = ps(u).
+template <bool HAS_BOX>
+__global__ void __launch_bounds__(NTR) k2_segments(SceneWs ws) {
+  const int u = blockIdx.x * NTR + threadIdx.x;
+  if (u >= ws.T) return;
+  const int ds = ws.t_dstart[u];
+  int dtop = ds - 1;
+  const int dbot = ds - 1 - ws.t_a[u];
+  int own = ws.t_q[u];
+  int n = 0;
+  int4* seg = ws.t_seg + (size_t)u * SEGK;
+  while (dtop >= dbot && n < SEGK) {
+    if (dtop < 0 || own < 0) {
+      seg[n++] = make_int4(-1, 0, dbot, dtop);
+      dtop = dbot - 1;
+      break;
     }
-    __syncthreads();
+    const int lo_o = ws.t_lo[own];
+    const int lo_s = lo_o > dbot ? lo_o : dbot;
+    seg[n++] = make_int4(own, lo_o, lo_s, dtop);
+    dtop = lo_s - 1;
+    own = ws.t_ps[own];
   }
-  for (int u = tid; u < T; u += NT2) {
-    const int lo = tree[P + u], ds = ws.t_dstart[u];
-    const int p = lo - 1 >= 0 ? tree_last_le(tree, P, u, lo - 1) : -1;
-    ps[u] = p;
-    if (SMEM) ws.t_ps[u] = p;
-    ws.t_q[u] = ds - 1 >= 0 ? tree_last_le(tree, P, u, ds - 1) : -1;
-  }
-  __syncthreads();
-  // Owner segments of the stack at each tile start, depths ds-1 .. ds-1-a:
-  // from the owner q of depth ds-1, each owner covers down to its lowest
-  // depth and hands over to its ps.
-  for (int u = tid; u < T; u += NT2) {
-    const int ds = ws.t_dstart[u];
-    int dtop = ds - 1;
-    const int dbot = ds - 1 - ws.t_a[u];
-    int own = ws.t_q[u];
-    int n = 0;
-    int4* seg = ws.t_seg + (size_t)u * SEGK;
-    while (dtop >= dbot && n < SEGK) {
-      if (dtop < 0 || own < 0) {
-        seg[n++] = make_int4(-1, 0, dbot, dtop);
-        dtop = dbot - 1;
-        break;
-      }
-      const int lo_o = tree[P + own];
-      const int lo_s = lo_o > dbot ? lo_o : dbot;
-      seg[n++] = make_int4(own, lo_o, lo_s, dtop);
-      dtop = lo_s - 1;
-      own = ps[own];
-    }
-    if (dtop >= dbot) {
-      ws.t_nseg[u] = SEGK + 1;
-      ws.t_cont[u] = make_int2(own, dtop);
-    } else {
-      ws.t_nseg[u] = n;
-    }
+  if (dtop >= dbot) {
+    ws.t_nseg[u] = SEGK + 1;
+    ws.t_cont[u] = make_int2(own, dtop);
+  } else {
+    ws.t_nseg[u] = n;
   }
   if constexpr (HAS_BOX) {
-  // v(u): relative clip of the ps tile's slice entry at depth lo(u)-1;
-  // B(u) = B(ps(u)) * v(u) is then a fold along the ps chain, done by
-  // pointer jumping: each round doubles the covered chain length.
-  for (int u = tid; u < T; u += NT2) {
-    const int lo = tree[P + u], p = ps[u];
+    const int lo = ws.t_lo[u], p = ws.t_ps[u];
     float4 v = box_universe();
     int l = -1;
     if (lo - 1 >= 0 && p >= 0) {
-      v = ws.slice_rel[(size_t)p * TILE + (lo - 1 - tree[P + p])];
+      v = ws.slice_rel[(size_t)p * TILE + (lo - 1 - ws.t_lo[p])];
       l = p;
     }
     ws.t_val[0][u] = v;
     ws.t_link[0][u] = l;
   }
-  __syncthreads();
+}
+
+// B(u) = B(ps(u)) * v(u) is a fold along the ps chain: pointer jumping in
+// one block, each round doubling the covered chain length (Sec. 6.1).  The
+// loads of a round are issued in batches of KB tiles per thread.
+constexpr int K2_KB = 4;
+__global__ void __launch_bounds__(NT2) k2_jump(SceneWs ws) {
+  const int T = ws.T, tid = threadIdx.x;
   int cur = 0;
-  for (;;) {
+  for (int round = 0; round < 40; ++round) {
     bool any = false;
-    for (int u = tid; u < T; u += NT2) {
-      const int l = ws.t_link[cur][u];
-      float4 v = ws.t_val[cur][u];
-      int nl = -1;
-      if (l >= 0) {
-        v = box_isect(ws.t_val[cur][l], v);
-        nl = ws.t_link[cur][l];
+    for (int u0 = tid; u0 < T; u0 += NT2 * K2_KB) {
+      int l[K2_KB], nl[K2_KB];
+      float4 v[K2_KB], pv[K2_KB];
+#pragma unroll
+      for (int b = 0; b < K2_KB; ++b) {
+        const int u = u0 + b * NT2;
+        l[b] = -1;
+        if (u < T) {
+          l[b] = ws.t_link[cur][u];
+          v[b] = ws.t_val[cur][u];
+        }
       }
-      ws.t_val[cur ^ 1][u] = v;
-      ws.t_link[cur ^ 1][u] = nl;
-      any |= nl >= 0;
+#pragma unroll
+      for (int b = 0; b < K2_KB; ++b) {
+        nl[b] = -1;
+        if (l[b] >= 0) {
+          pv[b] = ws.t_val[cur][l[b]];
+          nl[b] = ws.t_link[cur][l[b]];
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < K2_KB; ++b) {
+        const int u = u0 + b * NT2;
+        if (u < T) {
+          ws.t_val[cur ^ 1][u] = l[b] >= 0 ? box_isect(pv[b], v[b]) : v[b];
+          ws.t_link[cur ^ 1][u] = nl[b];
+          any |= nl[b] >= 0;
+        }
+      }
     }
-    any = block_or(any);
     cur ^= 1;
-    if (!any) break;
+    if (!block_or(any)) break;
   }
   for (int u = tid; u < T; u += NT2) ws.t_B[u] = ws.t_val[cur][u];
-  }
 }
 
 // ----------------------------------------------------- tile context helpers
