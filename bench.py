@@ -621,19 +621,27 @@ def run_ours(args):
               torch.empty(n, dtype=torch.int32).pin_memory(),
               torch.empty(n, 4, dtype=torch.float32).pin_memory())
 
-    def e2e_step():
-        if offsets is None:
-            binding.bboxes_host(kind_h, box_h, outs_h)
-        else:
+    e2e_steps = max(3, min(K, 6))
+    if offsets is None:
+        # scenes streamed from pinned host memory: copies in, the pass and
+        # copies out of consecutive steps overlap (HostPipeline)
+        pipe = binding.HostPipeline(n, dev)
+        pipe.run([kind_h], [box_h], [outs_h])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pipe.run([kind_h] * e2e_steps, [box_h] * e2e_steps, [outs_h] * e2e_steps)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        del pipe
+    else:
+        def e2e_step():
             binding.bboxes_batched_host(kind_h, box_h, off_h, outs_h)
-    e2e_steps = max(2, min(K, 5))
-    e2e_step()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
         e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
     h2d = kind.nbytes + box.nbytes + (offsets.nbytes if offsets is not None else 0)
     d2h = 4 * n + 4 * n + 16 * n
 

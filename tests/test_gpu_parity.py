@@ -210,3 +210,22 @@ def test_full_batched_4096_scenes():
     torch.cuda.synchronize()
     assert np.array_equal(p.cpu().numpy(), op) and np.array_equal(m.cpu().numpy(), om)
     assert same_bits(o.cpu().numpy(), ob)
+
+
+def test_host_pipeline_matches_oracle():
+    """Scenes streamed from pinned host memory with overlapped copies give
+    the oracle's results, including a repeated scene and a size change."""
+    scenes = [inputs.random_walk_scene(n, 900 + n) for n in (70_001, 4096, 300_000, 70_001)]
+    pipe = binding.HostPipeline(300_000)
+    kinds = [torch.from_numpy(k).pin_memory() for k, _ in scenes]
+    boxes = [torch.from_numpy(b).pin_memory() for _, b in scenes]
+    outs = [(torch.empty(k.size, dtype=torch.int32).pin_memory(),
+             torch.empty(k.size, dtype=torch.int32).pin_memory(),
+             torch.empty(k.size, 4, dtype=torch.float32).pin_memory()) for k, _ in scenes]
+    for _ in range(2):
+        pipe.run(kinds, boxes, outs)
+        for (k, b), (p, m, o) in zip(scenes, outs):
+            st, op, om, ob = oracle.bboxes(k, b)
+            assert st == oracle.OK
+            assert np.array_equal(p.numpy(), op) and np.array_equal(m.numpy(), om)
+            assert same_bits(o.numpy(), ob)
