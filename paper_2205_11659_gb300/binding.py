@@ -80,6 +80,8 @@ def lib():
             L.tb_set_phase_events.argtypes = [p, i32]
             L.tb_bboxes_static_ws.argtypes = [p, p, i64, p, p, p, p, p]
             L.tb_tree_scan.argtypes = [i32, i32, p, i64, i64, p, p, p, sz, p, p]
+            L.tb_debug_withhold_tile.argtypes = [i32]
+            L.tb_debug_withhold_tile.restype = i32
             L.tb_tree_scan_affine_backward.argtypes = [p, i64, i64, p, p, p, p, sz, p, p]
             for f in (L.tb_match_parens, L.tb_bboxes, L.tb_bboxes_batched, L.tb_set_phase_events,
                       L.tb_bboxes_static_ws, L.tb_tree_scan, L.tb_tree_scan_affine_backward):
@@ -160,6 +162,12 @@ def tb_tree_scan_affine_backward(kind, n, num_joints, local, grad_world, grad_lo
     return lib().tb_tree_scan_affine_backward(_ptr(kind), int(n), int(num_joints), _ptr(local),
                                               _ptr(grad_world), _ptr(grad_local), _ptr(ws),
                                               int(ws_bytes), _ptr(d_status), _stream(stream))
+
+
+def tb_debug_withhold_tile(tile):
+    """Test hook: tile `tile` of the following scene calls on this thread never
+    publishes its look-back word (-1 turns it off)."""
+    return lib().tb_debug_withhold_tile(int(tile))
 
 
 def tb_set_phase_events(events):

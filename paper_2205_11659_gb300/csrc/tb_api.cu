@@ -121,6 +121,10 @@ thread_local cudaEvent_t g_phase_events[kMaxPhaseEvents];
 thread_local int g_phase_n = 0;
 thread_local int g_phase_next = 0;
 
+// Test hook: a tile of the following scene calls that never publishes its
+// look-back word (-1: none).
+thread_local int g_withhold = -1;
+
 inline void phase_mark(cudaStream_t s) {
   if (g_phase_next < g_phase_n) cudaEventRecord(g_phase_events[g_phase_next++], s);
 }
@@ -176,7 +180,8 @@ tb_status run_scene(const uint8_t* kind, const float* box, int64_t n, int32_t* p
   if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return TB_ERR_CUDA;
   if (n == 0) return TB_OK;
 
-  const SceneWs w = scene_ws(L, ws, HAS_BOX);
+  SceneWs w = scene_ws(L, ws, HAS_BOX);
+  w.status = d_status;
   if (cudaMemsetAsync(ws, 0, L.t_a, s) != cudaSuccess) return TB_ERR_CUDA;
   if (cudaMemsetAsync(static_cast<unsigned char*>(ws) + L.lo_tree, 0x7f, (size_t)2 * L.P * 4, s) !=
       cudaSuccess)
@@ -232,7 +237,7 @@ tb_status tb_match_parens(const uint8_t* kind, int64_t n, int32_t* parent, int32
                           size_t ws_bytes, int32_t* d_status, void* stream) {
   g_phase_next = 0;
   return run_scene<false>(kind, nullptr, n, parent, match, nullptr, nullptr, 0, ws, ws_bytes,
-                          d_status, stream, -1);
+                          d_status, stream, g_withhold);
 }
 
 tb_status tb_bboxes(const uint8_t* kind, const float* box, int64_t n, int32_t* parent,
@@ -240,7 +245,7 @@ tb_status tb_bboxes(const uint8_t* kind, const float* box, int64_t n, int32_t* p
                     void* stream) {
   g_phase_next = 0;
   return run_scene<true>(kind, box, n, parent, match, box_out, nullptr, 0, ws, ws_bytes, d_status,
-                         stream, -1);
+                         stream, g_withhold);
 }
 
 tb_status tb_bboxes_batched(const uint8_t* kind, const float* box, const int64_t* offsets,
@@ -250,7 +255,7 @@ tb_status tb_bboxes_batched(const uint8_t* kind, const float* box, const int64_t
   if (offsets == nullptr || num_scenes < 1) return TB_ERR_INVALID_ARG;
   g_phase_next = 0;
   return run_scene<true>(kind, box, n_total, parent, match, box_out, offsets, num_scenes, ws,
-                         ws_bytes, d_status, stream, -1);
+                         ws_bytes, d_status, stream, g_withhold);
 }
 
 tb_status tb_set_phase_events(void* const* events, int num_events) {
@@ -267,6 +272,12 @@ tb_status tb_set_phase_events(void* const* events, int num_events) {
 }
 
 const char* tb_version(void) { return "treebox-gb300 0.1 (sm_103a)"; }
+
+tb_status tb_debug_withhold_tile(int tile) {
+  if (tile < -1) return TB_ERR_INVALID_ARG;
+  g_withhold = tile;
+  return TB_OK;
+}
 
 }  // extern "C"
 
@@ -324,7 +335,7 @@ tb_status tb_bboxes_static_ws(const uint8_t* kind, const float* box, int64_t n, 
   // on every call; everything else in it is written before it is read.
   g_phase_next = 0;
   return run_scene<true>(kind, box, n, parent, match, box_out, nullptr, 0, ws, kStaticWsBytes,
-                         d_status, stream, -1);
+                         d_status, stream, g_withhold);
 }
 
 }  // extern "C"

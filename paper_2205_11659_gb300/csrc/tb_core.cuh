@@ -248,6 +248,8 @@ struct SceneWs {
   int* t_ps;
   int* t_q;
   int* lo_tree;      // 2P
+  const int* status; // status word of the call: the passes after the tile
+                     // summaries stop at once when it already holds an error
   int* t_link[2];
   float4* t_val[2];
   float4* t_B;

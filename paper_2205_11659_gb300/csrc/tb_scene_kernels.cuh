@@ -224,7 +224,7 @@ constexpr int NTR = 256;
 // depth is at most lo - 1), q = owner of depth dstart - 1.
 __global__ void __launch_bounds__(NTR) k2_links(SceneWs ws) {
   const int u = blockIdx.x * NTR + threadIdx.x;
-  if (u >= ws.T) return;
+  if (u >= ws.T || *ws.status != ST_OK) return;
   const int lo = ws.t_lo[u], ds = ws.t_dstart[u];
   ws.t_ps[u] = lo - 1 >= 0 ? tree_last_le(ws.lo_tree, ws.P, u, lo - 1) : -1;
   ws.t_q[u] = ds - 1 >= 0 ? tree_last_le(ws.lo_tree, ws.P, u, ds - 1) : -1;
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(NTR) k2_links(SceneWs ws) {
 template <bool HAS_BOX>
 __global__ void __launch_bounds__(NTR) k2_segments(SceneWs ws) {
   const int u = blockIdx.x * NTR + threadIdx.x;
-  if (u >= ws.T) return;
+  if (u >= ws.T || *ws.status != ST_OK) return;
   const int ds = ws.t_dstart[u];
   int dtop = ds - 1;
   const int dbot = ds - 1 - ws.t_a[u];
@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(NTR) k2_segments(SceneWs ws) {
 constexpr int K2_KB = 4;
 __global__ void __launch_bounds__(NT2) k2_jump(SceneWs ws) {
   const int T = ws.T, tid = threadIdx.x;
+  if (*ws.status != ST_OK) return;  // no pass running now writes it: uniform
   int cur = 0;
   for (int round = 0; round < 40; ++round) {
     bool any = false;
@@ -494,6 +495,7 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
   __shared__ int s_scr[NW + 1];
   __shared__ int4 s_seg[SEGK];
   __shared__ int s_info[3];
+  __shared__ int s_stop;
   __shared__ int s_cidx[CTXC];
   __shared__ float4 s_cclip[CTXC];
   __shared__ float4 s_fscr[NW];
@@ -507,6 +509,12 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
   const int cnt = min(TILE, a.n - base);
   const int p0 = tid * KPT;
   const SceneWs& ws = a.ws;
+  // An error of the earlier passes leaves their tile data inconsistent: stop.
+  // (This pass may itself report an unbalanced scene while other blocks run,
+  // so one thread reads the word and the block follows it.)
+  if (tid == 0) s_stop = *a.status;
+  __syncthreads();
+  if (s_stop != ST_OK) return;
 
   unsigned char* sp = smem;
   float4* s_box = reinterpret_cast<float4*>(sp);
@@ -1020,6 +1028,7 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
 // ------------------------------------------------------------------- K4
 __global__ void __launch_bounds__(NT2) k4_union_tree(SceneWs ws) {
   const int T = ws.T, P = ws.P, tid = threadIdx.x;
+  if (*ws.status != ST_OK) return;
   float4* tree = ws.uall_tree;
   for (int u = tid; u < P; u += NT2) tree[P + u] = u < T ? ws.t_uall[u] : box_empty();
   __syncthreads();
@@ -1045,7 +1054,7 @@ __global__ void __launch_bounds__(NT) k4_cross_tile_unions(K4Args a) {
   const SceneWs& ws = a.ws;
   const int t = blockIdx.x, tid = threadIdx.x;
   const int a_t = ws.t_a[t];
-  if (a_t == 0) return;
+  if (a_t == 0 || *ws.status != ST_OK) return;
   const int dstart = ws.t_dstart[t];
   if (tid == 0) s_nseg = ws.t_nseg[t];
   if (tid < SEGK) {

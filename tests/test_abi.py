@@ -31,7 +31,7 @@ def test_header_declares_entry_points():
     names = declared_functions()
     for n in ("tb_workspace_size", "tb_match_parens", "tb_bboxes", "tb_bboxes_batched",
               "tb_tree_scan", "tb_tree_scan_affine_backward", "tb_set_phase_events",
-              "tb_version"):
+              "tb_debug_withhold_tile", "tb_version"):
         assert n in names
 
 
@@ -81,6 +81,8 @@ def test_argument_errors_before_any_launch(lib):
     assert lib.tb_bboxes(p(fake), p(fake), 1 << 31, None, None, p(fake), p(fake), 1 << 40, p(fake),
                          None) == b.TB_ERR_INVALID_ARG
     assert lib.tb_set_phase_events(None, 0) == b.TB_OK
+    assert lib.tb_debug_withhold_tile(-2) == b.TB_ERR_INVALID_ARG
+    assert lib.tb_debug_withhold_tile(-1) == b.TB_OK
 
 
 def test_tree_scan_argument_errors(lib):
