@@ -796,8 +796,18 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
   float4 o_cx = box_universe();
   int4 pg = make_int4(-1, -1, -1, -1), mg = make_int4(-1, -1, -1, -1);
 #pragma unroll 1
-  for (int i = 0; i < KPT; ++i) {
-    const int k = (int)((kpack >> (4 * i)) & 15ull);
+  for (int g = 0; g < KPT / 4; ++g) {
+    // the group's 4-bit fields, so that the element loop below shifts by
+    // compile-time amounts
+    const unsigned gk = (unsigned)(kpack >> (16 * g)) & 0xffffu;
+    const unsigned gpar = (unsigned)(lpar >> (16 * g)) & 0xffffu;
+    const unsigned gmate = (unsigned)(lmate >> (16 * g)) & 0xffffu;
+    const unsigned gA = (unsigned)(lA >> (16 * g)) & 0xffffu;
+    const unsigned gB = (unsigned)(lB >> (16 * g)) & 0xffffu;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = 4 * g + q;
+    const int k = (int)((gk >> (4 * q)) & 15u);
     const unsigned bit = 1u << i;
     const int p = p0 + i;
     const int e = base + p;
@@ -813,7 +823,7 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
         }
         if (e == sc_start && dstart_t + D != 0) atomic_cas_i32(a.status, ST_OK, ST_UNBALANCED);
       }
-      const int lp = (int)((lpar >> (4 * i)) & 15ull);
+      const int lp = (int)((gpar >> (4 * q)) & 15u);
       int par = base + p0 + lp;
       float4 cx = top_clip;
       if (!(inside & bit)) {
@@ -833,7 +843,7 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
         cx = o_cx;
       }
       par_i = par;
-      if (pairm & bit) mat_i = base + p0 + (int)((lmate >> (4 * i)) & 15ull);
+      if (pairm & bit) mat_i = base + p0 + (int)((gmate >> (4 * q)) & 15u);
       else if (k == K_CLOSE) mat_i = par;
       if (HAS_BOX) {
         float4* b = &s_box[box_slot(p)];
@@ -852,11 +862,11 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
             *b = U;
             cur_acc = box_empty();
             if (cl_gin & bit) {
-              const int gp = (int)((lA >> (4 * i)) & 15ull);
+              const int gp = (int)((gA >> (4 * q)) & 15u);
               const float4 g = s_box[box_slot(p0 + gp)];
               top_clip = (cl_gum & bit) ? box_isect(Bx, g) : g;
               if (cl_gpair & bit)
-                cur_acc = box_unite(s_box[box_slot(p0 + (int)((lB >> (4 * i)) & 15ull))], U);
+                cur_acc = box_unite(s_box[box_slot(p0 + (int)((gB >> (4 * q)) & 15u))], U);
             }
           } else {
             *b = pre;  // matches an open before the chunk: everything before it is inside
@@ -870,7 +880,7 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
             *b = clip;  // read back when a close returns to this open
           }
           top_clip = clip;
-          if (savem & bit) s_box[box_slot(p0 + (int)((lA >> (4 * i)) & 15ull))] = cur_acc;
+          if (savem & bit) s_box[box_slot(p0 + (int)((gA >> (4 * q)) & 15u))] = cur_acc;
           if (pairm & bit) cur_acc = box_empty();
         }
       }
@@ -881,15 +891,10 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
       D += kind_delta(k);
     }
     bcur = bnext;
-    const int q = i & 3;
-    pg.x = q == 0 ? par_i : pg.x;
-    pg.y = q == 1 ? par_i : pg.y;
-    pg.z = q == 2 ? par_i : pg.z;
-    pg.w = q == 3 ? par_i : pg.w;
-    mg.x = q == 0 ? mat_i : mg.x;
-    mg.y = q == 1 ? mat_i : mg.y;
-    mg.z = q == 2 ? mat_i : mg.z;
-    mg.w = q == 3 ? mat_i : mg.w;
+    if (q == 0) { pg.x = par_i; mg.x = mat_i; }
+    if (q == 1) { pg.y = par_i; mg.y = mat_i; }
+    if (q == 2) { pg.z = par_i; mg.z = mat_i; }
+    if (q == 3) { pg.w = par_i; mg.w = mat_i; }
     if (q == 3) {
       // parent / match of four elements (opens matched outside the chunk get
       // -1 here; their close writes the real value later)
@@ -909,6 +914,7 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
         }
       }
     }
+  }
   }
   __syncthreads();  // every walk has finished; relative clips are no longer read
 
