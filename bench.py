@@ -287,6 +287,18 @@ def run_tree(args, torch, world, rank, dev):
             raise binding.TBError(rc, "backward")
 
     graph = None
+    if not batched:
+        # the plain forward + backward calls, captured once in a CUDA graph
+        fwd()
+        bwd()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            rc1 = binding.tb_tree_scan(binding.TB_MONOID_AFFINE3X4_F32, binding.TB_DOWN, k_d, n, J,
+                                       L_d, world_d, ws, nb, status, None)
+            rc2 = binding.tb_tree_scan_affine_backward(k_d, n, J, L_d, W_d, grad_d, ws, nb, status,
+                                                       None)
+        assert rc1 == binding.TB_OK and rc2 == binding.TB_OK
     if batched:
         # forward + backward through the autograd function, one graph
         bws = binding.workspace(dev)
@@ -367,8 +379,30 @@ def run_tree(args, torch, world, rank, dev):
                 for j, nm in enumerate(names)}
     fph = spans(ev_f, fnames)
     bph = spans(ev_b, bnames)
-    fwd_ms = statistics.mean(ev_f[i][0].elapsed_time(ev_f[i][nf - 1]) for i in range(K))
-    bwd_ms = statistics.mean(ev_b[i][0].elapsed_time(ev_b[i][nbk - 1]) for i in range(K))
+    fwd_calls_ms = statistics.mean(ev_f[i][0].elapsed_time(ev_f[i][nf - 1]) for i in range(K))
+    bwd_calls_ms = statistics.mean(ev_b[i][0].elapsed_time(ev_b[i][nbk - 1]) for i in range(K))
+
+    # forward and backward each captured alone and replayed: their launches
+    # without host gaps (the roofline fractions use these)
+    def graph_ms(call):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            call(None)
+        g.replay()
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(K):
+            g.replay()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / K
+    fwd_ms = graph_ms(lambda st: binding.tb_tree_scan(binding.TB_MONOID_AFFINE3X4_F32, binding.TB_DOWN,
+                                                      k_d, n, J, L_d, world_d, ws, nb, status, st))
+    bwd_ms = graph_ms(lambda st: binding.tb_tree_scan_affine_backward(k_d, n, J, L_d, W_d, grad_d, ws,
+                                                                      nb, status, st))
+    assert int(status.item()) == binding.TB_OK
 
     per_scene = None
     if batched:
@@ -443,7 +477,8 @@ def run_tree(args, torch, world, rank, dev):
             "config": {"workload": WORKLOADS[args.workload], "n": n, "joints": J, "seed": 0,
                        "gjoint_per_s": round(world * J / (ms_step * 1e-3) / 1e9, 3),
                        "step": "one CUDA graph of TreeTransform forward + backward" if batched
-                               else "tb_tree_scan (affine DOWN) + tb_tree_scan_affine_backward",
+                               else "one CUDA graph of tb_tree_scan (affine DOWN) + "
+                                    "tb_tree_scan_affine_backward",
                        "l2": "inputs larger than L2, no flush" if 98 * J > 130e6 else
                              "inputs (%.0f MB) L2-resident, no flush" % (98 * J / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -454,6 +489,7 @@ def run_tree(args, torch, world, rank, dev):
                          "algorithmic_bytes_per_launch": bwd_alg},
             "forward_roofline_frac": round(FWD_BYTES_PER_JOINT * J / (fwd_ms * 1e-3) / 1e9 / peak, 4),
             "forward_ms": round(fwd_ms, 4), "backward_ms": round(bwd_ms, 4),
+            "forward_backward_plain_calls_ms": [round(fwd_calls_ms, 4), round(bwd_calls_ms, 4)],
             "backward_gjoint_per_s": round(J / (bwd_ms * 1e-3) / 1e9, 3),
             "phases_ms": {"forward": {k: round(v, 4) for k, v in fph.items()},
                           "backward": {k: round(v, 4) for k, v in bph.items()}},

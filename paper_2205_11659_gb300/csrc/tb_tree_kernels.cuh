@@ -109,6 +109,17 @@ __host__ __device__ __forceinline__ Aff aff_add(const Aff& a, const Aff& b) {
   c.r2 = f4_add(a.r2, b.r2);
   return c;
 }
+__device__ __forceinline__ float4 shfl_idx(float4 v, int src) {
+  return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                     __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+__device__ __forceinline__ Aff shfl_idx(const Aff& a, int src) {
+  Aff b;
+  b.r0 = shfl_idx(a.r0, src);
+  b.r1 = shfl_idx(a.r1, src);
+  b.r2 = shfl_idx(a.r2, src);
+  return b;
+}
 __device__ __forceinline__ Aff shfl_up(const Aff& a, int d) {
   Aff b;
   b.r0 = shfl_up(a.r0, d);
@@ -407,16 +418,12 @@ __global__ void __launch_bounds__(NT) k_jstruct(TreeWs w, const void* __restrict
   __shared__ int s_rep[JT];
   __shared__ int s_q[2 * JT];
   __shared__ int s_nq;
-  __shared__ V s_scr[NW + 1];
-  __shared__ int s_first;
+  __shared__ int s_scri[NW + 1];
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT, R1 = R0 + JT;
   const int cnt = min(JT, w.J - R0);
   for (int k = tid; k < JT; k += NT) s_tree[JT + k] = k < cnt ? w.jdepth[R0 + k] : INT_MAX;
-  if (tid == 0) {
-    s_first = JT;
-    s_nq = 0;
-  }
+  if (tid == 0) s_nq = 0;
   __syncthreads();
   for (int h = JT / 2; h >= 1; h >>= 1) {
     for (int i = h + tid; i < 2 * h; i += NT) {
@@ -534,31 +541,36 @@ __global__ void __launch_bounds__(NT) k_jstruct(TreeWs w, const void* __restrict
     if (end[i] > R1) xm |= 1u << i;
   }
   if (CHAIN) {
-    V agg = M::identity();
+    // The exported joints of the tile form one chain: list them in order in
+    // shared memory, then one warp folds the list 32 links at a time.
+    int nx_all;
+    const int off = block_excl_scan(popc(xm), 0, OpAdd(), s_scri, &nx_all);
+    {
+      int o = off;
 #pragma unroll
-    for (int i = 0; i < JC; ++i)
-      if (xm & (1u << i)) agg = M::combine(agg, M::load(in, R0 + tid * JC + i));
-    if (xm) atomicMin(&s_first, tid * JC + lowest_set(xm));
-    V tot;
-    V acc = block_excl_scan(agg, M::identity(), MonoidOp<M>(), s_scr, &tot);
-#pragma unroll
-    for (int i = 0; i < JC; ++i) {
-      if (xm & (1u << i)) {
-        const int r = R0 + tid * JC + i;
-        acc = M::combine(acc, M::load(in, r));
-        M::store(w.relT, r, acc);
-      }
+      for (int i = 0; i < JC; ++i)
+        if (xm & (1u << i)) s_q[o++] = tid * JC + i;
     }
-    // block_excl_scan ended with a barrier, so s_first is final
-    const int f = s_first;
-    if (f == JT) {
-      if (tid == 0) w.t_base[t] = NO_CHAIN;
-    } else if (f / JC == tid) {
+    if (xm != 0u && off == 0) {
+      // the chain's first link; its parent is the chain's base
       int pv = -1;
 #pragma unroll
       for (int i = 0; i < JC; ++i)
-        if (i == f % JC) pv = par[i];
+        if (i == lowest_set(xm)) pv = par[i];
       w.t_base[t] = pv;
+    }
+    if (nx_all == 0 && tid == 0) w.t_base[t] = NO_CHAIN;
+    __syncthreads();
+    if (warp_id() == 0) {
+      const int lane = lane_id();
+      V carry = M::identity();
+      for (int b = 0; b < nx_all; b += 32) {
+        const int idx = b + lane;
+        V v = idx < nx_all ? M::load(in, R0 + s_q[idx]) : M::identity();
+        v = M::combine(carry, warp_incl_scan(v, MonoidOp<M>()));
+        if (idx < nx_all) M::store(w.relT, R0 + s_q[idx], v);
+        carry = shfl_idx(v, 31);
+      }
     }
   }
 }
