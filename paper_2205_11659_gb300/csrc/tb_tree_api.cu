@@ -186,7 +186,7 @@ tb_status launch_up(const TreeWs& w, Values values, void* out, Finish fin, cudaS
   k_up_tiles<M><<<1, 1024, 0, s>>>(w);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   tb_internal::phase_mark(s);
-  k_up_cross<M, Finish><<<grid_for(w.TJ * 64, 256), 256, 0, s>>>(w, out, fin);
+  k_up_cross<M, Values, Finish><<<grid_for(w.TJ * 64, 256), 256, 0, s>>>(w, values, out, fin);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   return TB_OK;
 }

@@ -918,9 +918,11 @@ __global__ void __launch_bounds__(NT, 2) k_up_tile(TreeWs w, Values values, void
   const V pre = block_excl_scan(tot, M::identity(), MonoidOp<M>(), s_scr, &all);
   M::store(w.cpre, (int64_t)t * (NCH + 1) + tid, pre);
   if (tid == 0) M::store(w.cpre, (int64_t)t * (NCH + 1) + NCH, all);
+  // Store the folds (with a finish, only the partial folds of the subtrees
+  // leaving the tile are needed later; the others are finished here).
   for (int k = tid; k < cnt; k += NT) {
     const V A = s_val[jslot(k)];
-    M::store(out, R0 + k, A);
+    if (!Finish::active || s_end[k] > JT) M::store(out, R0 + k, A);
     if (Finish::active && s_end[k] <= JT) fin(w, R0 + k, A);
   }
 }
@@ -945,8 +947,8 @@ __global__ void __launch_bounds__(1024) k_up_tiles(TreeWs w) {
 // Completes the folds of the subtrees that leave their tile: the partial fold
 // written by k_up_tile, the whole tiles in between, and the prefix of the
 // tile where the subtree ends.
-template <class M, class Finish>
-__global__ void k_up_cross(TreeWs w, void* __restrict__ out, Finish fin) {
+template <class M, class Values, class Finish>
+__global__ void k_up_cross(TreeWs w, Values values, void* __restrict__ out, Finish fin) {
   using V = typename M::V;
   const int count = (int)*w.xcount;
   const void* tree = w.t_tree;
@@ -962,7 +964,9 @@ __global__ void k_up_cross(TreeWs w, void* __restrict__ out, Finish fin) {
     if (e > R2) {
       const int c2 = (e - R2) / JC;
       acc = M::combine(acc, M::load(w.cpre, (int64_t)t2 * (NCH + 1) + c2));
-      for (int j = R2 + c2 * JC; j < e; j = w.jend[j]) acc = M::combine(acc, M::load(out, j));
+      // the joints of the end tile's chunk c2 before e (fewer than JC), from
+      // their values: the fold over a range is the fold of its elements
+      for (int j = R2 + c2 * JC; j < e; ++j) acc = M::combine(acc, values(j));
     }
     if (Finish::active) fin(w, r, acc);
     else M::store(out, r, acc);
