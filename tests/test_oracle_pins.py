@@ -171,6 +171,29 @@ def test_stack_slice_is_bic_with_indices():
             assert after[o:].min() >= after[o]
 
 
+def test_bic_and_stack_laws():
+    """Sec. 3 and Sec. 4 laws on random strings: Bic is a monoid homomorphism
+    (Bic(st) = Bic(s) . Bic(t), identity (0, 0)); the stack slice combines
+    by dropping the first a(t) unmatched opens from the top of s's slice and
+    appending t's (shifted); Bic(s[i..j]).b never grows as i moves right."""
+    rng = np.random.default_rng(11)
+    assert oracle.bic(np.zeros(0, np.uint8)) == (0, 0)
+    for _ in range(300):
+        s = rng.choice([0, 1, 2, 3], size=int(rng.integers(0, 30))).astype(np.uint8)
+        t = rng.choice([0, 1, 2, 3], size=int(rng.integers(0, 30))).astype(np.uint8)
+        st = np.concatenate([s, t])
+        assert oracle.bic(st) == bic_cat(oracle.bic(s), oracle.bic(t))
+        a_s, ls = oracle.stack_slice(s)
+        a_t, lt = oracle.stack_slice(t)
+        a_st, lst = oracle.stack_slice(st)
+        keep = max(len(ls) - a_t, 0)
+        assert a_st == a_s + max(a_t - len(ls), 0)
+        assert list(lst) == list(ls[:keep]) + [int(i) + len(s) for i in lt]
+        j = len(st)
+        bs = [oracle.bic(st[i:j])[1] for i in range(j + 1)]
+        assert all(x >= y for x, y in zip(bs, bs[1:]))
+
+
 # --- matching -------------------------------------------------------------
 
 def test_matching_exhaustive_small():
