@@ -588,6 +588,30 @@ def run_ours(args):
               for j, nm in enumerate(names)}
     value = world * n / (ms_step * 1e-3) / 1e9
 
+    # ---- the same step captured once in a CUDA graph and replayed (what a
+    # caller repeating the pass would do; at small sizes launch latency
+    # dominates the plain calls)
+    gstep = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gstep):
+        if offsets is None:
+            rcg = binding.tb_bboxes(k_d, b_d, n, parent, match, box_out, ws, nb, status, None)
+        else:
+            rcg = binding.tb_bboxes_batched(k_d, b_d, off_d, S, n, parent, match, box_out, ws, nb,
+                                            status, None)
+    assert rcg == binding.TB_OK
+    gstep.replay()
+    torch.cuda.synchronize()
+    assert int(status.item()) == binding.TB_OK
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(K):
+        gstep.replay()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    graph_step_ms = g0.elapsed_time(g1) / K
+    del gstep
+
     # ---- batched: the same scenes as separate plain calls, same outputs
     per_scene = None
     if offsets is not None:
@@ -710,6 +734,9 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": BYTES_PER_ELEM * n},
             "step_roofline_frac": round(BYTES_PER_ELEM * n / (ms_step * 1e-3) / 1e9 / peak, 4),
             "phases_ms": {k: round(v, 4) for k, v in phases.items()},
+            "graph": {"ms_per_step": round(graph_step_ms, 4),
+                      "value": round(world * n / (graph_step_ms * 1e-3) / 1e9, 3),
+                      "unit": "Gelem/s", "note": "the same step replayed as one CUDA graph"},
             "per_scene": per_scene,
             "cpu_baseline": cpu,
             "e2e": {"value": round(world * n / e2e_s / 1e9, 3), "unit": "Gelem/s",
