@@ -154,6 +154,22 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def job_time_ms(ms_local, world, device):
+    """Whole-job duration of a timed region: the maximum over the ranks."""
+    if world <= 1:
+        return ms_local
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms_step):
+    """Whole-job throughput in G units/s: every rank processes its own copy
+    of the workload (replicas, weak scaling)."""
+    return world * units_per_rank / (ms_step * 1e-3) / 1e9
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -354,13 +370,9 @@ def run_tree(args, torch, world, rank, dev):
     binding.tb_set_phase_events(None)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = job_time_ms(ev0.elapsed_time(ev1), world, dev)
     ms_step = ms_total / K
-    value = world * n / (ms_step * 1e-3) / 1e9
+    value = job_rate(n, world, ms_step)
 
     # per-kernel times of the plain calls (event pairs in launch order)
     fnames = ["depth", "minmax", "min_tree", "jstruct_chain", "down_tiles", "down_tile"]
@@ -576,17 +588,13 @@ def run_ours(args):
     binding.tb_set_phase_events(None)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = job_time_ms(ev0.elapsed_time(ev1), world, dev)
     ms_step = ms_total / K
     assert int(status.item()) == binding.TB_OK
     names = ["k1_tile_summary", "k2_tile_resolve", "k3_tile", "k4_cross_tile_unions"]
     phases = {nm: statistics.mean(phase[i][j].elapsed_time(phase[i][j + 1]) for i in range(K))
               for j, nm in enumerate(names)}
-    value = world * n / (ms_step * 1e-3) / 1e9
+    value = job_rate(n, world, ms_step)
 
     # ---- the same step captured once in a CUDA graph and replayed (what a
     # caller repeating the pass would do; at small sizes launch latency
