@@ -128,8 +128,8 @@ tb_status tb_bboxes_batched(const uint8_t* kind, const float* box,
  * idempotent required).  Values belong to the opens ("joints"): joint r is
  * the r-th open of the stream (pre-order rank), leaves carry none.
  * num_joints must equal the number of opens (at most n / 2); in and out hold
- * num_joints values of the monoid's type (4, 16 or 48 bytes each) and must
- * not overlap.
+ * num_joints values of the monoid's type (4, 16 or 48 bytes each), are
+ * 16-byte aligned whatever the monoid, and must not overlap.
  *   TB_DOWN: out[r] = in[root] * ... * in[parent(r)] * in[r]
  *            (ancestor on the left; for transforms, world = parent world
  *            times local).

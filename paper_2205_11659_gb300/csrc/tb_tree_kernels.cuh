@@ -64,6 +64,8 @@ constexpr int NO_CHAIN = -2;   // tile without exported joints
 constexpr int kMaxJumpRounds = 40;
 constexpr int ST_INVALID = 1;  // TB_ERR_INVALID_ARG
 
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
 // ------------------------------------------------------------- monoids
 // A 3x4 affine transform [R | t] acting on column vectors, stored as three
 // rows (R_i0, R_i1, R_i2, t_i).
@@ -434,41 +436,96 @@ __global__ void __launch_bounds__(NT) k_jstruct(TreeWs w, const void* __restrict
   }
   // In the tile: parent = the previous joint if it is shallower, else the
   // last shallower joint (tree search); end = the next joint if it is not
-  // deeper, else the first later joint not deeper (tree search).  What the
-  // tile cannot answer goes to a queue served by whole warps below.  All
-  // joints of the tile at depth d whose parent lies before the tile share
-  // that parent (the stack entry at depth d-1 at the tile start), so only
-  // the first joint of the tile at or above depth d (its representative)
-  // queues the question; s_rep maps a representative to its queue slot.
+  // deeper, else the first later joint not deeper (tree search).
   int par[JC], end[JC], dep[JC], rep[JC];
+  // The JC searches of each kind run in lockstep with fixed trip counts, so
+  // their dependent shared-memory loads overlap.
+  int pl[JC], pr[JC], pn[JC];  // parent: last earlier leaf <= d-1 (climb, then descend)
+  int en[JC];                  // end: first later leaf <= d (0 = none)
+  bool ef[JC];
 #pragma unroll
   for (int i = 0; i < JC; ++i) {
     const int k = tid * JC + i;
-    par[i] = -1;
-    end[i] = -1;
-    rep[i] = -1;
+    par[i] = end[i] = rep[i] = -1;
     dep[i] = k < cnt ? s_tree[JT + k] : INT_MAX;
+    const int d = dep[i];
+    // shortcuts: the previous joint is the parent when shallower, the next
+    // joint is the end when not deeper
+    const bool pdone = k >= cnt || k == 0 || s_tree[JT + k - 1] < d;
+    if (k < cnt && k > 0 && s_tree[JT + k - 1] < d) par[i] = R0 + k - 1;
+    pl[i] = JT;
+    pr[i] = pdone ? JT : JT + k;  // empty range when done
+    pn[i] = -1;
+    const bool edone = k >= cnt || (k + 1 < cnt && s_tree[JT + k + 1] <= d);
+    if (k < cnt && k + 1 < cnt && s_tree[JT + k + 1] <= d) end[i] = R0 + k + 1;
+    en[i] = (!edone && k + 1 < JT) ? JT + k + 1 : 0;
+    ef[i] = false;
+  }
+  constexpr int LOGJT = ilog2(JT);
+  for (int it = 0; it <= LOGJT; ++it) {
+#pragma unroll
+    for (int i = 0; i < JC; ++i) {
+      if (pn[i] < 0 && pl[i] < pr[i]) {
+        if (pr[i] & 1) {
+          --pr[i];
+          if (s_tree[pr[i]] <= dep[i] - 1) pn[i] = pr[i];
+        }
+        if (pn[i] < 0) {
+          pl[i] >>= 1;
+          pr[i] >>= 1;
+        }
+      }
+    }
+  }
+  for (int it = 0; it < 2 * LOGJT + 1; ++it) {
+#pragma unroll
+    for (int i = 0; i < JC; ++i) {
+      if (en[i] > 0 && !ef[i]) {
+        if (s_tree[en[i]] <= dep[i]) {
+          ef[i] = true;
+        } else {
+          // next subtree to the right: drop the trailing right-child steps
+          const int t1 = lowest_set(~(unsigned)en[i]);
+          const int up = en[i] >> t1;
+          en[i] = up == 0 ? 0 : up + 1;
+        }
+      }
+    }
+  }
+  for (int it = 0; it < LOGJT; ++it) {
+#pragma unroll
+    for (int i = 0; i < JC; ++i) {
+      if (pn[i] >= 1 && pn[i] < JT) pn[i] = s_tree[2 * pn[i] + 1] <= dep[i] - 1 ? 2 * pn[i] + 1 : 2 * pn[i];
+      if (ef[i] && en[i] < JT) en[i] = s_tree[2 * en[i]] <= dep[i] ? 2 * en[i] : 2 * en[i] + 1;
+    }
+  }
+  // What the tile cannot answer goes to a queue served below.  All joints of
+  // the tile at depth d whose parent lies before the tile share that parent
+  // (the stack entry at depth d-1 at the tile start), so only the first
+  // joint of the tile at or above depth d (its representative) queues the
+  // question; s_rep maps a representative to its queue slot.
+#pragma unroll
+  for (int i = 0; i < JC; ++i) {
+    const int k = tid * JC + i;
     if (k >= cnt) continue;
     const int d = dep[i];
-    int p;
-    if (k > 0 && s_tree[JT + k - 1] < d) p = k - 1;
-    else p = tree_last_le(s_tree, JT, k, d - 1);
-    if (p >= 0) {
-      par[i] = R0 + p;
-    } else if (d > 1) {
-      rep[i] = tree_first_le(s_tree, JT, 0, d);
-      if (rep[i] == k) s_rep[k] = atomicAdd(&s_nq, 1);
-      if (rep[i] == k) s_q[s_rep[k]] = k;
+    if (par[i] < 0) {
+      if (pn[i] >= 0) {
+        par[i] = R0 + pn[i] - JT;
+      } else if (d > 1) {
+        rep[i] = tree_first_le(s_tree, JT, 0, d);
+        if (rep[i] == k) s_rep[k] = atomicAdd(&s_nq, 1);
+        if (rep[i] == k) s_q[s_rep[k]] = k;
+      }
     }
-    int e;
-    if (k + 1 < cnt && s_tree[JT + k + 1] <= d) e = k + 1;
-    else e = tree_first_le(s_tree, JT, k + 1, d);
-    if (e >= 0) {
-      end[i] = R0 + e;
-    } else {
-      const int slot = atomicAdd(&s_nq, 1);
-      s_q[slot] = k | (1 << 30);
-      end[i] = -2 - slot;
+    if (end[i] < 0) {
+      if (ef[i]) {
+        end[i] = R0 + en[i] - JT;
+      } else {
+        const int slot = atomicAdd(&s_nq, 1);
+        s_q[slot] = k | (1 << 30);
+        end[i] = -2 - slot;
+      }
     }
   }
   __syncthreads();
