@@ -94,6 +94,10 @@ def kernel_hash():
     for f in sorted(os.listdir(csrc)):
         if f.endswith((".cu", ".cuh")):
             h.update(open(os.path.join(csrc, f), "rb").read())
+    from paper_2205_11659_gb300 import _build
+    nt, kpt = _build.tuned_shape()
+    if (nt, kpt) != (256, 16):
+        h.update(b"shape %d %d" % (nt, kpt))
     return h.hexdigest()[:16]
 
 

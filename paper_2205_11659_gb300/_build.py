@@ -3,7 +3,8 @@
 ``nvcc -gencode arch=compute_103a,code=sm_103a -lineinfo -O3`` for every
 ``csrc/*.cu`` translation unit (in parallel), then one ``nvcc -shared`` link
 into ``_build/libtb.so``.  Rebuilds only when a source or header is newer than
-the library.
+the library.  The tile shape of the scene kernels (threads per block, elements
+per thread) comes from ``tuned_shape.json``, written by ``autotune.py``.
 """
 import glob
 import os
@@ -17,6 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libtb.so")
+SHAPE_FILE = os.path.join(PKG, "tuned_shape.json")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -36,30 +38,48 @@ def _sources():
 
 
 def _deps():
-    return (_sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+    deps = (_sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
             glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
+    if os.path.exists(SHAPE_FILE):
+        deps.append(SHAPE_FILE)
+    return deps
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def tuned_shape():
+    """(threads per block, elements per thread) of the scene kernels."""
+    import json
+    if os.path.exists(SHAPE_FILE):
+        with open(SHAPE_FILE) as f:
+            d = json.load(f)
+        return int(d["threads_per_block"]), int(d["elements_per_thread"])
+    return 256, 16
+
+
+def up_to_date(lib=LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force=False, verbose=False):
-    """Build _build/libtb.so if needed; returns its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force=False, verbose=False, shape=None, out_dir=None):
+    """Build the library if needed; returns its path.  shape = (threads per
+    block, elements per thread) overrides the tuned shape and out_dir the
+    output folder (the autotuner builds its candidates that way)."""
+    out_dir = OUT_DIR if out_dir is None else out_dir
+    lib_path = os.path.join(out_dir, "libtb.so")
+    if not force and up_to_date(lib_path):
+        return lib_path
+    os.makedirs(out_dir, exist_ok=True)
     exe = nvcc()
+    nt, kpt = tuned_shape() if shape is None else shape
     common = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-                     "-I" + INCLUDE, "-I" + CSRC]
+                     "-I" + INCLUDE, "-I" + CSRC, "-DTB_NT=%d" % nt, "-DTB_KPT=%d" % kpt]
     if verbose:
         common += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [exe] + common + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -71,13 +91,13 @@ def build(force=False, verbose=False):
     srcs = _sources()
     with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib_path + ".%d.tmp" % os.getpid()
     cmd = [exe] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -1,0 +1,153 @@
+"""Autotuner of the scene kernels' tile shape.
+
+    python -m paper_2205_11659_gb300.autotune [--write]
+
+Builds the library once per candidate (threads per block, elements per
+thread), checks each build bit for bit against the build with the current
+tuned shape (the one the test suite checks against the oracle) on scenes
+that span several tiles and a ragged tail and on a batch of scenes, times
+the bounding-box pass with CUDA events on a 2^24-element random-walk scene
+and on a batch of 512 scenes, and reports every candidate.  With --write the
+fastest correct one goes to tuned_shape.json, which the build uses from then
+on.  Needs a CUDA GPU.
+"""
+import argparse
+import json
+import os
+import statistics
+import sys
+import time
+
+import numpy as np
+
+from . import _build
+
+CANDIDATES = [(256, 16), (256, 8), (128, 16), (512, 8)]
+
+
+def _time_calls(call, reps):
+    import torch
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for a, b in ev:
+        a.record()
+        call()
+        b.record()
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+
+def _outputs(binding, dev, checks):
+    """parent, match and box_out of every check case, on the host."""
+    import torch
+    res = []
+    for k, b, off in checks:
+        kd, bd = torch.from_numpy(k).to(dev), torch.from_numpy(b).to(dev)
+        if off is None:
+            p, m, o = binding.bboxes(kd, bd)
+        else:
+            p, m, o = binding.bboxes_batched(kd, bd, torch.from_numpy(off).to(dev))
+        res.append((p.cpu().numpy(), m.cpu().numpy(), o.cpu().numpy().view(np.uint32)))
+    return res
+
+
+def evaluate(shape, scenes, checks, reference):
+    """(outputs of the check cases, ms per pass per scene); ms is None when
+    the outputs differ from the reference."""
+    import torch
+    from . import binding
+    lib_path = _build.build(shape=shape, out_dir=os.path.join(_build.OUT_DIR, "tune_%d_%d" % shape))
+    saved = _build.LIB
+    binding._lib = None
+    _build.LIB = lib_path
+    try:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        outs = _outputs(binding, dev, checks)
+        if reference is not None:
+            for got, want in zip(outs, reference):
+                if not all(np.array_equal(g, w) for g, w in zip(got, want)):
+                    return outs, None
+        times = {}
+        for name, (kd, bd, od) in scenes.items():
+            n = kd.numel()
+            parent = torch.empty(n, dtype=torch.int32, device=dev)
+            match = torch.empty(n, dtype=torch.int32, device=dev)
+            box_out = torch.empty(n, 4, dtype=torch.float32, device=dev)
+            ws = binding.workspace(dev)
+            if od is None:
+                nb = binding.tb_workspace_size(binding.TB_OP_BBOXES, n)
+                buf = ws.get(nb)
+
+                def call():
+                    return binding.tb_bboxes(kd, bd, n, parent, match, box_out, buf, nb, ws.status)
+            else:
+                S = od.numel() - 1
+                nb = binding.tb_workspace_size(binding.TB_OP_BBOXES_BATCHED, n, S)
+                buf = ws.get(nb)
+
+                def call():
+                    return binding.tb_bboxes_batched(kd, bd, od, S, n, parent, match, box_out, buf,
+                                                     nb, ws.status)
+            times[name] = round(_time_calls(call, 10), 4)
+            binding.check_status(ws, "autotune " + name)
+        return outs, times
+    finally:
+        binding._lib = None
+        _build.LIB = saved
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--write", action="store_true")
+    args = ap.parse_args(argv)
+    import torch
+    from . import inputs
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    k, b = inputs.random_walk_scene(1 << 24, 0)
+    kb, bb, off = inputs.batched_scenes(512, 0)
+    scenes = {"rw24": (torch.from_numpy(k).to(dev), torch.from_numpy(b).to(dev), None),
+              "batch512": (torch.from_numpy(kb).to(dev), torch.from_numpy(bb).to(dev),
+                           torch.from_numpy(off).to(dev))}
+    # check cases: several tiles of every candidate and a ragged tail, and a
+    # batch of scenes
+    checks = []
+    for n, seed in ((1, 1), (4 * 8192 + 777, 2), (40 * 4096 + 5, 3)):
+        kk, bx = inputs.random_walk_scene(n, seed)
+        checks.append((kk, bx, None))
+    checks.append(inputs.batched_scenes(64, 4, 4.0, 14.0))
+    current = _build.tuned_shape()
+    order = [current] + [c for c in CANDIDATES if c != current]
+    reference = None
+    results = []
+    for shape in order:
+        t0 = time.time()
+        outs, ms = evaluate(shape, scenes, checks, reference)
+        if reference is None:
+            reference = outs  # the current shape, which the tests check against the oracle
+        results.append({"threads_per_block": shape[0], "elements_per_thread": shape[1],
+                        "correct": ms is not None, "ms": ms,
+                        "seconds": round(time.time() - t0, 1)})
+        print(json.dumps(results[-1]), flush=True)
+    ok = [r for r in results if r["correct"]]
+    if not ok:
+        print("no correct candidate", file=sys.stderr)
+        return 1
+    best = min(ok, key=lambda r: r["ms"]["rw24"] + r["ms"]["batch512"])
+    summary = {"threads_per_block": best["threads_per_block"],
+               "elements_per_thread": best["elements_per_thread"],
+               "chosen_by": "autotune.py: fastest correct candidate on rw24 + batch512",
+               "candidates": results}
+    print(json.dumps(summary), flush=True)
+    if args.write:
+        with open(_build.SHAPE_FILE, "w") as f:
+            json.dump(summary, f, indent=1)
+            f.write("\n")
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

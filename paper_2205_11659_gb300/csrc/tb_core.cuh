@@ -16,10 +16,21 @@ namespace tb {
 // A tile is TILE consecutive elements handled by one block of NT threads;
 // thread j owns the KPT consecutive elements [j*KPT, j*KPT + KPT) of the
 // tile (its "chunk").
-constexpr int NT = 256;
-constexpr int KPT = 16;
+// The shape is a build parameter (TB_NT threads per block, TB_KPT elements
+// per thread), chosen among a few candidates by the project's autotuner;
+// 256 x 16 when not given.
+#ifndef TB_NT
+#define TB_NT 256
+#endif
+#ifndef TB_KPT
+#define TB_KPT 16
+#endif
+constexpr int NT = TB_NT;
+constexpr int KPT = TB_KPT;
 constexpr int TILE = NT * KPT;
 constexpr int NW = NT / 32;
+static_assert(NT == 128 || NT == 256 || NT == 512, "block size must be 128, 256 or 512");
+static_assert(KPT == 8 || KPT == 16, "elements per thread must be 8 or 16");
 
 // Element kinds; K_PAD marks positions past the end of the stream.
 constexpr int K_LEAF = 0, K_CLIP = 1, K_BLEND = 2, K_CLOSE = 3, K_PAD = 4;
@@ -90,33 +101,35 @@ __device__ __forceinline__ T warp_incl_scan(T v, Op op) {
   return v;
 }
 
-// Exclusive scan over the NT threads of the block in thread order.  s holds
-// NW + 1 values of scratch; *total receives the fold of all NT inputs.
-template <class T, class Op>
+// Exclusive scan over the threads of the block (NWARPS warps, NW by
+// default) in thread order.  s holds NWARPS + 1 values of scratch; *total
+// receives the fold of all inputs.
+template <int NWARPS = NW, class T, class Op>
 __device__ T block_excl_scan(T v, T ident, Op op, T* s, T* total) {
   const int lane = lane_id(), w = warp_id();
   T incl = warp_incl_scan(v, op);
   if (lane == 31) s[w] = incl;
   __syncthreads();
   if (threadIdx.x < 32) {
-    T wv = threadIdx.x < NW ? s[threadIdx.x] : ident;
+    T wv = threadIdx.x < NWARPS ? s[threadIdx.x] : ident;
     T wi = warp_incl_scan(wv, op);
     T we = shfl_up(wi, 1);
     if (lane == 0) we = ident;
-    if (threadIdx.x < NW) s[threadIdx.x] = we;
-    if (threadIdx.x == 31) s[NW] = wi;
+    if (threadIdx.x < NWARPS) s[threadIdx.x] = we;
+    if (threadIdx.x == 31) s[NWARPS] = wi;
   }
   __syncthreads();
   T ex = shfl_up(incl, 1);
   if (lane == 0) ex = ident;
   T r = op(s[w], ex);
-  *total = s[NW];
+  *total = s[NWARPS];
   __syncthreads();
   return r;
 }
 
-// Exclusive suffix minimum: thread j gets min over threads j+1 .. NT-1
-// (INT_MAX for the last thread).
+// Exclusive suffix minimum: thread j gets min over the later threads of the
+// block (INT_MAX for the last thread).
+template <int NWARPS = NW>
 __device__ __forceinline__ int block_excl_suffix_min(int v, int* s) {
   const int lane = lane_id(), w = warp_id();
   int incl = v;
@@ -129,7 +142,7 @@ __device__ __forceinline__ int block_excl_suffix_min(int v, int* s) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int acc = INT_MAX;
-    for (int i = NW - 1; i >= 0; --i) {
+    for (int i = NWARPS - 1; i >= 0; --i) {
       int x = s[i];
       s[i] = acc;
       acc = acc < x ? acc : x;

@@ -65,6 +65,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // 128-bit read-only loads of input streams (ld.global.nc.v4).
 __device__ __forceinline__ uint4 ld_nc_u4(const void* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+__device__ __forceinline__ uint2 ld_nc_u2(const void* p) { return __ldg(reinterpret_cast<const uint2*>(p)); }
 __device__ __forceinline__ float4 ld_nc_f4(const void* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 
 }  // namespace tb

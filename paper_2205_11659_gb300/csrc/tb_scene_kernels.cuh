@@ -41,8 +41,19 @@ __device__ __forceinline__ bool load_kinds(const uint8_t* __restrict__ kind, int
                                            uint8_t (&kk)[KPT]) {
   bool bad = false;
   if (e0 + KPT <= n) {
-    uint4 v = ld_nc_u4(kind + e0);
-    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+    // one aligned vector load of the chunk's KPT bytes (e0 is a multiple of KPT)
+    unsigned w[KPT / 4];
+    if constexpr (KPT == 16) {
+      const uint4 v = ld_nc_u4(kind + e0);
+      w[0] = v.x;
+      w[1] = v.y;
+      w[2] = v.z;
+      w[3] = v.w;
+    } else {
+      const uint2 v = ld_nc_u2(kind + e0);
+      w[0] = v.x;
+      w[1] = v.y;
+    }
 #pragma unroll
     for (int i = 0; i < KPT; ++i) kk[i] = (uint8_t)((w[i >> 2] >> (8 * (i & 3))) & 0xffu);
 #pragma unroll

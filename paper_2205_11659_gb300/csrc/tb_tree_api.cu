@@ -13,7 +13,7 @@ namespace {
 
 using namespace tb;
 
-constexpr int64_t kMaxN = (int64_t)INT_MAX - TILE;
+constexpr int64_t kMaxN = (int64_t)INT_MAX - TTILE;
 constexpr size_t kValBytes = sizeof(Aff);  // the widest monoid value
 
 constexpr size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -34,7 +34,7 @@ struct TreeLayout {
 
 TreeLayout tree_layout(int64_t n, bool backward) {
   TreeLayout L{};
-  const int TE = (int)((n + TILE - 1) / TILE);
+  const int TE = (int)((n + TTILE - 1) / TTILE);
   const int Jmax = (int)(n / 2);
   const int TJ = (Jmax + JT - 1) / JT;
   const int PJ = next_pow2(TJ > 0 ? TJ : 1);
@@ -131,11 +131,11 @@ tb_status prelude(const uint8_t* kind, int64_t n, int J, const TreeLayout& L, vo
   if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return TB_ERR_CUDA;
   if (cudaMemsetAsync(b + L.lb, 0, L.zero_end - L.lb, s) != cudaSuccess) return TB_ERR_CUDA;
   tb_internal::phase_mark(s);
-  k_tdepth<<<L.TE, NT, 0, s>>>(kind, w, d_status);
+  k_tdepth<<<L.TE, TNT, 0, s>>>(kind, w, d_status);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   if (J > 0) {
     tb_internal::phase_mark(s);
-    k_jminmax<<<w.TJ, NT, 0, s>>>(w);
+    k_jminmax<<<w.TJ, TNT, 0, s>>>(w);
     if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
     tb_internal::phase_mark(s);
     k_jmin_tree<<<1, 1024, 0, s>>>(w);
@@ -148,7 +148,7 @@ tb_status prelude(const uint8_t* kind, int64_t n, int J, const TreeLayout& L, vo
 template <class M, bool CHAIN>
 tb_status launch_jstruct(const TreeWs& w, const void* in, cudaStream_t s) {
   tb_internal::phase_mark(s);
-  k_jstruct<M, CHAIN><<<w.TJ, NT, 0, s>>>(w, in);
+  k_jstruct<M, CHAIN><<<w.TJ, TNT, 0, s>>>(w, in);
   return cudaGetLastError() == cudaSuccess ? TB_OK : TB_ERR_CUDA;
 }
 
@@ -166,7 +166,7 @@ tb_status launch_down(const TreeWs& w, const void* in, void* out, int32_t* d_sta
     if (allow_smem(k_down_tile<M>, smem) != cudaSuccess) return TB_ERR_CUDA;
     attr_set = true;
   }
-  k_down_tile<M><<<w.TJ, NT, smem, s>>>(w, in, out);
+  k_down_tile<M><<<w.TJ, TNT, smem, s>>>(w, in, out);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   return TB_OK;
 }
@@ -180,7 +180,7 @@ tb_status launch_up(const TreeWs& w, Values values, void* out, Finish fin, cudaS
     if (allow_smem(k_up_tile<M, Values, Finish>, smem) != cudaSuccess) return TB_ERR_CUDA;
     attr_set = true;
   }
-  k_up_tile<M, Values, Finish><<<w.TJ, NT, smem, s>>>(w, values, out, fin);
+  k_up_tile<M, Values, Finish><<<w.TJ, TNT, smem, s>>>(w, values, out, fin);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   tb_internal::phase_mark(s);
   k_up_tiles<M><<<1, 1024, 0, s>>>(w);

@@ -25,7 +25,7 @@
 //                prefix folds of the tile's exported chain (below)
 //
 // Joints are processed in tiles of JT = 1024 consecutive joints, one block of
-// NT threads each; thread c owns the chunk of JC = 4 joints [c*JC, c*JC+JC).
+// TNT threads each; thread c owns the chunk of JC = 4 joints [c*JC, c*JC+JC).
 //
 // DOWN (root-path fold, ancestor on the left, Sec. 6.1):
 //   * A joint whose subtree runs past the end of its chunk (or tile) is
@@ -57,9 +57,16 @@
 
 namespace tb {
 
+// The tree kernels keep their own shape whatever the scene kernels are
+// built with: blocks of TNT threads, TKPT elements per thread in the depth
+// pass, JC joints per thread in the joint passes.
+constexpr int TNT = 256;
+constexpr int TNW = TNT / 32;
+constexpr int TKPT = 16;
+constexpr int TTILE = TNT * TKPT;
 constexpr int JC = 4;          // joints per thread
-constexpr int JT = NT * JC;    // joints per tile
-constexpr int NCH = NT;        // chunks per tile
+constexpr int JT = TNT * JC;    // joints per tile
+constexpr int NCH = TNT;        // chunks per tile
 constexpr int NO_CHAIN = -2;   // tile without exported joints
 constexpr int kMaxJumpRounds = 40;
 constexpr int ST_INVALID = 1;  // TB_ERR_INVALID_ARG
@@ -220,7 +227,7 @@ struct TreeWs {
   int* xlist;    // joints whose subtree leaves their tile
   int n;         // elements
   int J;         // joints (opens) announced by the caller
-  int TE;        // element tiles (TILE elements each)
+  int TE;        // element tiles (TTILE elements each)
   int TJ;        // joint tiles (JT joints each)
   int PJ;        // next power of two >= TJ
 };
@@ -247,30 +254,30 @@ __device__ __forceinline__ unsigned oc_closes(unsigned long long w) { return (un
 // the earlier tiles (warp 0 polls 32 predecessors at a time).  Also checks
 // the kinds, that the depth never drops below 0, that it ends at 0, and that
 // the stream has exactly J opens.
-__global__ void __launch_bounds__(NT) k_tdepth(const uint8_t* __restrict__ kind, TreeWs w,
+__global__ void __launch_bounds__(TNT) k_tdepth(const uint8_t* __restrict__ kind, TreeWs w,
                                                int* status) {
-  __shared__ int s_scr[NW + 1];
+  __shared__ int s_scr[TNW + 1];
   __shared__ int s_t;
   __shared__ unsigned s_o, s_c;
   const int tid = threadIdx.x;
   if (tid == 0) s_t = (int)atomic_add_u32(w.counter, 1u);
   __syncthreads();
   const int t = s_t;
-  const int64_t e0 = (int64_t)t * TILE + (int64_t)tid * KPT;
-  uint8_t kk[KPT];
-  if (e0 + KPT <= w.n) {
+  const int64_t e0 = (int64_t)t * TTILE + (int64_t)tid * TKPT;
+  uint8_t kk[TKPT];
+  if (e0 + TKPT <= w.n) {
     const uint4 q = ld_nc_u4(kind + e0);
     const uint32_t wds[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-    for (int i = 0; i < KPT; ++i) kk[i] = (uint8_t)(wds[i >> 2] >> (8 * (i & 3)));
+    for (int i = 0; i < TKPT; ++i) kk[i] = (uint8_t)(wds[i >> 2] >> (8 * (i & 3)));
   } else {
 #pragma unroll
-    for (int i = 0; i < KPT; ++i) kk[i] = e0 + i < w.n ? kind[e0 + i] : (uint8_t)K_PAD;
+    for (int i = 0; i < TKPT; ++i) kk[i] = e0 + i < w.n ? kind[e0 + i] : (uint8_t)K_PAD;
   }
   int co = 0, cc = 0, run = 0, mn = 0;
   bool bad = false;
 #pragma unroll
-  for (int i = 0; i < KPT; ++i) {
+  for (int i = 0; i < TKPT; ++i) {
     const int k = kk[i];
     bad |= k > K_CLOSE && k != K_PAD;
     co += kind_open(k) ? 1 : 0;
@@ -280,9 +287,9 @@ __global__ void __launch_bounds__(NT) k_tdepth(const uint8_t* __restrict__ kind,
   }
   if (bad) atomic_cas_i32(status, ST_OK, ST_BAD_KIND);
   int tot_o, tot_c, tile_mn;
-  const int ex_o = block_excl_scan(co, 0, OpAdd(), s_scr, &tot_o);
-  const int ex_c = block_excl_scan(cc, 0, OpAdd(), s_scr, &tot_c);
-  block_excl_scan(ex_o - ex_c + mn, INT_MAX, OpMin(), s_scr, &tile_mn);
+  const int ex_o = block_excl_scan<TNW>(co, 0, OpAdd(), s_scr, &tot_o);
+  const int ex_c = block_excl_scan<TNW>(cc, 0, OpAdd(), s_scr, &tot_c);
+  block_excl_scan<TNW>(ex_o - ex_c + mn, INT_MAX, OpMin(), s_scr, &tile_mn);
   if (warp_id() == 0) {
     const int lane = lane_id();
     unsigned long long* lb = w.lb;
@@ -334,7 +341,7 @@ __global__ void __launch_bounds__(NT) k_tdepth(const uint8_t* __restrict__ kind,
   __syncthreads();
   int o = (int)s_o + ex_o, c = (int)s_c + ex_c;
 #pragma unroll
-  for (int i = 0; i < KPT; ++i) {
+  for (int i = 0; i < TKPT; ++i) {
     const int k = kk[i];
     if (kind_open(k)) {
       if (o < w.J) w.jdepth[o] = o - c + 1;
@@ -346,8 +353,8 @@ __global__ void __launch_bounds__(NT) k_tdepth(const uint8_t* __restrict__ kind,
 }
 
 // Per joint tile: inclusive prefix and suffix minima of jdepth, tile minimum.
-__global__ void __launch_bounds__(NT) k_jminmax(TreeWs w) {
-  __shared__ int s_scr[NW + 1];
+__global__ void __launch_bounds__(TNT) k_jminmax(TreeWs w) {
+  __shared__ int s_scr[TNW + 1];
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT, cnt = min(JT, w.J - R0);
   int d[JC];
@@ -359,8 +366,8 @@ __global__ void __launch_bounds__(NT) k_jminmax(TreeWs w) {
     mn = mn < d[i] ? mn : d[i];
   }
   int all;
-  int pre = block_excl_scan(mn, INT_MAX, OpMin(), s_scr, &all);
-  int suf = block_excl_suffix_min(mn, s_scr);
+  int pre = block_excl_scan<TNW>(mn, INT_MAX, OpMin(), s_scr, &all);
+  int suf = block_excl_suffix_min<TNW>(mn, s_scr);
   int sv[JC];
 #pragma unroll
   for (int i = JC - 1; i >= 0; --i) {
@@ -414,21 +421,21 @@ __device__ __forceinline__ int tree_first_le(const int* tree, int P, int x, int 
 // Parent and subtree end of every joint of the tile; with CHAIN, also the
 // prefix folds of the tile's exported chain (the input of the DOWN scan).
 template <class M, bool CHAIN>
-__global__ void __launch_bounds__(NT) k_jstruct(TreeWs w, const void* __restrict__ in) {
+__global__ void __launch_bounds__(TNT) k_jstruct(TreeWs w, const void* __restrict__ in) {
   using V = typename M::V;
   __shared__ int s_tree[2 * JT];
   __shared__ int s_rep[JT];
   __shared__ int s_q[2 * JT];
   __shared__ int s_nq;
-  __shared__ int s_scri[NW + 1];
+  __shared__ int s_scri[TNW + 1];
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT, R1 = R0 + JT;
   const int cnt = min(JT, w.J - R0);
-  for (int k = tid; k < JT; k += NT) s_tree[JT + k] = k < cnt ? w.jdepth[R0 + k] : INT_MAX;
+  for (int k = tid; k < JT; k += TNT) s_tree[JT + k] = k < cnt ? w.jdepth[R0 + k] : INT_MAX;
   if (tid == 0) s_nq = 0;
   __syncthreads();
   for (int h = JT / 2; h >= 1; h >>= 1) {
-    for (int i = h + tid; i < 2 * h; i += NT) {
+    for (int i = h + tid; i < 2 * h; i += TNT) {
       const int a = s_tree[2 * i], b = s_tree[2 * i + 1];
       s_tree[i] = a < b ? a : b;
     }
@@ -533,7 +540,7 @@ __global__ void __launch_bounds__(NT) k_jstruct(TreeWs w, const void* __restrict
   // first), then the position in that tile's monotone prefix minima (first
   // position <= thr) or suffix minima (last position <= thr) by an 8-way
   // search (eight independent probes per round).
-  for (int qi = tid; qi < s_nq; qi += NT) {
+  for (int qi = tid; qi < s_nq; qi += TNT) {
     const int qv = s_q[qi];
     const bool is_end = ((qv >> 30) & 1) != 0;
     const int k = qv & ((1 << 30) - 1);
@@ -601,7 +608,7 @@ __global__ void __launch_bounds__(NT) k_jstruct(TreeWs w, const void* __restrict
     // The exported joints of the tile form one chain: list them in order in
     // shared memory, then one warp folds the list 32 links at a time.
     int nx_all;
-    const int off = block_excl_scan(popc(xm), 0, OpAdd(), s_scri, &nx_all);
+    const int off = block_excl_scan<TNW>(popc(xm), 0, OpAdd(), s_scri, &nx_all);
     {
       int o = off;
 #pragma unroll
@@ -692,7 +699,7 @@ constexpr size_t down_tile_smem() {
 }
 
 template <class M>
-__global__ void __launch_bounds__(NT, 2) k_down_tile(TreeWs w, const void* __restrict__ in,
+__global__ void __launch_bounds__(TNT, 2) k_down_tile(TreeWs w, const void* __restrict__ in,
                                                      void* __restrict__ out) {
   using V = typename M::V;
   TB_DYNAMIC_SMEM(smem);
@@ -703,7 +710,7 @@ __global__ void __launch_bounds__(NT, 2) k_down_tile(TreeWs w, const void* __res
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT;
   const int cnt = min(JT, w.J - R0);
-  for (int k = tid; k < cnt; k += NT) {
+  for (int k = tid; k < cnt; k += TNT) {
     s_val[jslot(k)] = M::load(in, R0 + k);
     s_anc[k] = w.jparent[R0 + k];
   }
@@ -785,7 +792,7 @@ __global__ void __launch_bounds__(NT, 2) k_down_tile(TreeWs w, const void* __res
     }
   }
   __syncthreads();
-  for (int k = tid; k < cnt; k += NT) M::store(out, R0 + k, s_val[jslot(k)]);
+  for (int k = tid; k < cnt; k += TNT) M::store(out, R0 + k, s_val[jslot(k)]);
 }
 
 // ------------------------------------------------------------- adjoint
@@ -915,22 +922,22 @@ struct AdjointValues {
 template <class M>
 constexpr size_t up_tile_smem() {
   return (size_t)JSLOTS * sizeof(typename M::V) + (size_t)2 * NCH * sizeof(typename M::V) +
-         (size_t)(NW + 1) * sizeof(typename M::V) + (size_t)JT * sizeof(int);
+         (size_t)(TNW + 1) * sizeof(typename M::V) + (size_t)JT * sizeof(int);
 }
 
 template <class M, class Values, class Finish>
-__global__ void __launch_bounds__(NT, 2) k_up_tile(TreeWs w, Values values, void* __restrict__ out,
+__global__ void __launch_bounds__(TNT, 2) k_up_tile(TreeWs w, Values values, void* __restrict__ out,
                                                    Finish fin) {
   using V = typename M::V;
   TB_DYNAMIC_SMEM(smem);
   V* s_val = reinterpret_cast<V*>(smem);
   V* s_tree = s_val + JSLOTS;  // chunk totals at [NCH, 2 NCH)
   V* s_scr = s_tree + 2 * NCH;
-  int* s_end = reinterpret_cast<int*>(s_scr + NW + 1);  // local subtree ends
+  int* s_end = reinterpret_cast<int*>(s_scr + TNW + 1);  // local subtree ends
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT;
   const int cnt = min(JT, w.J - R0);
-  for (int k = tid; k < cnt; k += NT) {
+  for (int k = tid; k < cnt; k += TNT) {
     s_val[jslot(k)] = values(R0 + k);
     s_end[k] = w.jend[R0 + k] - R0;
   }
@@ -972,12 +979,12 @@ __global__ void __launch_bounds__(NT, 2) k_up_tile(TreeWs w, Values values, void
   }
   // Prefix folds over the chunks, for subtrees of earlier tiles ending here.
   V all;
-  const V pre = block_excl_scan(tot, M::identity(), MonoidOp<M>(), s_scr, &all);
+  const V pre = block_excl_scan<TNW>(tot, M::identity(), MonoidOp<M>(), s_scr, &all);
   M::store(w.cpre, (int64_t)t * (NCH + 1) + tid, pre);
   if (tid == 0) M::store(w.cpre, (int64_t)t * (NCH + 1) + NCH, all);
   // Store the folds (with a finish, only the partial folds of the subtrees
   // leaving the tile are needed later; the others are finished here).
-  for (int k = tid; k < cnt; k += NT) {
+  for (int k = tid; k < cnt; k += TNT) {
     const V A = s_val[jslot(k)];
     if (!Finish::active || s_end[k] > JT) M::store(out, R0 + k, A);
     if (Finish::active && s_end[k] <= JT) fin(w, R0 + k, A);

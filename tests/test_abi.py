@@ -124,3 +124,9 @@ def test_phase_event_count_limits(lib):
     assert lib.tb_set_phase_events(arr, 17) == b.TB_ERR_INVALID_ARG
     assert lib.tb_set_phase_events(arr, 0) == b.TB_ERR_INVALID_ARG
     assert lib.tb_set_phase_events(None, 0) == b.TB_OK
+
+
+def test_tuned_shape_is_a_candidate():
+    from paper_2205_11659_gb300 import _build, autotune
+    assert _build.tuned_shape() in autotune.CANDIDATES
+    assert (256, 16) in autotune.CANDIDATES
