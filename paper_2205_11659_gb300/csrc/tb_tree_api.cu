@@ -28,7 +28,7 @@ constexpr int next_pow2(int x) {
 // clears them.
 struct TreeLayout {
   size_t lb, counter, xcount, zero_end, jdepth, premin, sufmin, jparent, jend, g_tree, relT, t_base,
-      t_link0, t_link1, t_val0, t_val1, t_world, cpre, t_tree, xlist, world, acc, total;
+      t_link0, t_link1, t_val0, t_val1, t_world, ctree, t_tree, xlist, world, acc, total;
   int TE, TJ, PJ, Jmax;
 };
 
@@ -70,7 +70,7 @@ TreeLayout tree_layout(int64_t n, bool backward) {
   L.t_val0 = take((size_t)TJ * kValBytes);
   L.t_val1 = take((size_t)TJ * kValBytes);
   L.t_world = take((size_t)TJ * kValBytes);
-  L.cpre = take((size_t)TJ * (NCH + 1) * kValBytes);
+  L.ctree = take((size_t)TJ * 2 * NCH * kValBytes);
   L.t_tree = take((size_t)2 * PJ * kValBytes);
   L.xlist = take(J4);
   if (backward) {
@@ -100,7 +100,7 @@ TreeWs tree_ws(const TreeLayout& L, void* ws, int64_t n, int J) {
   w.t_val[0] = b + L.t_val0;
   w.t_val[1] = b + L.t_val1;
   w.t_world = b + L.t_world;
-  w.cpre = b + L.cpre;
+  w.ctree = b + L.ctree;
   w.t_tree = b + L.t_tree;
   w.xlist = reinterpret_cast<int*>(b + L.xlist);
   w.n = (int)n;

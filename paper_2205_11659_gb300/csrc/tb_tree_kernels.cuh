@@ -43,7 +43,7 @@
 // UP (subtree fold in stream order):
 //   * k_up_tile: in-chunk subtree folds by walking each joint's children,
 //     folds that leave the chunk completed with a segment tree over the
-//     tile's chunk totals, prefix folds over chunks published per tile.
+//     tile's chunk totals, which is published per tile.
 //   * k_up_tiles: segment tree over the tiles' totals.
 //   * k_up_cross: completes the folds of subtrees that leave their tile.
 //
@@ -222,7 +222,7 @@ struct TreeWs {
   void* t_val[2];
   void* t_world;  // per tile: fold at the base joint
   // UP
-  void* cpre;    // per tile: NCH + 1 prefix folds over its chunks
+  void* ctree;   // per tile: its chunk segment tree, 2 * NCH values (node 1 = tile total)
   void* t_tree;  // segment tree over the tiles' totals, 2 * PJ values
   int* xlist;    // joints whose subtree leaves their tile
   int n;         // elements
@@ -922,7 +922,7 @@ struct AdjointValues {
 template <class M>
 constexpr size_t up_tile_smem() {
   return (size_t)JSLOTS * sizeof(typename M::V) + (size_t)2 * NCH * sizeof(typename M::V) +
-         (size_t)(TNW + 1) * sizeof(typename M::V) + (size_t)JT * sizeof(int);
+         (size_t)JT * sizeof(int);
 }
 
 template <class M, class Values, class Finish>
@@ -932,8 +932,7 @@ __global__ void __launch_bounds__(TNT, 2) k_up_tile(TreeWs w, Values values, voi
   TB_DYNAMIC_SMEM(smem);
   V* s_val = reinterpret_cast<V*>(smem);
   V* s_tree = s_val + JSLOTS;  // chunk totals at [NCH, 2 NCH)
-  V* s_scr = s_tree + 2 * NCH;
-  int* s_end = reinterpret_cast<int*>(s_scr + TNW + 1);  // local subtree ends
+  int* s_end = reinterpret_cast<int*>(s_tree + 2 * NCH);  // local subtree ends
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT;
   const int cnt = min(JT, w.J - R0);
@@ -977,11 +976,11 @@ __global__ void __launch_bounds__(TNT, 2) k_up_tile(TreeWs w, Values values, voi
     }
     s_val[jslot(k)] = acc;
   }
-  // Prefix folds over the chunks, for subtrees of earlier tiles ending here.
-  V all;
-  const V pre = block_excl_scan<TNW>(tot, M::identity(), MonoidOp<M>(), s_scr, &all);
-  M::store(w.cpre, (int64_t)t * (NCH + 1) + tid, pre);
-  if (tid == 0) M::store(w.cpre, (int64_t)t * (NCH + 1) + NCH, all);
+  // The chunk tree, for subtrees of earlier tiles ending here (their end
+  // tile's prefix over whole chunks) and for the tile total.
+  for (int i = tid; i < 2 * NCH; i += TNT)
+    if (i > 0) M::store(w.ctree, (int64_t)t * 2 * NCH + i, s_tree[i]);
+  __syncthreads();  // every chunk's folds are complete before they are stored
   // Store the folds (with a finish, only the partial folds of the subtrees
   // leaving the tile are needed later; the others are finished here).
   for (int k = tid; k < cnt; k += TNT) {
@@ -998,7 +997,7 @@ __global__ void __launch_bounds__(1024) k_up_tiles(TreeWs w) {
   const int P = w.PJ;
   for (int t = threadIdx.x; t < P; t += blockDim.x)
     M::store(w.t_tree, P + t,
-             t < w.TJ ? M::load(w.cpre, (int64_t)t * (NCH + 1) + NCH) : M::identity());
+             t < w.TJ ? M::load(w.ctree, (int64_t)t * 2 * NCH + 1) : M::identity());
   for (int h = P / 2; h >= 1; h >>= 1) {
     __syncthreads();
     for (int i = h + threadIdx.x; i < 2 * h; i += blockDim.x) {
@@ -1027,7 +1026,10 @@ __global__ void k_up_cross(TreeWs w, Values values, void* __restrict__ out, Fini
     const int R2 = t2 * JT;
     if (e > R2) {
       const int c2 = (e - R2) / JC;
-      acc = M::combine(acc, M::load(w.cpre, (int64_t)t2 * (NCH + 1) + c2));
+      const void* ct = static_cast<const unsigned char*>(w.ctree) +
+                       (size_t)t2 * 2 * NCH * sizeof(V);
+      auto cnode = [ct](int j) { return M::load(ct, j); };
+      acc = M::combine(acc, seg_fold<M>(cnode, NCH, 0, c2 - 1));
       // the joints of the end tile's chunk c2 before e (fewer than JC), from
       // their values: the fold over a range is the fold of its elements
       for (int j = R2 + c2 * JC; j < e; ++j) acc = M::combine(acc, values(j));
