@@ -2,7 +2,7 @@
 differentiable transform tree scan on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload rw26|chain24|flat24|batched|rw24|rw16|skel20|skel20s|skelbatch]
+                    [--workload rw26|match26|chain24|flat24|batched|rw24|rw16|skel20|skel20s|skelbatch]
 
 Scene workloads: one step = one full pass (tile summaries with look-back,
 tile-level resolve, main tile pass, cross-tile unions) over one synthetic
@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gelem/s bbox+paren pass & fwd+bwd tree scan; % HBM roofline; batched vs plain"
 BYTES_PER_ELEM = 41  # kind 1 + box 16 read; parent 4 + match 4 + box_out 16 written
+MATCH_BYTES_PER_ELEM = 9  # kind 1 read; parent 4 + match 4 written
 
 WORKLOADS = {
     "rw26": "bbox+paren pass, one random-walk scene (OPEN 0.2 clip/blend 50/50, CLOSE 0.2), N=2^26",
@@ -39,6 +40,7 @@ WORKLOADS = {
     "batched": "bbox+paren pass, 4096 random-walk scenes with N_s = round(2^U[8,18]), one batched call",
     "rw16": "bbox+paren pass, one random-walk scene, N=2^16 (L2-resident)",
     "rw24": "bbox+paren pass, one random-walk scene, N=2^24 (profiling size)",
+    "match26": "parentheses matching only (parent and match indices), one random-walk scene, N=2^26",
     "skel20": "affine tree scan forward + adjoint, one skeleton of J=2^20 joints (N=2J), depth <= 64",
     "skel20s": "affine tree scan forward + adjoint, one skeleton of J=2^18 joints (profiling size)",
     "skelbatch": "affine tree scan forward + adjoint through TreeTransform, 256 skeletons with "
@@ -60,7 +62,7 @@ NCU_TRAFFIC = {
 
 def make_workload(name, seed=0):
     from paper_2205_11659_gb300 import inputs
-    if name == "rw26":
+    if name in ("rw26", "match26"):
         k, b = inputs.random_walk_scene(1 << 26, seed)
         return k, b, None
     if name == "rw24":
@@ -181,12 +183,14 @@ def dist_setup():
     return world, rank, local
 
 
-def time_oracle(kind, box, offsets, budget_s=12.0, min_runs=1, max_runs=50):
+def time_oracle(kind, box, offsets, match_only=False, budget_s=12.0, min_runs=1, max_runs=50):
     import oracle
     oracle.build()
     runs, t0 = 0, time.perf_counter()
     while True:
-        if offsets is None:
+        if match_only:
+            st = oracle.match_parens(kind)[0]
+        elif offsets is None:
             st = oracle.bboxes(kind, box)[0]
         else:
             st = oracle.bboxes_batched(kind, box, offsets)[0]
@@ -222,6 +226,8 @@ def run_reference(args):
     oracle.build()
 
     def once():
+        if args.workload == "match26":
+            return oracle.match_parens(kind)[0]
         if offsets is None:
             return oracle.bboxes(kind, box)[0]
         return oracle.bboxes_batched(kind, box, offsets)[0]
@@ -550,18 +556,25 @@ def run_ours(args):
     parent = torch.empty(n, dtype=torch.int32, device=dev)
     match = torch.empty(n, dtype=torch.int32, device=dev)
     box_out = torch.empty(n, 4, dtype=torch.float32, device=dev)
-    op = binding.TB_OP_BBOXES if offsets is None else binding.TB_OP_BBOXES_BATCHED
+    match_only = args.workload == "match26"
+    bytes_per_elem = MATCH_BYTES_PER_ELEM if match_only else BYTES_PER_ELEM
+    op = binding.TB_OP_MATCH_PARENS if match_only else (
+        binding.TB_OP_BBOXES if offsets is None else binding.TB_OP_BBOXES_BATCHED)
     nb = binding.tb_workspace_size(op, n, S)
     ws = torch.empty(nb, dtype=torch.uint8, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
+    def call(st):
+        if match_only:
+            return binding.tb_match_parens(k_d, n, parent, match, ws, nb, status, st)
         if offsets is None:
-            rc = binding.tb_bboxes(k_d, b_d, n, parent, match, box_out, ws, nb, status, stream)
-        else:
-            rc = binding.tb_bboxes_batched(k_d, b_d, off_d, S, n, parent, match, box_out, ws, nb,
-                                           status, stream)
+            return binding.tb_bboxes(k_d, b_d, n, parent, match, box_out, ws, nb, status, st)
+        return binding.tb_bboxes_batched(k_d, b_d, off_d, S, n, parent, match, box_out, ws, nb,
+                                         status, st)
+
+    def step():
+        rc = call(stream)
         if rc != binding.TB_OK:
             raise binding.TBError(rc, "bench step")
 
@@ -605,11 +618,7 @@ def run_ours(args):
     # dominates the plain calls)
     gstep = torch.cuda.CUDAGraph()
     with torch.cuda.graph(gstep):
-        if offsets is None:
-            rcg = binding.tb_bboxes(k_d, b_d, n, parent, match, box_out, ws, nb, status, None)
-        else:
-            rcg = binding.tb_bboxes_batched(k_d, b_d, off_d, S, n, parent, match, box_out, ws, nb,
-                                            status, None)
+        rcg = call(None)
     assert rcg == binding.TB_OK
     gstep.replay()
     torch.cuda.synchronize()
@@ -694,7 +703,20 @@ def run_ours(args):
               torch.empty(n, 4, dtype=torch.float32).pin_memory())
 
     e2e_steps = max(3, min(K, 6))
-    if offsets is None:
+    if match_only:
+        def e2e_step():
+            k_d.copy_(kind_h, non_blocking=True)
+            step()
+            outs_h[0].copy_(parent, non_blocking=True)
+            outs_h[1].copy_(match, non_blocking=True)
+            stream.synchronize()
+        e2e_step()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        assert int(status.item()) == binding.TB_OK
+    elif offsets is None:
         # scenes streamed from pinned host memory: copies in, the pass and
         # copies out of consecutive steps overlap (HostPipeline)
         pipe = binding.HostPipeline(n, dev)
@@ -714,17 +736,17 @@ def run_ours(args):
             e2e_step()
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
-    h2d = kind.nbytes + box.nbytes + (offsets.nbytes if offsets is not None else 0)
-    d2h = 4 * n + 4 * n + 16 * n
+    h2d = kind.nbytes + (0 if match_only else box.nbytes) + (offsets.nbytes if offsets is not None else 0)
+    d2h = 4 * n + 4 * n + (0 if match_only else 16 * n)
 
     peak, peak_src = measured_peaks()
     k3_ms = phases["k3_tile"]
-    achieved = BYTES_PER_ELEM * n / (k3_ms * 1e-3) / 1e9
+    achieved = bytes_per_elem * n / (k3_ms * 1e-3) / 1e9
     traffic = NCU_TRAFFIC.get(kernel_hash(), {}).get(args.workload)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, runs, el = time_oracle(kind, box, offsets)
+        v, runs, el = time_oracle(kind, box, offsets, match_only)
         cpu = {"value": round(v, 4), "unit": "Gelem/s", "cores": 1, "kind": "oracle",
                "sample": "the full workload (%d elements) x %d runs, %.1f s, single thread"
                          % (n, runs, el)}
@@ -743,8 +765,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": "k3_tile", "achieved": round(achieved, 1),
                          "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "algorithmic_bytes_per_launch": BYTES_PER_ELEM * n},
-            "step_roofline_frac": round(BYTES_PER_ELEM * n / (ms_step * 1e-3) / 1e9 / peak, 4),
+                         "algorithmic_bytes_per_launch": bytes_per_elem * n},
+            "step_roofline_frac": round(bytes_per_elem * n / (ms_step * 1e-3) / 1e9 / peak, 4),
             "phases_ms": {k: round(v, 4) for k, v in phases.items()},
             "graph": {"ms_per_step": round(graph_step_ms, 4),
                       "value": round(world * n / (graph_step_ms * 1e-3) / 1e9, 3),
@@ -753,7 +775,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": {"value": round(world * n / e2e_s / 1e9, 3), "unit": "Gelem/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": 5 * K,
+            "gpu_launches": (5 if match_only else 7) * K,
             "clocks": clk,
             "kernel_hash": kernel_hash(),
         }
