@@ -73,10 +73,20 @@ __host__ __device__ __forceinline__ float4 box_canon(float4 b) {
 }
 
 struct OpAdd { __device__ int operator()(int a, int b) const { return a + b; } };
+// (depth change, lowest depth reached relative to the start) of consecutive
+// spans: the earlier span on the left.
+struct OpDepth {
+  __device__ int2 operator()(int2 a, int2 b) const {
+    const int lo = a.x + b.y;
+    return make_int2(a.x + b.x, a.y < lo ? a.y : lo);
+  }
+};
+constexpr int DEPTH_NONE = 1 << 30;  // "no lowest depth yet" (identity of OpDepth)
 struct OpMin { __device__ int operator()(int a, int b) const { return a < b ? a : b; } };
 struct OpIsect { __device__ float4 operator()(float4 a, float4 b) const { return box_isect(a, b); } };
 struct OpUnite { __device__ float4 operator()(float4 a, float4 b) const { return box_unite(a, b); } };
 
+__device__ __forceinline__ int2 shfl_up(int2 v, int d) { return make_int2(shfl_up(v.x, d), shfl_up(v.y, d)); }
 __device__ __forceinline__ float4 shfl_xor(float4 v, int m) {
   return make_float4(shfl_xor(v.x, m), shfl_xor(v.y, m), shfl_xor(v.z, m), shfl_xor(v.w, m));
 }

@@ -97,6 +97,7 @@ struct K1Args {
 template <bool HAS_BOX>
 __global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
   __shared__ int s_scr[NW + 1];
+  __shared__ int2 s_scr2[NW + 1];
   __shared__ float4 s_fscr[NW + 1];
   __shared__ int s_t;
   const int tid = threadIdx.x;
@@ -120,11 +121,13 @@ __global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
     mn = mn < r ? mn : r;
     mn_after = mn_after < r ? mn_after : r;
   }
-  int tot;
-  const int ds = block_excl_scan(r, 0, OpAdd(), s_scr, &tot);  // tile-relative depth at chunk start
-  const int lo_j = ds + mn;
-  int tile_lo;
-  block_excl_scan(lo_j, INT_MAX, OpMin(), s_scr, &tile_lo);
+  // one scan gives the tile-relative depth at the chunk start and, in its
+  // total, the tile's depth change and lowest depth
+  int2 tot2;
+  const int2 ex2 = block_excl_scan(make_int2(r, mn), make_int2(0, DEPTH_NONE), OpDepth(), s_scr2, &tot2);
+  const int ds = ex2.x;  // tile-relative depth at chunk start
+  const int tot = tot2.x;
+  const int tile_lo = tot2.y;
   const int a_t = -tile_lo;  // Bic(tile).a: closes that pop below the tile start
   const int b_t = tot + a_t;  // Bic(tile).b: opens left unmatched at the tile end
   const int suf_after = block_excl_suffix_min(ds + mn_after, s_scr);
