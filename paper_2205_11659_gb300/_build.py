@@ -4,7 +4,8 @@
 ``csrc/*.cu`` translation unit (in parallel), then one ``nvcc -shared`` link
 into ``_build/libtb.so``.  Rebuilds only when a source or header is newer than
 the library.  The tile shape of the scene kernels (threads per block, elements
-per thread) comes from ``tuned_shape.json``, written by ``autotune.py``.
+per thread) and whether the main tile pass runs as persistent blocks come from
+``tuned_shape.json``, written by ``autotune.py``.
 """
 import glob
 import os
@@ -55,6 +56,15 @@ def tuned_shape():
     return 256, 16
 
 
+def tuned_persistent():
+    """Whether the main tile pass runs as persistent blocks."""
+    import json
+    if os.path.exists(SHAPE_FILE):
+        with open(SHAPE_FILE) as f:
+            return bool(json.load(f).get("persistent", False))
+    return False
+
+
 def up_to_date(lib=LIB):
     if not os.path.exists(lib):
         return False
@@ -62,10 +72,11 @@ def up_to_date(lib=LIB):
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force=False, verbose=False, shape=None, out_dir=None):
+def build(force=False, verbose=False, shape=None, out_dir=None, persistent=None):
     """Build the library if needed; returns its path.  shape = (threads per
-    block, elements per thread) overrides the tuned shape and out_dir the
-    output folder (the autotuner builds its candidates that way)."""
+    block, elements per thread) and persistent override the tuned values and
+    out_dir the output folder (the autotuner builds its candidates that
+    way)."""
     out_dir = OUT_DIR if out_dir is None else out_dir
     lib_path = os.path.join(out_dir, "libtb.so")
     if not force and up_to_date(lib_path):
@@ -73,8 +84,10 @@ def build(force=False, verbose=False, shape=None, out_dir=None):
     os.makedirs(out_dir, exist_ok=True)
     exe = nvcc()
     nt, kpt = tuned_shape() if shape is None else shape
+    persist = tuned_persistent() if persistent is None else bool(persistent)
     common = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-                     "-I" + INCLUDE, "-I" + CSRC, "-DTB_NT=%d" % nt, "-DTB_KPT=%d" % kpt]
+                     "-I" + INCLUDE, "-I" + CSRC, "-DTB_NT=%d" % nt, "-DTB_KPT=%d" % kpt,
+                     "-DTB_PERSIST=%d" % int(persist)]
     if verbose:
         common += ["-Xptxas", "-v"]
 

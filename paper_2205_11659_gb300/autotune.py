@@ -1,15 +1,16 @@
-"""Autotuner of the scene kernels' tile shape.
+"""Autotuner of the scene kernels' tile shape and launch mode.
 
     python -m paper_2205_11659_gb300.autotune [--write]
 
 Builds the library once per candidate (threads per block, elements per
-thread), checks each build bit for bit against the build with the current
-tuned shape (the one the test suite checks against the oracle) on scenes
-that span several tiles and a ragged tail and on a batch of scenes, times
-the bounding-box pass with CUDA events on a 2^24-element random-walk scene
-and on a batch of 512 scenes, and reports every candidate.  With --write the
-fastest correct one goes to tuned_shape.json, which the build uses from then
-on.  Needs a CUDA GPU.
+thread, whether the main tile pass runs as persistent blocks), checks each
+build bit for bit against the build with the current tuned values (the one
+the test suite checks against the oracle) on scenes that span several tiles
+and a ragged tail and on a batch of scenes, times with CUDA events the
+bounding-box pass on a 2^24-element random-walk scene and on a batch of 512
+scenes and the matching-only pass on the same 2^24 scene, and reports every
+candidate.  With --write the fastest correct one goes to tuned_shape.json,
+which the build uses from then on.  Needs a CUDA GPU.
 """
 import argparse
 import json
@@ -22,7 +23,9 @@ import numpy as np
 
 from . import _build
 
-CANDIDATES = [(256, 16), (256, 8), (128, 16), (512, 8)]
+# (threads per block, elements per thread, persistent main pass)
+CANDIDATES = [(256, 16, False), (256, 16, True), (256, 8, False), (128, 16, False),
+              (512, 8, False)]
 
 
 def _time_calls(call, reps):
@@ -41,25 +44,30 @@ def _time_calls(call, reps):
 
 
 def _outputs(binding, dev, checks):
-    """parent, match and box_out of every check case, on the host."""
+    """parent, match and box_out of every check case, and parent and match
+    of the matching-only pass on the single scenes, on the host."""
     import torch
     res = []
     for k, b, off in checks:
         kd, bd = torch.from_numpy(k).to(dev), torch.from_numpy(b).to(dev)
         if off is None:
             p, m, o = binding.bboxes(kd, bd)
+            pm, mm = binding.match_parens(kd)
+            res.append((pm.cpu().numpy(), mm.cpu().numpy()))
         else:
             p, m, o = binding.bboxes_batched(kd, bd, torch.from_numpy(off).to(dev))
         res.append((p.cpu().numpy(), m.cpu().numpy(), o.cpu().numpy().view(np.uint32)))
     return res
 
 
-def evaluate(shape, scenes, checks, reference):
+def evaluate(cand, scenes, checks, reference):
     """(outputs of the check cases, ms per pass per scene); ms is None when
     the outputs differ from the reference."""
     import torch
     from . import binding
-    lib_path = _build.build(shape=shape, out_dir=os.path.join(_build.OUT_DIR, "tune_%d_%d" % shape))
+    nt, kpt, persist = cand
+    lib_path = _build.build(shape=(nt, kpt), persistent=persist,
+                            out_dir=os.path.join(_build.OUT_DIR, "tune_%d_%d_%d" % (nt, kpt, persist)))
     saved = _build.LIB
     binding._lib = None
     _build.LIB = lib_path
@@ -77,7 +85,13 @@ def evaluate(shape, scenes, checks, reference):
             match = torch.empty(n, dtype=torch.int32, device=dev)
             box_out = torch.empty(n, 4, dtype=torch.float32, device=dev)
             ws = binding.workspace(dev)
-            if od is None:
+            if bd is None:
+                nb = binding.tb_workspace_size(binding.TB_OP_MATCH_PARENS, n)
+                buf = ws.get(nb)
+
+                def call():
+                    return binding.tb_match_parens(kd, n, parent, match, buf, nb, ws.status)
+            elif od is None:
                 nb = binding.tb_workspace_size(binding.TB_OP_BBOXES, n)
                 buf = ws.get(nb)
 
@@ -109,9 +123,11 @@ def main(argv=None):
     dev = torch.device("cuda", 0)
     k, b = inputs.random_walk_scene(1 << 24, 0)
     kb, bb, off = inputs.batched_scenes(512, 0)
-    scenes = {"rw24": (torch.from_numpy(k).to(dev), torch.from_numpy(b).to(dev), None),
+    kd = torch.from_numpy(k).to(dev)
+    scenes = {"rw24": (kd, torch.from_numpy(b).to(dev), None),
               "batch512": (torch.from_numpy(kb).to(dev), torch.from_numpy(bb).to(dev),
-                           torch.from_numpy(off).to(dev))}
+                           torch.from_numpy(off).to(dev)),
+              "match24": (kd, None, None)}
     # check cases: several tiles of every candidate and a ragged tail, and a
     # batch of scenes
     checks = []
@@ -119,27 +135,28 @@ def main(argv=None):
         kk, bx = inputs.random_walk_scene(n, seed)
         checks.append((kk, bx, None))
     checks.append(inputs.batched_scenes(64, 4, 4.0, 14.0))
-    current = _build.tuned_shape()
+    current = _build.tuned_shape() + (_build.tuned_persistent(),)
     order = [current] + [c for c in CANDIDATES if c != current]
     reference = None
     results = []
-    for shape in order:
+    for cand in order:
         t0 = time.time()
-        outs, ms = evaluate(shape, scenes, checks, reference)
+        outs, ms = evaluate(cand, scenes, checks, reference)
         if reference is None:
-            reference = outs  # the current shape, which the tests check against the oracle
-        results.append({"threads_per_block": shape[0], "elements_per_thread": shape[1],
-                        "correct": ms is not None, "ms": ms,
+            reference = outs  # the current build, which the tests check against the oracle
+        results.append({"threads_per_block": cand[0], "elements_per_thread": cand[1],
+                        "persistent": bool(cand[2]), "correct": ms is not None, "ms": ms,
                         "seconds": round(time.time() - t0, 1)})
         print(json.dumps(results[-1]), flush=True)
     ok = [r for r in results if r["correct"]]
     if not ok:
         print("no correct candidate", file=sys.stderr)
         return 1
-    best = min(ok, key=lambda r: r["ms"]["rw24"] + r["ms"]["batch512"])
+    best = min(ok, key=lambda r: sum(r["ms"].values()))
     summary = {"threads_per_block": best["threads_per_block"],
                "elements_per_thread": best["elements_per_thread"],
-               "chosen_by": "autotune.py: fastest correct candidate on rw24 + batch512",
+               "persistent": best["persistent"],
+               "chosen_by": "autotune.py: fastest correct candidate on rw24 + batch512 + match24",
                "candidates": results}
     print(json.dumps(summary), flush=True)
     if args.write:

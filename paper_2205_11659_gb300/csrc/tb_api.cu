@@ -25,8 +25,9 @@ constexpr int next_pow2(int x) {
 }
 
 // Workspace carving shared by tb_workspace_size and the launches.  The
-// look-back words and the tile counter come first so one memset clears
-// both.
+// look-back words and the tile counters (the tile-summary pass's ticket and,
+// with persistent blocks, the main pass's) come first so one memset clears
+// them.
 struct Layout {
   size_t lb, counter, t_a, t_b, t_dstart, t_lo, t_ps, t_q, lo_tree, t_link0, t_link1, t_val0,
       t_val1, t_B, t_uall, uall_tree, slice_pos, slice_rel, usuf, upre, cpos, cval, t_seg, t_nseg,
@@ -131,6 +132,31 @@ inline void phase_mark(cudaStream_t s) {
 
 bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
+// Blocks of the main pass that are resident on the current device at once
+// (persistent launch), found once per device.
+template <bool HAS_BOX, bool BATCHED>
+cudaError_t k3_resident_blocks(int* out) {
+  constexpr int kMaxDevices = 64;
+  static int cached[kMaxDevices] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < kMaxDevices && cached[dev] > 0) {
+    *out = cached[dev];
+    return cudaSuccess;
+  }
+  int sms = 0, per_sm = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_tile<HAS_BOX, BATCHED>, NT,
+                                                    k3_smem_bytes(HAS_BOX));
+  if (e != cudaSuccess) return e;
+  const int nb = sms * (per_sm > 0 ? per_sm : 1);
+  if (dev < kMaxDevices) cached[dev] = nb;
+  *out = nb;
+  return cudaSuccess;
+}
+
 template <bool HAS_BOX, bool BATCHED>
 cudaError_t launch_k3(const K3Args& a, int T, cudaStream_t s) {
   static bool attr_set = false;
@@ -141,7 +167,14 @@ cudaError_t launch_k3(const K3Args& a, int T, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k3_tile<HAS_BOX, BATCHED><<<T, NT, smem, s>>>(a);
+  int grid = T;
+  if (PERSIST) {
+    int nb = 0;
+    cudaError_t e = k3_resident_blocks<HAS_BOX, BATCHED>(&nb);
+    if (e != cudaSuccess) return e;
+    grid = T < nb ? T : nb;
+  }
+  k3_tile<HAS_BOX, BATCHED><<<grid, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -25,8 +25,15 @@ namespace tb {
 #ifndef TB_KPT
 #define TB_KPT 16
 #endif
+// TB_PERSIST: the main tile pass runs as persistent blocks (as many as fit
+// on the device at once, each taking tiles in turn) instead of one block per
+// tile; also chosen by the autotuner.
+#ifndef TB_PERSIST
+#define TB_PERSIST 0
+#endif
 constexpr int NT = TB_NT;
 constexpr int KPT = TB_KPT;
+constexpr bool PERSIST = TB_PERSIST != 0;
 constexpr int TILE = NT * KPT;
 constexpr int NW = NT / 32;
 static_assert(NT == 128 || NT == 256 || NT == 512, "block size must be 128, 256 or 512");

@@ -503,8 +503,15 @@ __device__ __forceinline__ OutRes out_lookup(const OutCtx& c, const SceneWs& ws,
   return r;
 }
 
+// One block per tile, or (TB_PERSIST) a grid of resident blocks that take
+// tiles in order from a ticket counter (counter[1] of the workspace, zeroed
+// with the look-back words), the next ticket drawn while the current tile is
+// processed.  The per-tile code below is the same in both builds; it leaves a
+// tile through K3_TILE_DONE (a return, or a break to the next ticket).  The
+// matching-only pass is held to 64 registers a thread so that 1024 threads
+// per SM stay resident.
 template <bool HAS_BOX, bool BATCHED>
-__global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
+__global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a) {
   TB_DYNAMIC_SMEM(smem);
   __shared__ int s_scr[NW + 1];
   __shared__ int4 s_seg[SEGK];
@@ -518,7 +525,21 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
   __shared__ int s_sc[2];
 
   const int tid = threadIdx.x;
-  const int t = blockIdx.x;
+#if TB_PERSIST
+  __shared__ int s_next;
+  if (tid == 0) s_next = (int)atomic_add_u32(a.ws.counter + 1, 1u);
+  __syncthreads();
+  for (int t = s_next; t < a.ws.T; t = s_next) {
+    __syncthreads();  // every thread has read s_next
+    if (tid == 0) s_next = (int)atomic_add_u32(a.ws.counter + 1, 1u);
+    do {
+#define K3_TILE_DONE break
+#else
+  {
+    const int t = blockIdx.x;
+#define K3_TILE_DONE return
+#endif
+  // ---- tile t
   const int base = t * TILE;
   const int cnt = min(TILE, a.n - base);
   const int p0 = tid * KPT;
@@ -528,7 +549,7 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
   // so one thread reads the word and the block follows it.)
   if (tid == 0) s_stop = *a.status;
   __syncthreads();
-  if (s_stop != ST_OK) return;
+  if (s_stop != ST_OK) K3_TILE_DONE;
 
   unsigned char* sp = smem;
   float4* s_box = reinterpret_cast<float4*>(sp);
@@ -962,7 +983,7 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
         ws.cval[(size_t)t * TILE + (-1 - dd)] = eo;
       }
     }
-    return;
+    K3_TILE_DONE;
   }
 
   // ---- unions across chunks (and the partial unions of cross-tile pairs)
@@ -1043,6 +1064,14 @@ __global__ void __launch_bounds__(NT, 2) k3_tile(K3Args a) {
     const int p = i * NT + tid;
     if (p < cnt) a.box_out[base + p] = s_box[box_slot(p)];
   }
+#if TB_PERSIST
+    } while (0);
+    __syncthreads();  // the next tile reuses the shared memory; s_next is set
+  }
+#else
+  }
+#endif
+#undef K3_TILE_DONE
 }
 
 // ------------------------------------------------------------------- K4

@@ -128,5 +128,5 @@ def test_phase_event_count_limits(lib):
 
 def test_tuned_shape_is_a_candidate():
     from paper_2205_11659_gb300 import _build, autotune
-    assert _build.tuned_shape() in autotune.CANDIDATES
-    assert (256, 16) in autotune.CANDIDATES
+    assert _build.tuned_shape() + (_build.tuned_persistent(),) in autotune.CANDIDATES
+    assert (256, 16, False) in autotune.CANDIDATES
