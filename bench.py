@@ -38,7 +38,7 @@ WORKLOADS = {
     "chain24": "bbox+paren pass, one chain scene: 2^23 nested clip opens, a leaf, 2^23 closes",
     "flat24": "bbox+paren pass, one flat scene of depth <= 4 (~90% leaves), N=2^24",
     "batched": "bbox+paren pass, 4096 random-walk scenes with N_s = round(2^U[8,18]), one batched call",
-    "rw16": "bbox+paren pass, one random-walk scene, N=2^16 (L2-resident)",
+    "rw16": "bbox+paren pass, one random-walk scene, N=2^16 (launch-latency size)",
     "rw24": "bbox+paren pass, one random-walk scene, N=2^24 (profiling size)",
     "match26": "parentheses matching only (parent and match indices), one random-walk scene, N=2^26",
     "skel20": "affine tree scan forward + adjoint, one skeleton of J=2^20 joints (N=2J), depth <= 64",
@@ -170,6 +170,44 @@ def job_time_ms(ms_local, world, device):
     t = torch.tensor([ms_local], dtype=torch.float64, device=device)
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return float(t.item())
+
+
+L2_BYTES = 130e6  # GB300 L2 (129 MB), rounded up
+
+
+class L2Flush:
+    """Evicts L2 between timed steps when a workload's inputs fit in it: a
+    256 MB write (twice the L2) issued before each step, outside the step's
+    timed event pair.  Inactive (no buffer, no writes) when the inputs are
+    larger than L2."""
+
+    def __init__(self, torch, dev, input_bytes):
+        self.active = input_bytes <= L2_BYTES
+        self.buf = torch.empty(64 << 20, dtype=torch.float32, device=dev) if self.active else None
+
+    def __call__(self):
+        if self.active:
+            self.buf.fill_(1.0)
+
+    def describe(self, input_bytes):
+        if self.active:
+            return ("inputs (%.1f MB) fit in L2: 256 MB written before each timed step, outside "
+                    "its events" % (input_bytes / 1e6))
+        return "inputs (%.2f GB) larger than L2, no flush" % (input_bytes / 1e9)
+
+
+def timed_each(torch, stream, call, K, flush):
+    """Mean ms of K calls, each between its own pair of events on `stream`,
+    with flush() before each call (outside the pair)."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    for a, b in ev:
+        flush()
+        a.record(stream)
+        call()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / K
 
 
 def job_rate(units_per_rank, world, ms_step):
@@ -344,6 +382,8 @@ def run_tree(args, torch, world, rank, dev):
         with torch.cuda.graph(graph):
             (binding.TreeTransform.apply(k_d, local, False) * W_d).sum().backward()
 
+    in_bytes = kind.nbytes + L.nbytes + W.nbytes
+    flush = L2Flush(torch, dev, in_bytes)
     for _ in range(max(args.warmup, 3)):
         fwd()
         bwd()
@@ -361,16 +401,17 @@ def run_tree(args, torch, world, rank, dev):
     for evs in ev_f + ev_b:
         for e in evs:
             e.record(stream)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    steps_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(K)]
     clocks = ClockSampler(dev.index)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    ev0.record(stream)
     for i in range(K):
+        flush()
+        steps_ev[i][0].record(stream)
         if graph is not None:
             graph.replay()
         else:
@@ -378,11 +419,11 @@ def run_tree(args, torch, world, rank, dev):
             fwd()
             binding.tb_set_phase_events(ev_b[i])
             bwd()
-    ev1.record(stream)
+        steps_ev[i][1].record(stream)
     binding.tb_set_phase_events(None)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms_total = job_time_ms(ev0.elapsed_time(ev1), world, dev)
+    ms_total = job_time_ms(sum(a.elapsed_time(b) for a, b in steps_ev), world, dev)
     ms_step = ms_total / K
     value = job_rate(n, world, ms_step)
 
@@ -391,6 +432,7 @@ def run_tree(args, torch, world, rank, dev):
     bnames = fnames + ["up_tile", "up_tiles", "up_cross"]
     if graph is not None:
         for i in range(K):
+            flush()
             binding.tb_set_phase_events(ev_f[i])
             fwd()
             binding.tb_set_phase_events(ev_b[i])
@@ -414,14 +456,7 @@ def run_tree(args, torch, world, rank, dev):
             call(None)
         g.replay()
         torch.cuda.synchronize()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(K):
-            g.replay()
-        a1.record(stream)
-        torch.cuda.synchronize()
-        return a0.elapsed_time(a1) / K
+        return timed_each(torch, stream, g.replay, K, flush)
     fwd_ms = graph_ms(lambda st: binding.tb_tree_scan(binding.TB_MONOID_AFFINE3X4_F32, binding.TB_DOWN,
                                                       k_d, n, J, L_d, world_d, ws, nb, status, st))
     bwd_ms = graph_ms(lambda st: binding.tb_tree_scan_affine_backward(k_d, n, J, L_d, W_d, grad_d, ws,
@@ -503,8 +538,7 @@ def run_tree(args, torch, world, rank, dev):
                        "step": "one CUDA graph of TreeTransform forward + backward" if batched
                                else "one CUDA graph of tb_tree_scan (affine DOWN) + "
                                     "tb_tree_scan_affine_backward",
-                       "l2": "inputs larger than L2, no flush" if 98 * J > 130e6 else
-                             "inputs (%.0f MB) L2-resident, no flush" % (98 * J / 1e6),
+                       "l2": flush.describe(in_bytes),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "kernel": "tb_tree_scan_affine_backward (all its launches)",
                          "achieved": round(bwd_alg / (bwd_ms * 1e-3) / 1e9, 1), "peak": peak,
@@ -580,34 +614,38 @@ def run_ours(args):
         if rc != binding.TB_OK:
             raise binding.TBError(rc, "bench step")
 
+    in_bytes = kind.nbytes + (0 if match_only else box.nbytes)
+    flush = L2Flush(torch, dev, in_bytes)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
     assert int(status.item()) == binding.TB_OK, int(status.item())
 
-    # ---- device-timed region: inputs resident in HBM (larger than L2)
+    # ---- device-timed region: inputs resident in HBM (L2 flushed before
+    # each step when they would fit in it)
     K = args.steps
     phase = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
     for evs in phase:           # create the event handles
         for e in evs:
             e.record(stream)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    steps_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(K)]
     clocks = ClockSampler(dev.index)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    ev0.record(stream)
     for i in range(K):
+        flush()
+        steps_ev[i][0].record(stream)
         binding.tb_set_phase_events(phase[i])
         step()
-    ev1.record(stream)
+        steps_ev[i][1].record(stream)
     binding.tb_set_phase_events(None)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms_total = job_time_ms(ev0.elapsed_time(ev1), world, dev)
+    ms_total = job_time_ms(sum(a.elapsed_time(b) for a, b in steps_ev), world, dev)
     ms_step = ms_total / K
     assert int(status.item()) == binding.TB_OK
     names = ["k1_tile_summary", "k2_tile_resolve", "k3_tile", "k4_cross_tile_unions"]
@@ -625,14 +663,7 @@ def run_ours(args):
     gstep.replay()
     torch.cuda.synchronize()
     assert int(status.item()) == binding.TB_OK
-    g0 = torch.cuda.Event(enable_timing=True)
-    g1 = torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    for _ in range(K):
-        gstep.replay()
-    g1.record(stream)
-    torch.cuda.synchronize()
-    graph_step_ms = g0.elapsed_time(g1) / K
+    graph_step_ms = timed_each(torch, stream, gstep.replay, K, flush)
     del gstep
 
     # ---- batched: the same scenes as separate plain calls, same outputs
@@ -761,8 +792,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "n": n, "seed": 0,
                        "scenes": S if S else 1,
-                       "l2": "inputs (%.2f GB) larger than L2, no flush" % ((kind.nbytes + box.nbytes) / 1e9)
-                       if kind.nbytes + box.nbytes > 130e6 else "L2-resident, no flush",
+                       "l2": flush.describe(in_bytes),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "kernel": "k3_tile", "achieved": round(achieved, 1),
                          "peak": peak, "peak_source": peak_src, "unit": "GB/s",
