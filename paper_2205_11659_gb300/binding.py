@@ -414,44 +414,57 @@ class TreeTransform(torch.autograd.Function):
 
 # ----------------------------------------------------- host pipelines
 class HostPipeline:
-    """tb_bboxes over a sequence of scenes held in pinned host memory, with
-    the copies overlapped: while the pass runs on scene i, scene i+1 is
-    copied in and the results of scene i-1 are copied out (three CUDA
-    streams, two sets of device buffers, one workspace).
+    """tb_bboxes (or, with boxes=False, tb_match_parens) over a sequence of
+    scenes held in pinned host memory, with the copies overlapped: while the
+    pass runs on scene i, scene i+1 is copied in and the results of scene
+    i-1 are copied out (three CUDA streams, two sets of device buffers, one
+    workspace).
 
     run(kinds, boxes, outs): kinds[i] uint8 (n_i,), boxes[i] float32
-    (n_i, 4), outs[i] = (parent, match, box_out) pinned host tensors of
-    shapes (n_i,), (n_i,), (n_i, 4).  An entry may repeat a tensor: the
-    copies of consecutive scenes are ordered on their own stream.  Returns
-    after the last result is in host memory and raises TBError if any
+    (n_i, 4) (None for a matching-only pipeline), outs[i] = (parent, match,
+    box_out) pinned host tensors of shapes (n_i,), (n_i,), (n_i, 4), or
+    (parent, match) for a matching-only pipeline.  An entry may repeat a
+    tensor: the copies of consecutive scenes are ordered on their own stream.
+    Returns after the last result is in host memory and raises TBError if any
     scene's status word is not TB_OK."""
 
-    def __init__(self, n_max, device=None):
+    def __init__(self, n_max, device=None, boxes=True):
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
             else torch.device(device)
         dev = self.device
         self.n_max = int(n_max)
+        self.boxes = bool(boxes)
         self.sets = []
         for _ in range(2):
-            self.sets.append({
+            S = {
                 "kind": torch.empty(self.n_max, dtype=torch.uint8, device=dev),
-                "box": torch.empty(self.n_max, 4, dtype=torch.float32, device=dev),
                 "parent": torch.empty(self.n_max, dtype=torch.int32, device=dev),
                 "match": torch.empty(self.n_max, dtype=torch.int32, device=dev),
-                "box_out": torch.empty(self.n_max, 4, dtype=torch.float32, device=dev),
                 "status": torch.zeros(1, dtype=torch.int32, device=dev),
                 "ev_in": torch.cuda.Event(), "ev_comp": torch.cuda.Event(),
                 "ev_out": torch.cuda.Event(), "used": False,
-            })
-        self.ws_bytes = tb_workspace_size(TB_OP_BBOXES, max(self.n_max, 1))
+            }
+            if self.boxes:
+                S["box"] = torch.empty(self.n_max, 4, dtype=torch.float32, device=dev)
+                S["box_out"] = torch.empty(self.n_max, 4, dtype=torch.float32, device=dev)
+            self.sets.append(S)
+        self.op = TB_OP_BBOXES if self.boxes else TB_OP_MATCH_PARENS
+        self.ws_bytes = tb_workspace_size(self.op, max(self.n_max, 1))
         self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
         self.s_in = torch.cuda.Stream(dev)
         self.s_comp = torch.cuda.Stream(dev)
         self.s_out = torch.cuda.Stream(dev)
 
     def run(self, kinds, boxes, outs):
+        if boxes is None:
+            if self.boxes:
+                raise ValueError("this pipeline computes boxes: pass the boxes of every scene")
+            boxes = [None] * len(kinds)
+        elif not self.boxes:
+            raise ValueError("a matching-only pipeline takes boxes=None")
         if not (len(kinds) == len(boxes) == len(outs)):
             raise ValueError("kinds, boxes and outs must have the same length")
+        name = "tb_bboxes" if self.boxes else "tb_match_parens"
         statuses = torch.zeros(len(kinds), dtype=torch.int32).pin_memory()
         for i, (k_h, b_h, o_h) in enumerate(zip(kinds, boxes, outs)):
             n = k_h.numel()
@@ -462,21 +475,26 @@ class HostPipeline:
                 if S["used"]:
                     self.s_in.wait_event(S["ev_comp"])  # inputs no longer read
                 S["kind"][:n].copy_(k_h, non_blocking=True)
-                S["box"][:n].copy_(b_h.reshape(-1, 4), non_blocking=True)
+                if self.boxes:
+                    S["box"][:n].copy_(b_h.reshape(-1, 4), non_blocking=True)
                 S["ev_in"].record(self.s_in)
             self.s_comp.wait_event(S["ev_in"])
             if S["used"]:
                 self.s_comp.wait_event(S["ev_out"])  # outputs already copied out
-            rc = tb_bboxes(S["kind"], S["box"], n, S["parent"], S["match"], S["box_out"], self.ws,
-                           self.ws_bytes, S["status"], self.s_comp)
-            _check(rc, "tb_bboxes")
+            if self.boxes:
+                rc = tb_bboxes(S["kind"], S["box"], n, S["parent"], S["match"], S["box_out"],
+                               self.ws, self.ws_bytes, S["status"], self.s_comp)
+            else:
+                rc = tb_match_parens(S["kind"], n, S["parent"], S["match"], self.ws, self.ws_bytes,
+                                     S["status"], self.s_comp)
+            _check(rc, name)
             S["ev_comp"].record(self.s_comp)
             with torch.cuda.stream(self.s_out):
                 self.s_out.wait_event(S["ev_comp"])
-                parent_h, match_h, box_h = o_h
-                parent_h.copy_(S["parent"][:n], non_blocking=True)
-                match_h.copy_(S["match"][:n], non_blocking=True)
-                box_h.copy_(S["box_out"][:n], non_blocking=True)
+                o_h[0].copy_(S["parent"][:n], non_blocking=True)
+                o_h[1].copy_(S["match"][:n], non_blocking=True)
+                if self.boxes:
+                    o_h[2].copy_(S["box_out"][:n], non_blocking=True)
                 statuses[i:i + 1].copy_(S["status"], non_blocking=True)
                 S["ev_out"].record(self.s_out)
             S["used"] = True
@@ -484,5 +502,5 @@ class HostPipeline:
         self.s_comp.synchronize()
         self.s_in.synchronize()
         for i in range(len(kinds)):
-            _check(int(statuses[i]), "tb_bboxes (scene %d)" % i)
+            _check(int(statuses[i]), "%s (scene %d)" % (name, i))
         return outs

@@ -231,6 +231,28 @@ def test_host_pipeline_matches_oracle():
             assert same_bits(o.numpy(), ob)
 
 
+def test_host_pipeline_matching_only():
+    """The matching-only pipeline gives the oracle's parent and match, and
+    reports an unbalanced scene of the sequence."""
+    scenes = [inputs.random_walk_scene(n, 950 + n)[0] for n in (50_001, 200_000, 4097)]
+    pipe = binding.HostPipeline(200_000, boxes=False)
+    kinds = [torch.from_numpy(k).pin_memory() for k in scenes]
+    outs = [(torch.empty(k.size, dtype=torch.int32).pin_memory(),
+             torch.empty(k.size, dtype=torch.int32).pin_memory()) for k in scenes]
+    pipe.run(kinds, None, outs)
+    for k, (p, m) in zip(scenes, outs):
+        st, op, om = oracle.match_parens(k)
+        assert st == oracle.OK
+        assert np.array_equal(p.numpy(), op) and np.array_equal(m.numpy(), om)
+    bad = scenes[1].copy()
+    bad[np.nonzero(bad == 3)[0][0]] = 0  # one close fewer
+    kinds[1] = torch.from_numpy(bad).pin_memory()
+    with pytest.raises(binding.TBError):
+        pipe.run(kinds, None, outs)
+    with pytest.raises(ValueError):
+        pipe.run(kinds, kinds, outs)
+
+
 def test_lookback_timeout_reported_and_recovered():
     """A tile that never publishes makes the bounded look-back waits of the
     tiles after it give up: the call reports TB_ERR_TIMEOUT (after about a
