@@ -803,7 +803,7 @@ def run_ours(args):
                     "how": ("HostPipeline: copies of consecutive scenes overlap the pass; fill and "
                             "drain timed" if offsets is None else
                             "bboxes_batched_host: copies in, the batched pass, copies out")},
-            "gpu_launches": (5 if match_only else 7) * K,
+            "gpu_launches": (6 if match_only else 8) * K,
             "clocks": clk,
             "kernel_hash": kernel_hash(),
         }

@@ -198,14 +198,15 @@ tb_status tb_bboxes_static_ws(const uint8_t* kind, const float* box, int64_t n,
                               int32_t* d_status, void* stream);
 
 /* Test hook for the bounded cross-block waits (failure detection): after
- * tb_debug_withhold_tile(t), tile t (4096 elements each) of the following
- * tb_match_parens / tb_bboxes / tb_bboxes_batched / tb_bboxes_static_ws
+ * tb_debug_withhold_tile(t), element tile t (4096 elements each) of the
+ * depth pass of the following tb_tree_scan / tb_tree_scan_affine_backward
  * calls on this host thread never publishes its look-back word, so the
  * tiles after it give up after about a second and the call reports
- * TB_ERR_TIMEOUT in d_status; the later passes then stop and the outputs
- * are unspecified, and the CUDA context stays usable.  -1 turns the hook
- * off; values below -1 return TB_ERR_INVALID_ARG.  The paper has no
- * counterpart. */
+ * TB_ERR_TIMEOUT in d_status; the later kernels then stop and the outputs
+ * are unspecified, and the CUDA context stays usable.  The matching and
+ * bounding-box calls have no cross-block wait and ignore the hook.  -1
+ * turns the hook off; values below -1 return TB_ERR_INVALID_ARG.  The paper
+ * has no counterpart. */
 tb_status tb_debug_withhold_tile(int tile);
 
 /* Library version string. */

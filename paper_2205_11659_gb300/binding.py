@@ -165,8 +165,9 @@ def tb_tree_scan_affine_backward(kind, n, num_joints, local, grad_world, grad_lo
 
 
 def tb_debug_withhold_tile(tile):
-    """Test hook: tile `tile` of the following scene calls on this thread never
-    publishes its look-back word (-1 turns it off)."""
+    """Test hook: element tile `tile` of the depth pass of the following tree
+    scans on this thread never publishes its look-back word (-1 turns it
+    off)."""
     return lib().tb_debug_withhold_tile(int(tile))
 
 

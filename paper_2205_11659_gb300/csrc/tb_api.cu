@@ -24,12 +24,11 @@ constexpr int next_pow2(int x) {
   return p;
 }
 
-// Workspace carving shared by tb_workspace_size and the launches.  The
-// look-back words and the tile counters (the tile-summary pass's ticket and,
-// with persistent blocks, the main pass's) come first so one memset clears
-// them.
+// Workspace carving shared by tb_workspace_size and the launches.  The tile
+// counters (the persistent main pass's ticket) come first so one memset
+// clears them.
 struct Layout {
-  size_t lb, counter, t_a, t_b, t_dstart, t_lo, t_ps, t_q, lo_tree, t_link0, t_link1, t_val0,
+  size_t counter, t_a, t_b, t_tot, t_dstart, t_lo, t_ps, t_q, lo_tree, t_link0, t_link1, t_val0,
       t_val1, t_B, t_uall, uall_tree, slice_pos, slice_rel, usuf, upre, cpos, cval, t_seg, t_nseg,
       t_cont, ctx_src, total;
   int T, P;
@@ -48,10 +47,10 @@ constexpr Layout scene_layout(int64_t n, bool has_box) {
     o = align_up(o + bytes);
     return at;
   };
-  L.lb = take((size_t)T * 8);
   L.counter = take(16);
   L.t_a = take(t4);
   L.t_b = take(t4);
+  L.t_tot = take(t4);
   L.t_dstart = take(t4);
   L.t_lo = take(t4);
   L.t_ps = take(t4);
@@ -83,10 +82,10 @@ constexpr Layout scene_layout(int64_t n, bool has_box) {
 SceneWs scene_ws(const Layout& L, void* ws, bool has_box) {
   unsigned char* b = static_cast<unsigned char*>(ws);
   SceneWs w{};
-  w.lb = reinterpret_cast<unsigned long long*>(b + L.lb);
   w.counter = reinterpret_cast<unsigned*>(b + L.counter);
   w.t_a = reinterpret_cast<int*>(b + L.t_a);
   w.t_b = reinterpret_cast<int*>(b + L.t_b);
+  w.t_tot = reinterpret_cast<int*>(b + L.t_tot);
   w.t_dstart = reinterpret_cast<int*>(b + L.t_dstart);
   w.t_lo = reinterpret_cast<int*>(b + L.t_lo);
   w.t_ps = reinterpret_cast<int*>(b + L.t_ps);
@@ -122,8 +121,8 @@ thread_local cudaEvent_t g_phase_events[kMaxPhaseEvents];
 thread_local int g_phase_n = 0;
 thread_local int g_phase_next = 0;
 
-// Test hook: a tile of the following scene calls that never publishes its
-// look-back word (-1: none).
+// Test hook: an element tile of the following tree-scan calls that never
+// publishes its look-back word (-1: none).
 thread_local int g_withhold = -1;
 
 inline void phase_mark(cudaStream_t s) {
@@ -192,8 +191,7 @@ cudaError_t launch_k2(const SceneWs& w, cudaStream_t s) {
 template <bool HAS_BOX>
 tb_status run_scene(const uint8_t* kind, const float* box, int64_t n, int32_t* parent,
                     int32_t* match, float* box_out, const int64_t* offsets, int64_t num_scenes,
-                    void* ws, size_t ws_bytes, int32_t* d_status, void* stream,
-                    int withhold_tile) {
+                    void* ws, size_t ws_bytes, int32_t* d_status, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (n < 0 || n > kMaxN || d_status == nullptr) return TB_ERR_INVALID_ARG;
   if (!aligned(d_status, 4)) return TB_ERR_INVALID_ARG;
@@ -216,13 +214,11 @@ tb_status run_scene(const uint8_t* kind, const float* box, int64_t n, int32_t* p
   SceneWs w = scene_ws(L, ws, HAS_BOX);
   w.status = d_status;
   if (cudaMemsetAsync(ws, 0, L.t_a, s) != cudaSuccess) return TB_ERR_CUDA;
-  if (cudaMemsetAsync(static_cast<unsigned char*>(ws) + L.lo_tree, 0x7f, (size_t)2 * L.P * 4, s) !=
-      cudaSuccess)
-    return TB_ERR_CUDA;
 
   phase_mark(s);
-  K1Args a1{kind, reinterpret_cast<const float4*>(box), (int)n, w, d_status, withhold_tile};
+  K1Args a1{kind, reinterpret_cast<const float4*>(box), (int)n, w, d_status};
   k1_tile_summary<HAS_BOX><<<L.T, NT, 0, s>>>(a1);
+  k1_tile_prefix<<<1, NT2, 0, s>>>(w, d_status);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   phase_mark(s);
   if (launch_k2<HAS_BOX>(w, s) != cudaSuccess) return TB_ERR_CUDA;
@@ -270,7 +266,7 @@ tb_status tb_match_parens(const uint8_t* kind, int64_t n, int32_t* parent, int32
                           size_t ws_bytes, int32_t* d_status, void* stream) {
   g_phase_next = 0;
   return run_scene<false>(kind, nullptr, n, parent, match, nullptr, nullptr, 0, ws, ws_bytes,
-                          d_status, stream, g_withhold);
+                          d_status, stream);
 }
 
 tb_status tb_bboxes(const uint8_t* kind, const float* box, int64_t n, int32_t* parent,
@@ -278,7 +274,7 @@ tb_status tb_bboxes(const uint8_t* kind, const float* box, int64_t n, int32_t* p
                     void* stream) {
   g_phase_next = 0;
   return run_scene<true>(kind, box, n, parent, match, box_out, nullptr, 0, ws, ws_bytes, d_status,
-                         stream, g_withhold);
+                         stream);
 }
 
 tb_status tb_bboxes_batched(const uint8_t* kind, const float* box, const int64_t* offsets,
@@ -288,7 +284,7 @@ tb_status tb_bboxes_batched(const uint8_t* kind, const float* box, const int64_t
   if (offsets == nullptr || num_scenes < 1) return TB_ERR_INVALID_ARG;
   g_phase_next = 0;
   return run_scene<true>(kind, box, n_total, parent, match, box_out, offsets, num_scenes, ws,
-                         ws_bytes, d_status, stream, g_withhold);
+                         ws_bytes, d_status, stream);
 }
 
 tb_status tb_set_phase_events(void* const* events, int num_events) {
@@ -318,6 +314,7 @@ namespace tb_internal {
 
 void phase_reset() { g_phase_next = 0; }
 void phase_mark(cudaStream_t s) { ::phase_mark(s); }
+int withheld_tile() { return g_withhold; }
 
 }  // namespace tb_internal
 
@@ -364,11 +361,11 @@ tb_status tb_bboxes_static_ws(const uint8_t* kind, const float* box, int64_t n, 
   void* ws = nullptr;
   const tb_status st = static_ws_for_current_device(&ws);
   if (st != TB_OK) return st;
-  // run_scene clears the look-back words and the tile counter of the scratch
-  // on every call; everything else in it is written before it is read.
+  // run_scene clears the tile counters of the scratch on every call;
+  // everything else in it is written before it is read.
   g_phase_next = 0;
   return run_scene<true>(kind, box, n, parent, match, box_out, nullptr, 0, ws, kStaticWsBytes,
-                         d_status, stream, g_withhold);
+                         d_status, stream);
 }
 
 }  // extern "C"

@@ -269,10 +269,10 @@ __device__ __forceinline__ T tree_range(const T* tree, int P, int l, int r, T id
 //   upre         union of the tile's leaves before that close
 //   cpos         global index of that close
 struct SceneWs {
-  unsigned long long* lb;
-  unsigned* counter;
+  unsigned* counter;  // [1]: tile ticket of the persistent main pass
   int* t_a;
   int* t_b;
+  int* t_tot;         // per tile: depth change over the tile
   int* t_dstart;
   int* t_lo;
   int* t_ps;

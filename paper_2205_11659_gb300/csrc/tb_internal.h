@@ -1,5 +1,5 @@
 // tb_internal.h -- what the translation units of the library share: the
-// phase-event hook and the tree-scan workspace size.
+// phase-event hook, the look-back test hook and the tree-scan workspace size.
 #ifndef TB_INTERNAL_H
 #define TB_INTERNAL_H
 
@@ -16,6 +16,10 @@ namespace tb_internal {
 // before each kernel and one after the last.
 void phase_reset();
 void phase_mark(cudaStream_t s);
+
+// Element tile of the tree scans' depth pass that never publishes its
+// look-back word (tb_debug_withhold_tile), or -1.
+int withheld_tile();
 
 // Scratch bytes of the tree scans (op TB_OP_TREE_SCAN or TB_OP_TREE_BACKWARD).
 size_t tree_ws_bytes(int op, int64_t n);

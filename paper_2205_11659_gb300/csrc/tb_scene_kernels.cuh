@@ -4,11 +4,13 @@
 // owns a tile and each thread a chunk of KPT consecutive elements.
 //
 //   k1_tile_summary  one pass over the kind stream: per tile the bicyclic
-//                    summary Bic(tile) = (a, b) (Sec. 3), the global depth
-//                    at the tile start by a decoupled look-back over the
-//                    tiles' depth deltas, and the tile's stack slice (its
-//                    unmatched opens, Sec. 7.1) with the running
-//                    intersection of their clip boxes (Sec. 9).
+//                    summary Bic(tile) = (a, b) (Sec. 3) and depth change,
+//                    and the tile's stack slice (its unmatched opens,
+//                    Sec. 7.1) with the running intersection of their clip
+//                    boxes (Sec. 9).
+//   k1_tile_prefix   one block: the global depth at every tile start (scan
+//                    of the tiles' depth changes), the balance checks, and
+//                    the min tree over the tiles' lowest depths.
 //   k2_tile_resolve  the tile-level tree: for every tile the owner of the
 //                    depth just below its slice (ps) and of the depth just
 //                    below its start (q), found by the up/down tree search
@@ -74,16 +76,6 @@ __device__ __forceinline__ bool load_kinds(const uint8_t* __restrict__ kind, int
   return bad;
 }
 
-__device__ __forceinline__ unsigned long long lb_pack(unsigned flag, int v) {
-  return ((unsigned long long)flag << 32) | (unsigned long long)(unsigned)v;
-}
-
-__device__ __forceinline__ int warp_sum(int v) {
-#pragma unroll
-  for (int m = 16; m >= 1; m >>= 1) v += shfl_xor(v, m);
-  return v;
-}
-
 // ------------------------------------------------------------------- K1
 struct K1Args {
   const uint8_t* kind;
@@ -91,7 +83,6 @@ struct K1Args {
   int n;
   SceneWs ws;
   int* status;
-  int withhold;  // tile that never publishes (self-test of the bounded wait); -1 normally
 };
 
 template <bool HAS_BOX>
@@ -99,13 +90,8 @@ __global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
   __shared__ int s_scr[NW + 1];
   __shared__ int2 s_scr2[NW + 1];
   __shared__ float4 s_fscr[NW + 1];
-  __shared__ int s_t;
   const int tid = threadIdx.x;
-  // Tiles are numbered in the order blocks start, so every tile a block
-  // waits for belongs to a block that is already running.
-  if (tid == 0) s_t = (int)atomic_add_u32(a.ws.counter, 1u);
-  __syncthreads();
-  const int t = s_t;
+  const int t = blockIdx.x;
   const int base = t * TILE, p0 = tid * KPT;
 
   uint8_t kk[KPT];
@@ -131,10 +117,11 @@ __global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
   const int a_t = -tile_lo;  // Bic(tile).a: closes that pop below the tile start
   const int b_t = tot + a_t;  // Bic(tile).b: opens left unmatched at the tile end
   const int suf_after = block_excl_suffix_min(ds + mn_after, s_scr);
-
-  // Publish this tile's depth delta at once: later tiles may sum it while
-  // this block is still busy.
-  if (threadIdx.x == 0 && t != a.withhold) st_release_u64(a.ws.lb + t, lb_pack(1u, tot));
+  if (tid == 0) {
+    a.ws.t_a[t] = a_t;
+    a.ws.t_b[t] = b_t;
+    a.ws.t_tot[t] = tot;
+  }
 
   // The tile's stack slice: an open is unmatched in the tile when the depth
   // never comes back below its level before the tile ends.  Its slot is its
@@ -172,66 +159,107 @@ __global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
       }
     }
   }
+}
 
-  // Decoupled look-back (single pass) for the global depth at the tile
-  // start: this tile's depth delta was published above; warp 0 adds
-  // predecessors' deltas 32 tiles per poll until one that knows its
-  // inclusive prefix.  It runs last, after all the tile-local work, so no
-  // barrier of the block waits for it.
-  if (warp_id() == 0) {
-    const int lane = lane_id();
-    unsigned long long* lb = a.ws.lb;
-    int excl = 0;
-    bool timed_out = false;
-    for (int hi = t - 1; hi >= 0; hi -= 32) {
-      const int j = hi - lane;
-      unsigned flag = 2u;  // before tile 0: inclusive prefix 0
-      int val = 0;
-      if (j >= 0) {
-        unsigned long long w = 0;
-        unsigned it = 0;
-        for (;;) {
-          w = ld_acquire_u64(lb + j);
-          if ((w >> 32) != 0) break;
-          if (++it >= SPIN_LIMIT) break;
-          poll_backoff(it);
+// Global depth at every tile start (Sec. 3: the tiles' bicyclic summaries
+// combine in order; only their depth changes are needed here), in one block:
+// an exclusive scan of the tiles' depth changes, the tiles' lowest depths,
+// the balance checks, and the min tree over the lowest depths that the owner
+// searches of the tile-level resolve use (leaves at [P, 2P), the ones past
+// the last tile above any depth).  Warp w owns the leaves
+// [w * span, (w + 1) * span) and walks them 32 at a time (coalesced); each
+// such group's five lowest tree levels come from shuffles, the levels above
+// from global memory while a level is wide, then from shared memory.
+constexpr int NT2 = 1024;
+
+__global__ void __launch_bounds__(NT2) k1_tile_prefix(SceneWs ws, int* status) {
+  constexpr int NWP = NT2 / 32;
+  __shared__ int s_w[NWP];
+  __shared__ int s_top[2 * NT2];
+  const int T = ws.T, P = ws.P, tid = threadIdx.x, lane = lane_id(), wid = warp_id();
+  int* tree = ws.lo_tree;
+  const int LP = 31 - __clz(P);                 // P = 2^LP
+  const int span = P / NWP > 32 ? P / NWP : 32;
+  const int base = wid * span;
+  const int rounds = base < P ? span / 32 : 0;  // warp-uniform
+  // the warp's total depth change (RB rounds of loads in flight at a time)
+  constexpr int RB = 4;
+  int sum = 0;
+  for (int r0 = 0; r0 < rounds; r0 += RB) {
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+      const int t = base + (r0 + k) * 32 + lane;
+      if (r0 + k < rounds && t < T) sum += __ldg(ws.t_tot + t);
+    }
+  }
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) sum += shfl_xor(sum, m);
+  if (lane == 0) s_w[wid] = sum;
+  __syncthreads();
+  if (wid == 0) {
+    const int v = s_w[lane];
+    const int incl = warp_incl_scan(v, OpAdd());
+    s_w[lane] = incl - v;  // exclusive prefix of the warps
+    if (lane == NWP - 1 && incl != 0) atomic_cas_i32(status, ST_OK, ST_UNBALANCED);  // ends above 0
+  }
+  __syncthreads();
+  int carry = s_w[wid];
+  bool bad = false;
+  for (int r0 = 0; r0 < rounds; r0 += RB) {
+    int vt[RB], va[RB];
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+      const int t = base + (r0 + k) * 32 + lane;
+      const bool in = r0 + k < rounds && t < T;
+      vt[k] = in ? __ldg(ws.t_tot + t) : 0;
+      va[k] = in ? __ldg(ws.t_a + t) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+      if (r0 + k < rounds) {  // warp-uniform
+        const int t = base + (r0 + k) * 32 + lane;
+        const int incl = warp_incl_scan(vt[k], OpAdd());
+        const int excl = carry + incl - vt[k];
+        int v = 0x7f7f7f7f;  // past the last tile: above any depth
+        if (t < T) {
+          v = excl - va[k];
+          ws.t_dstart[t] = excl;
+          ws.t_lo[t] = v;
+          bad |= v < 0;  // a close pops below the root
         }
-        flag = (unsigned)(w >> 32);
-        val = (int)(unsigned)(w & 0xffffffffull);
-        if (flag == 0u) {
-          timed_out = true;
-          flag = 2u;
-          val = 0;
+        if (t < P) tree[P + t] = v;
+        carry += shfl_idx(incl, 31);
+#pragma unroll
+        for (int l = 1; l <= 5; ++l) {
+          v = min(v, shfl_xor(v, 1 << (l - 1)));
+          if (l <= LP && (lane & ((1 << l) - 1)) == 0 && t < P) tree[(P + t) >> l] = v;
         }
       }
-      const unsigned incl = ballot(flag == 2u);
-      if (incl != 0u && lane > lowest_set(incl)) val = 0;
-      excl += warp_sum(val);
-      if (incl != 0u) break;
     }
-    const bool any_timeout = ballot(timed_out) != 0u;
-    if (lane == 0) {
-      if (any_timeout) atomic_cas_i32(a.status, ST_OK, ST_TIMEOUT);
-      if (t != a.withhold) st_release_u64(lb + t, lb_pack(2u, excl + tot));
-      a.ws.t_a[t] = a_t;
-      a.ws.t_b[t] = b_t;
-      a.ws.t_dstart[t] = excl;
-      a.ws.t_lo[t] = excl - a_t;
-      // min tree over the tiles' lowest depths for the owner searches: this
-      // tile's leaf and the minimum along its path to the root (the tree
-      // starts out filled with 0x7f7f7f7f, above any depth)
-      a.ws.lo_tree[a.ws.P + t] = excl - a_t;
-      for (int i = (a.ws.P + t) >> 1; i >= 1; i >>= 1) atomic_min_i32(&a.ws.lo_tree[i], excl - a_t);
-      if (excl - a_t < 0) atomic_cas_i32(a.status, ST_OK, ST_UNBALANCED);
-      if (t == a.ws.T - 1 && excl + tot != 0) atomic_cas_i32(a.status, ST_OK, ST_UNBALANCED);
+  }
+  if (bad) atomic_cas_i32(status, ST_OK, ST_UNBALANCED);
+  __syncthreads();
+  // Levels above the fifth: nodes [h, 2h) from [2h, 4h), in global memory
+  // while a level has more nodes than half the block, then in shared memory.
+  int h = P >> 6;
+  for (; h > NT2 / 2; h >>= 1) {
+    for (int i = h + tid; i < 2 * h; i += NT2) tree[i] = min(tree[2 * i], tree[2 * i + 1]);
+    __syncthreads();
+  }
+  if (h >= 1) {
+    for (int i = 2 * h + tid; i < 4 * h; i += NT2) s_top[i] = tree[i];  // i < 4h <= 2 * NT2
+    __syncthreads();
+    for (int g = h; g >= 1; g >>= 1) {
+      for (int i = g + tid; i < 2 * g; i += NT2) s_top[i] = min(s_top[2 * i], s_top[2 * i + 1]);
+      __syncthreads();
     }
+    for (int i = 1 + tid; i < 2 * h; i += NT2) tree[i] = s_top[i];
   }
 }
 
 // ------------------------------------------------------------------- K2
 // Tile-level resolve, one thread per tile.  lo_tree, the min tree over the
-// tiles' lowest depths, was built by k1_tile_summary.
-constexpr int NT2 = 1024;
+// tiles' lowest depths, was built by k1_tile_prefix.
 constexpr int NTR = 256;
 
 // Owner links: ps = owner of depth lo - 1 (last earlier tile whose lowest
@@ -505,7 +533,7 @@ __device__ __forceinline__ OutRes out_lookup(const OutCtx& c, const SceneWs& ws,
 
 // One block per tile, or (TB_PERSIST) a grid of resident blocks that take
 // tiles in order from a ticket counter (counter[1] of the workspace, zeroed
-// with the look-back words), the next ticket drawn while the current tile is
+// at the start of each call), the next ticket drawn while the current tile is
 // processed.  The per-tile code below is the same in both builds; it leaves a
 // tile through K3_TILE_DONE (a return, or a break to the next ticket).  The
 // matching-only pass is held to 64 registers a thread so that 1024 threads

@@ -108,6 +108,7 @@ TreeWs tree_ws(const TreeLayout& L, void* ws, int64_t n, int J) {
   w.TE = L.TE;
   w.TJ = (J + JT - 1) / JT;
   w.PJ = next_pow2(w.TJ > 0 ? w.TJ : 1);
+  w.withhold = tb_internal::withheld_tile();
   return w;
 }
 
@@ -127,7 +128,8 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 tb_status prelude(const uint8_t* kind, int64_t n, int J, const TreeLayout& L, void* ws,
                   int32_t* d_status, cudaStream_t s, TreeWs* out) {
   unsigned char* b = static_cast<unsigned char*>(ws);
-  const TreeWs w = tree_ws(L, ws, n, J);
+  TreeWs w = tree_ws(L, ws, n, J);
+  w.status = d_status;
   if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return TB_ERR_CUDA;
   if (cudaMemsetAsync(b + L.lb, 0, L.zero_end - L.lb, s) != cudaSuccess) return TB_ERR_CUDA;
   tb_internal::phase_mark(s);

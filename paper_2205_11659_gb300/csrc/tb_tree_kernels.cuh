@@ -230,6 +230,10 @@ struct TreeWs {
   int TE;        // element tiles (TTILE elements each)
   int TJ;        // joint tiles (JT joints each)
   int PJ;        // next power of two >= TJ
+  int withhold;  // element tile that never publishes its look-back word
+                 // (self-test of the bounded wait); -1 normally
+  const int* status;  // status word of the call: the kernels after the depth
+                      // pass stop at once when it already holds an error
 };
 
 // ------------------------------------------------------------- joint tree
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(TNT) k_tdepth(const uint8_t* __restrict__ kind
   if (warp_id() == 0) {
     const int lane = lane_id();
     unsigned long long* lb = w.lb;
-    if (lane == 0) st_release_u64(lb + t, oc_pack(1u, (unsigned)tot_o, (unsigned)tot_c));
+    if (lane == 0 && t != w.withhold) st_release_u64(lb + t, oc_pack(1u, (unsigned)tot_o, (unsigned)tot_c));
     unsigned xo = 0, xc = 0;
     bool timed_out = false;
     for (int hi = t - 1; hi >= 0; hi -= 32) {
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(TNT) k_tdepth(const uint8_t* __restrict__ kind
     const bool any_timeout = ballot(timed_out) != 0u;
     if (lane == 0) {
       if (any_timeout) atomic_cas_i32(status, ST_OK, ST_TIMEOUT);
-      st_release_u64(lb + t, oc_pack(2u, xo + (unsigned)tot_o, xc + (unsigned)tot_c));
+      if (t != w.withhold) st_release_u64(lb + t, oc_pack(2u, xo + (unsigned)tot_o, xc + (unsigned)tot_c));
       s_o = xo;
       s_c = xc;
       const long long d0 = (long long)xo - (long long)xc;
@@ -355,6 +359,7 @@ __global__ void __launch_bounds__(TNT) k_tdepth(const uint8_t* __restrict__ kind
 // Per joint tile: inclusive prefix and suffix minima of jdepth, tile minimum.
 __global__ void __launch_bounds__(TNT) k_jminmax(TreeWs w) {
   __shared__ int s_scr[TNW + 1];
+  if (*w.status != ST_OK) return;  // the joint depths are not valid
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT, cnt = min(JT, w.J - R0);
   int d[JC];
@@ -389,6 +394,7 @@ __global__ void __launch_bounds__(TNT) k_jminmax(TreeWs w) {
 // Min tree over the joint tiles (one block); leaves past the last tile hold
 // INT_MAX.
 __global__ void __launch_bounds__(1024) k_jmin_tree(TreeWs w) {
+  if (*w.status != ST_OK) return;
   const int P = w.PJ;
   for (int t = w.TJ + threadIdx.x; t < P; t += blockDim.x) w.g_tree[P + t] = INT_MAX;
   for (int h = P / 2; h >= 1; h >>= 1) {
@@ -428,6 +434,7 @@ __global__ void __launch_bounds__(TNT) k_jstruct(TreeWs w, const void* __restric
   __shared__ int s_q[2 * JT];
   __shared__ int s_nq;
   __shared__ int s_scri[TNW + 1];
+  if (*w.status != ST_OK) return;
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT, R1 = R0 + JT;
   const int cnt = min(JT, w.J - R0);
@@ -645,6 +652,7 @@ __global__ void __launch_bounds__(TNT) k_jstruct(TreeWs w, const void* __restric
 template <class M>
 __global__ void __launch_bounds__(1024) k_down_tiles(TreeWs w, int* status) {
   using V = typename M::V;
+  if (*w.status != ST_OK) return;
   const int TJ = w.TJ;
   bool bad = false;
   for (int t = threadIdx.x; t < TJ; t += blockDim.x) {
@@ -707,6 +715,7 @@ __global__ void __launch_bounds__(TNT, 2) k_down_tile(TreeWs w, const void* __re
   V* s_cm = s_val + JSLOTS;
   int* s_anc = reinterpret_cast<int*>(s_cm + NCH);
   int* s_cl = s_anc + JT;
+  if (*w.status != ST_OK) return;
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT;
   const int cnt = min(JT, w.J - R0);
@@ -933,6 +942,7 @@ __global__ void __launch_bounds__(TNT, 2) k_up_tile(TreeWs w, Values values, voi
   V* s_val = reinterpret_cast<V*>(smem);
   V* s_tree = s_val + JSLOTS;  // chunk totals at [NCH, 2 NCH)
   int* s_end = reinterpret_cast<int*>(s_tree + 2 * NCH);  // local subtree ends
+  if (*w.status != ST_OK) return;
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT;
   const int cnt = min(JT, w.J - R0);
@@ -994,6 +1004,7 @@ __global__ void __launch_bounds__(TNT, 2) k_up_tile(TreeWs w, Values values, voi
 template <class M>
 __global__ void __launch_bounds__(1024) k_up_tiles(TreeWs w) {
   using V = typename M::V;
+  if (*w.status != ST_OK) return;
   const int P = w.PJ;
   for (int t = threadIdx.x; t < P; t += blockDim.x)
     M::store(w.t_tree, P + t,
@@ -1013,6 +1024,7 @@ __global__ void __launch_bounds__(1024) k_up_tiles(TreeWs w) {
 template <class M, class Values, class Finish>
 __global__ void k_up_cross(TreeWs w, Values values, void* __restrict__ out, Finish fin) {
   using V = typename M::V;
+  if (*w.status != ST_OK) return;
   const int count = (int)*w.xcount;
   const void* tree = w.t_tree;
   auto node = [tree](int i) { return M::load(tree, i); };

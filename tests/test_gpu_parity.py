@@ -253,25 +253,16 @@ def test_host_pipeline_matching_only():
         pipe.run(kinds, kinds, outs)
 
 
-def test_lookback_timeout_reported_and_recovered():
-    """A tile that never publishes makes the bounded look-back waits of the
-    tiles after it give up: the call reports TB_ERR_TIMEOUT (after about a
-    second), and the next call on the same context is correct."""
-    import time
+def test_withhold_hook_leaves_scene_passes_alone():
+    """The scene passes have no cross-block wait (the tile depths come from
+    a one-block scan): the look-back test hook does not affect them."""
     k, b = inputs.random_walk_scene(64 * TILE, 77)
     kd, bd = torch.from_numpy(k).cuda(), torch.from_numpy(b).cuda()
     assert binding.tb_debug_withhold_tile(5) == binding.TB_OK
     try:
-        t0 = time.perf_counter()
-        with pytest.raises(binding.TBError) as ei:
-            binding.bboxes(kd, bd)
-        assert ei.value.code == binding.TB_ERR_TIMEOUT
-        assert time.perf_counter() - t0 < 30.0
+        p, m, o = binding.bboxes(kd, bd)
     finally:
         assert binding.tb_debug_withhold_tile(-1) == binding.TB_OK
     st, op, om, ob = oracle.bboxes(k, b)
-    p, m, o = binding.bboxes(kd, bd)
-    torch.cuda.synchronize()
     assert np.array_equal(p.cpu().numpy(), op) and np.array_equal(m.cpu().numpy(), om)
     assert same_bits(o.cpu().numpy(), ob)
-    assert binding.tb_debug_withhold_tile(-2) == binding.TB_ERR_INVALID_ARG

@@ -271,3 +271,27 @@ def test_errors_reported_in_status():
     out = binding.tree_scan(binding.TB_MONOID_ADD_I32, binding.TB_UP, kd, v)
     st, ref = oracle.tree_scan_i32(oracle.UP, k, np.ones(J, np.int32))
     assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_lookback_timeout_reported_and_recovered():
+    """An element tile of the depth pass that never publishes makes the
+    bounded look-back waits of the tiles after it give up: the call reports
+    TB_ERR_TIMEOUT (after about a second), and the next call on the same
+    context is correct."""
+    import time
+    k, L, _ = inputs.skeleton(1 << 16, 21)  # 2^17 elements: 32 element tiles
+    kd, Ld = torch.from_numpy(k).cuda(), torch.from_numpy(L).cuda()
+    assert binding.tb_debug_withhold_tile(5) == binding.TB_OK
+    try:
+        t0 = time.perf_counter()
+        with pytest.raises(binding.TBError) as ei:
+            binding.tree_scan(binding.TB_MONOID_AFFINE3X4_F32, binding.TB_DOWN, kd, Ld)
+        assert ei.value.code == binding.TB_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 30.0
+    finally:
+        assert binding.tb_debug_withhold_tile(-1) == binding.TB_OK
+    world = binding.tree_scan(binding.TB_MONOID_AFFINE3X4_F32, binding.TB_DOWN, kd, Ld)
+    st, ref = oracle.affine_forward(k, L.astype(np.float64))
+    assert st == oracle.OK
+    assert rel_err(world.cpu().numpy(), ref) < REL_TOL
+    assert binding.tb_debug_withhold_tile(-2) == binding.TB_ERR_INVALID_ARG
