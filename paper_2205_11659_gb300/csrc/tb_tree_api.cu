@@ -119,6 +119,9 @@ int grid_for(int items, int per_block) {
   return g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g);
 }
 
+// Largest dynamic shared memory of one block on this architecture (227 KB).
+constexpr size_t kMaxBlockSmem = 227 * 1024;
+
 template <class K>
 cudaError_t allow_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -159,7 +162,17 @@ tb_status launch_down(const TreeWs& w, const void* in, void* out, int32_t* d_sta
   tb_status st = launch_jstruct<M, true>(w, in, s);
   if (st != TB_OK) return st;
   tb_internal::phase_mark(s);
-  k_down_tiles<M><<<1, 1024, 0, s>>>(w, d_status);
+  const size_t tsm = down_tiles_smem<M>(w.TJ);
+  if (tsm <= kMaxBlockSmem) {
+    static bool tiles_attr = false;
+    if (!tiles_attr) {
+      if (allow_smem(k_down_tiles<M, true>, kMaxBlockSmem) != cudaSuccess) return TB_ERR_CUDA;
+      tiles_attr = true;
+    }
+    k_down_tiles<M, true><<<1, 1024, tsm, s>>>(w, d_status);
+  } else {
+    k_down_tiles<M, false><<<1, 1024, 0, s>>>(w, d_status);
+  }
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   tb_internal::phase_mark(s);
   constexpr size_t smem = down_tile_smem<M>();

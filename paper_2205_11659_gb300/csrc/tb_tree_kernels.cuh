@@ -648,12 +648,28 @@ __global__ void __launch_bounds__(TNT) k_jstruct(TreeWs w, const void* __restric
 
 // ------------------------------------------------------------- DOWN
 // Pointer jumping over the tiles (one block): the fold at each tile's base is
-// the fold at its base's tile base times the base's chain prefix.
+// the fold at its base's tile base times the base's chain prefix.  With SM
+// the link and value buffers live in shared memory (down_tiles_smem bytes),
+// otherwise in the workspace.
 template <class M>
+constexpr size_t down_tiles_smem(int TJ) {
+  return (size_t)2 * TJ * (sizeof(typename M::V) + sizeof(int));
+}
+
+template <class M, bool SM>
 __global__ void __launch_bounds__(1024) k_down_tiles(TreeWs w, int* status) {
   using V = typename M::V;
+  TB_DYNAMIC_SMEM(smem);
   if (*w.status != ST_OK) return;
   const int TJ = w.TJ;
+  V* sv = reinterpret_cast<V*>(smem);              // values of buffers 0 and 1
+  int* sl = reinterpret_cast<int*>(sv + 2 * TJ);  // links of buffers 0 and 1
+  auto link = [&](int buf, int t) -> int& { return SM ? sl[buf * TJ + t] : w.t_link[buf][t]; };
+  auto val = [&](int buf, int t) -> V { return SM ? sv[buf * TJ + t] : M::load(w.t_val[buf], t); };
+  auto set_val = [&](int buf, int t, const V& v) {
+    if (SM) sv[buf * TJ + t] = v;
+    else M::store(w.t_val[buf], t, v);
+  };
   bool bad = false;
   for (int t = threadIdx.x; t < TJ; t += blockDim.x) {
     const int b = w.t_base[t];
@@ -668,8 +684,8 @@ __global__ void __launch_bounds__(1024) k_down_tiles(TreeWs w, int* status) {
         v = M::load(w.relT, b);
       }
     }
-    w.t_link[0][t] = l;
-    M::store(w.t_val[0], t, v);
+    link(0, t) = l;
+    set_val(0, t, v);
     if (l < 0) M::store(w.t_world, t, v);
   }
   if (bad) atomic_cas_i32(status, ST_OK, ST_INVALID);
@@ -678,17 +694,17 @@ __global__ void __launch_bounds__(1024) k_down_tiles(TreeWs w, int* status) {
     __syncthreads();
     bool any = false;
     for (int t = threadIdx.x; t < TJ; t += blockDim.x) {
-      const int l = w.t_link[cur][t];
-      V v = M::load(w.t_val[cur], t);
+      const int l = link(cur, t);
+      V v = val(cur, t);
       int nl = -1;
       if (l >= 0) {
-        v = M::combine(M::load(w.t_val[cur], l), v);
-        nl = w.t_link[cur][l];
+        v = M::combine(val(cur, l), v);
+        nl = link(cur, l);
         if (nl < 0) M::store(w.t_world, t, v);
         else any = true;
       }
-      w.t_link[cur ^ 1][t] = nl;
-      M::store(w.t_val[cur ^ 1], t, v);
+      link(cur ^ 1, t) = nl;
+      set_val(cur ^ 1, t, v);
     }
     cur ^= 1;
     if (!block_or(any)) break;

@@ -145,6 +145,31 @@ def test_skeleton_2p20_forward_backward():
     assert e_bwd < REL_TOL, e_bwd
 
 
+@pytest.mark.parametrize("J", [1 << 21, 2_400_000])
+def test_many_joint_tiles(J):
+    """2048 and 2344 joint tiles: the pointer jumping over tiles keeps its
+    buffers in shared memory (2048 tiles) or in the workspace (2344), and
+    the tile-level trees have several thousand leaves."""
+    k, L, W = inputs.skeleton(J, 31)
+    v = (np.arange(J, dtype=np.int64) * 2654435761 % 1000 - 500).astype(np.int32)
+    kd = torch.from_numpy(k).cuda()
+    for d in (oracle.DOWN, oracle.UP):
+        st, ref = oracle.tree_scan_i32(d, k, v)
+        assert st == oracle.OK
+        out = binding.tree_scan(binding.TB_MONOID_ADD_I32, binding.TB_DOWN if d == oracle.DOWN
+                                else binding.TB_UP, kd, torch.from_numpy(v).cuda())
+        assert np.array_equal(out.cpu().numpy(), ref)
+    Ld, Wd = torch.from_numpy(L).cuda(), torch.from_numpy(W).cuda()
+    world = binding.tree_scan(binding.TB_MONOID_AFFINE3X4_F32, binding.TB_DOWN, kd, Ld)
+    grad = binding.affine_backward(kd, Ld, Wd)
+    st, world_ref = oracle.affine_forward(k, L.astype(np.float64))
+    assert st == oracle.OK
+    assert rel_err(world.cpu().numpy(), world_ref) < REL_TOL
+    st, grad_ref = oracle.affine_backward(k, L.astype(np.float64), W.astype(np.float64))
+    assert st == oracle.OK
+    assert rel_err(grad.cpu().numpy(), grad_ref) < REL_TOL
+
+
 def test_backward_vs_fp64_finite_differences():
     """64-joint skeleton: the GPU adjoint against central differences of the
     fp64 oracle loss."""
