@@ -4,7 +4,7 @@ differentiable transform tree scan on GB300.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload rw26|match26|chain24|flat24|batched|rw24|rw16|skel20|skel20s|skelbatch]
 
-Scene workloads: one step = one full pass (tile summaries with look-back,
+Scene workloads: one step = one full pass (tile summaries and tile scan,
 tile-level resolve, main tile pass, cross-tile unions) over one synthetic
 scene already resident in HBM.  Skeleton workloads: one step = the affine
 DOWN scan (forward) plus its adjoint (backward) over the joint stream.
@@ -12,8 +12,8 @@ Prints one JSON line (rank 0).  With N > 1 (torchrun), each rank runs its own
 replica of the workload on its own GPU (independent scenes, no collective on
 the data path) and the value is the whole-job throughput.
 
-``--impl reference`` times the sequential CPU oracle (the checker) on the
-same workload on the host cores instead.
+``--impl reference`` times the sequential CPU oracle on the same workload on
+the host cores instead.
 """
 import argparse
 import hashlib

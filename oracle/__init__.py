@@ -1,6 +1,6 @@
 """Sequential CPU oracle (test infrastructure only).
 
-This package is the checker, not the product: only ``tests/``,
+This package is test infrastructure, not the product: only ``tests/``,
 ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference``
 legs of ``bench.py`` may import it.  It shares no code with the CUDA path and
 never imports it.  The arithmetic lives in ``tb_oracle.c`` (plain C, compiled

@@ -250,8 +250,8 @@ __device__ __forceinline__ T tree_range(const T* tree, int P, int l, int r, T id
 
 // ------------------------------------------------------------- workspace
 // Device view of the scratch of one scene pass.  Per tile t:
-//   lb[t]        look-back word (flag << 32 | value) for the depth prefix
 //   t_a, t_b     Bic(tile) = (unmatched closes, unmatched opens)
+//   t_tot        depth change over the tile (t_b - t_a)
 //   t_dstart     global depth before the tile's first element
 //   t_lo         t_dstart - t_a, the lowest depth the tile reaches
 //   t_ps         last earlier tile whose lo is below t_lo (owner of depth
