@@ -352,18 +352,24 @@ def run_tree(args, torch, world, rank, dev):
         if rc != binding.TB_OK:
             raise binding.TBError(rc, "backward")
 
+    def bwd_reuse(st):
+        # the backward that reads the joint structure the forward left in ws
+        return binding.tb_tree_scan_affine_backward_reuse(k_d, n, J, L_d, W_d, grad_d, ws, nb,
+                                                          status, st)
+
     graph = None
     if not batched:
-        # the plain forward + backward calls, captured once in a CUDA graph
+        # the forward and the structure-reusing backward, captured once in a
+        # CUDA graph
         fwd()
-        bwd()
+        assert bwd_reuse(stream) == binding.TB_OK
         torch.cuda.synchronize()
+        assert int(status.item()) == binding.TB_OK
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph):
             rc1 = binding.tb_tree_scan(binding.TB_MONOID_AFFINE3X4_F32, binding.TB_DOWN, k_d, n, J,
                                        L_d, world_d, ws, nb, status, None)
-            rc2 = binding.tb_tree_scan_affine_backward(k_d, n, J, L_d, W_d, grad_d, ws, nb, status,
-                                                       None)
+            rc2 = bwd_reuse(None)
         assert rc1 == binding.TB_OK and rc2 == binding.TB_OK
     if batched:
         # forward + backward through the autograd function, one graph
@@ -375,12 +381,12 @@ def run_tree(args, torch, world, rank, dev):
         with torch.cuda.stream(side):
             for _ in range(2):
                 local.grad = None
-                (binding.TreeTransform.apply(k_d, local, False) * W_d).sum().backward()
+                (binding.TreeTransform.apply(k_d, local, False, True) * W_d).sum().backward()
         stream.wait_stream(side)
         graph = torch.cuda.CUDAGraph()
         local.grad = None
         with torch.cuda.graph(graph):
-            (binding.TreeTransform.apply(k_d, local, False) * W_d).sum().backward()
+            (binding.TreeTransform.apply(k_d, local, False, True) * W_d).sum().backward()
 
     in_bytes = kind.nbytes + L.nbytes + W.nbytes
     flush = L2Flush(torch, dev, in_bytes)
@@ -461,6 +467,9 @@ def run_tree(args, torch, world, rank, dev):
                                                       k_d, n, J, L_d, world_d, ws, nb, status, st))
     bwd_ms = graph_ms(lambda st: binding.tb_tree_scan_affine_backward(k_d, n, J, L_d, W_d, grad_d, ws,
                                                                       nb, status, st))
+    # the structure-reusing backward alone (ws holds the structure of the
+    # same stream from the calls above)
+    bwd_reuse_ms = graph_ms(bwd_reuse)
     assert int(status.item()) == binding.TB_OK
 
     per_scene = None
@@ -478,7 +487,8 @@ def run_tree(args, torch, world, rank, dev):
                 ns, js = kk.numel(), ll.shape[0]
                 binding.tb_tree_scan(binding.TB_MONOID_AFFINE3X4_F32, binding.TB_DOWN, kk, ns, js, ll,
                                      wo, ws, nb, status, stream)
-                binding.tb_tree_scan_affine_backward(kk, ns, js, ll, wg, go, ws, nb, status, stream)
+                binding.tb_tree_scan_affine_backward_reuse(kk, ns, js, ll, wg, go, ws, nb, status,
+                                                           stream)
         per_scene_step()
         torch.cuda.synchronize()
         reps = max(2, min(K, 5))
@@ -492,7 +502,7 @@ def run_tree(args, torch, world, rank, dev):
         ps_ms = p0.elapsed_time(p1) / reps
         assert int(status.item()) == binding.TB_OK
         per_scene = {"value": round(n / (ps_ms * 1e-3) / 1e9, 3), "unit": "Gelem/s",
-                     "ms_per_step": round(ps_ms, 4), "launches": "%d x (forward + backward) plain calls" % S,
+                     "ms_per_step": round(ps_ms, 4), "launches": "%d x (forward + structure-reusing backward) plain calls" % S,
                      "batched_over_per_scene": round(ps_ms / ms_step, 2)}
 
     # end to end through the public API with pinned host buffers
@@ -506,12 +516,16 @@ def run_tree(args, torch, world, rank, dev):
         kd = kind_h.to(dev, non_blocking=True)
         ld = L_h.to(dev, non_blocking=True)
         wd = W_h.to(dev, non_blocking=True)
-        wo = binding.tree_scan(binding.TB_MONOID_AFFINE3X4_F32, binding.TB_DOWN, kd, ld, check=False)
-        go = binding.affine_backward(kd, ld, wd, check=False)
+        wo = torch.empty_like(ld)
+        go = torch.empty_like(ld)
+        assert binding.tb_tree_scan(binding.TB_MONOID_AFFINE3X4_F32, binding.TB_DOWN, kd, n, J, ld,
+                                    wo, ws, nb, status, stream) == binding.TB_OK
+        assert binding.tb_tree_scan_affine_backward_reuse(kd, n, J, ld, wd, go, ws, nb, status,
+                                                          stream) == binding.TB_OK
         world_h.copy_(wo, non_blocking=True)
         grad_h.copy_(go, non_blocking=True)
         stream.synchronize()
-        binding.check_status(binding.workspace(dev), "e2e")
+        assert int(status.item()) == binding.TB_OK
     e2e_step()
     e2e_steps = max(2, min(K, 5))
     t0 = time.perf_counter()
@@ -535,20 +549,27 @@ def run_tree(args, torch, world, rank, dev):
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "n": n, "joints": J, "seed": 0,
                        "gjoint_per_s": round(world * J / (ms_step * 1e-3) / 1e9, 3),
-                       "step": "one CUDA graph of TreeTransform forward + backward" if batched
+                       "step": "one CUDA graph of TreeTransform forward + backward "
+                               "(keep_structure=True)" if batched
                                else "one CUDA graph of tb_tree_scan (affine DOWN) + "
-                                    "tb_tree_scan_affine_backward",
+                                    "tb_tree_scan_affine_backward_reuse",
                        "l2": flush.describe(in_bytes),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "kernel": "tb_tree_scan_affine_backward (all its launches)",
-                         "achieved": round(bwd_alg / (bwd_ms * 1e-3) / 1e9, 1), "peak": peak,
+            "roofline": {"bound": "hbm",
+                         "kernel": "tb_tree_scan_affine_backward_reuse (all its launches; the joint "
+                                   "structure the step's forward left in the workspace)",
+                         "achieved": round(bwd_alg / (bwd_reuse_ms * 1e-3) / 1e9, 1), "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s",
-                         "frac": round(bwd_alg / (bwd_ms * 1e-3) / 1e9 / peak, 4), "traffic": None,
-                         "algorithmic_bytes_per_launch": bwd_alg},
+                         "frac": round(bwd_alg / (bwd_reuse_ms * 1e-3) / 1e9 / peak, 4),
+                         "traffic": None, "algorithmic_bytes_per_launch": bwd_alg},
             "forward_roofline_frac": round(FWD_BYTES_PER_JOINT * J / (fwd_ms * 1e-3) / 1e9 / peak, 4),
-            "forward_ms": round(fwd_ms, 4), "backward_ms": round(bwd_ms, 4),
+            "standalone_backward_roofline_frac": round(bwd_alg / (bwd_ms * 1e-3) / 1e9 / peak, 4),
+            "forward_ms": round(fwd_ms, 4), "backward_reuse_ms": round(bwd_reuse_ms, 4),
+            "standalone_backward_ms": round(bwd_ms, 4),
+            "step_roofline_frac": round((FWD_BYTES_PER_JOINT + BWD_BYTES_PER_JOINT) * world * J /
+                                        (ms_step * 1e-3) / 1e9 / peak, 4),
             "forward_backward_plain_calls_ms": [round(fwd_calls_ms, 4), round(bwd_calls_ms, 4)],
-            "backward_gjoint_per_s": round(J / (bwd_ms * 1e-3) / 1e9, 3),
+            "backward_gjoint_per_s": round(J / (bwd_reuse_ms * 1e-3) / 1e9, 3),
             "phases_ms": {"forward": {k: round(v, 4) for k, v in fph.items()},
                           "backward": {k: round(v, 4) for k, v in bph.items()}},
             "per_scene": per_scene,
@@ -556,7 +577,7 @@ def run_tree(args, torch, world, rank, dev):
             "e2e": {"value": round(world * n / e2e_s / 1e9, 3), "unit": "Gelem/s",
                     "h2d_bytes_per_step": int(kind.nbytes + L.nbytes + W.nbytes),
                     "d2h_bytes_per_step": int(2 * L.nbytes)},
-            "gpu_launches": (6 + 9) * K,
+            "gpu_launches": (6 + 6) * K,
             "clocks": clk,
             "kernel_hash": kernel_hash(),
         }

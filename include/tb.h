@@ -160,6 +160,28 @@ tb_status tb_tree_scan_affine_backward(const uint8_t* kind, int64_t n,
                                        size_t ws_bytes, int32_t* d_status,
                                        void* stream);
 
+/* tb_tree_scan_affine_backward after a scan of the same stream: the joint
+ * structure (joint depths, parents and subtree ends) is read from ws instead
+ * of being computed again; the forward transforms are still recomputed.
+ * ws (at least tb_workspace_size(TB_OP_TREE_BACKWARD, n) bytes) must hold
+ * what the last tb_tree_scan(..., TB_DOWN or TB_UP, ...) or
+ * tb_tree_scan_affine_backward call that used it left there, for this kind
+ * stream, n and num_joints, with nothing else writing ws in between.  That
+ * call records n and num_joints in ws once the structure is complete (its
+ * d_status TB_OK); when they differ, or that call failed, this call reports
+ * TB_ERR_INVALID_ARG in d_status and writes no gradients.  A different kind
+ * stream of the same n and num_joints is not detected and gives wrong
+ * gradients (every memory access stays inside the buffers all the same).
+ * Arguments and results otherwise as tb_tree_scan_affine_backward.  No paper
+ * counterpart: the reuse an autograd pair (forward, then its backward) can
+ * make of the forward's workspace. */
+tb_status tb_tree_scan_affine_backward_reuse(const uint8_t* kind, int64_t n,
+                                             int64_t num_joints, const float* local,
+                                             const float* grad_world,
+                                             float* grad_local, void* ws,
+                                             size_t ws_bytes, int32_t* d_status,
+                                             void* stream);
+
 /* Tracing hook.  After tb_set_phase_events(events, k) (1 <= k <= 16) every
  * later call on this host thread records, on its own stream, events[0],
  * events[1], ... in launch order: one before each kernel of the call and

@@ -83,8 +83,10 @@ def lib():
             L.tb_debug_withhold_tile.argtypes = [i32]
             L.tb_debug_withhold_tile.restype = i32
             L.tb_tree_scan_affine_backward.argtypes = [p, i64, i64, p, p, p, p, sz, p, p]
+            L.tb_tree_scan_affine_backward_reuse.argtypes = [p, i64, i64, p, p, p, p, sz, p, p]
             for f in (L.tb_match_parens, L.tb_bboxes, L.tb_bboxes_batched, L.tb_set_phase_events,
-                      L.tb_bboxes_static_ws, L.tb_tree_scan, L.tb_tree_scan_affine_backward):
+                      L.tb_bboxes_static_ws, L.tb_tree_scan, L.tb_tree_scan_affine_backward,
+                      L.tb_tree_scan_affine_backward_reuse):
                 f.restype = i32
             L.tb_version.argtypes = []
             L.tb_version.restype = ctypes.c_char_p
@@ -162,6 +164,13 @@ def tb_tree_scan_affine_backward(kind, n, num_joints, local, grad_world, grad_lo
     return lib().tb_tree_scan_affine_backward(_ptr(kind), int(n), int(num_joints), _ptr(local),
                                               _ptr(grad_world), _ptr(grad_local), _ptr(ws),
                                               int(ws_bytes), _ptr(d_status), _stream(stream))
+
+
+def tb_tree_scan_affine_backward_reuse(kind, n, num_joints, local, grad_world, grad_local, ws,
+                                       ws_bytes, d_status, stream=None):
+    return lib().tb_tree_scan_affine_backward_reuse(
+        _ptr(kind), int(n), int(num_joints), _ptr(local), _ptr(grad_world), _ptr(grad_local),
+        _ptr(ws), int(ws_bytes), _ptr(d_status), _stream(stream))
 
 
 def tb_debug_withhold_tile(tile):
@@ -391,26 +400,60 @@ def affine_backward(kind, local, grad_world, check=True):
 
 
 class TreeTransform(torch.autograd.Function):
-    """world = TreeTransform.apply(kind, local[, check]).
+    """world = TreeTransform.apply(kind, local[, check[, keep_structure]]).
 
     local: (J, 3, 4) float32 local transforms, one per open of ``kind`` in
     stream order; world[r] = world[parent(r)] * local[r].  The backward pass
-    recomputes world inside the library (nothing but kind and local is saved)
-    and runs the hand-written adjoint.  With check=False no call reads the
-    device status word, so forward and backward can be captured in a CUDA
-    graph (reserve the workspace first)."""
+    recomputes world inside the library and runs the hand-written adjoint.
+    By default nothing but kind and local is saved.  With
+    keep_structure=True the forward runs in a workspace of its own that the
+    node keeps until its backward, which then reads the joint structure from
+    it (tb_tree_scan_affine_backward_reuse) instead of computing it again;
+    the price is that workspace (tb_workspace_size(TB_OP_TREE_BACKWARD, n)
+    bytes) per node.  With check=False no call reads the device status word,
+    so forward and backward can be captured in a CUDA graph (reserve the
+    shared workspace first)."""
 
     @staticmethod
-    def forward(ctx, kind, local, check=True):
-        ctx.save_for_backward(kind, local)
+    def forward(ctx, kind, local, check=True, keep_structure=False):
         ctx.check = check
-        return tree_scan(TB_MONOID_AFFINE3X4_F32, TB_DOWN, kind, local.detach(), check=check)
+        ctx.keep = bool(keep_structure)
+        if not ctx.keep:
+            ctx.save_for_backward(kind, local)
+            return tree_scan(TB_MONOID_AFFINE3X4_F32, TB_DOWN, kind, local.detach(), check=check)
+        dev = kind.device
+        k = _on_device(kind, torch.uint8, "kind", dev)
+        L = _on_device(local.detach(), torch.float32, "local", dev)
+        if tuple(L.shape[1:]) != (3, 4):
+            raise ValueError("local must have shape (J, 3, 4)")
+        n, J = k.numel(), L.shape[0]
+        nb = tb_workspace_size(TB_OP_TREE_BACKWARD, n)
+        buf = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        world = torch.empty_like(L)
+        _check(tb_tree_scan(TB_MONOID_AFFINE3X4_F32, TB_DOWN, k, n, J, L, world, buf, nb, status),
+               "tb_tree_scan")
+        if check:
+            _check(int(status.item()), "tb_tree_scan")
+        ctx.buf, ctx.nb, ctx.status = buf, nb, status
+        ctx.save_for_backward(k, L)
+        return world
 
     @staticmethod
     def backward(ctx, grad_world):
         kind, local = ctx.saved_tensors
-        g = affine_backward(kind, local, grad_world.contiguous(), check=ctx.check)
-        return None, g, None
+        if not ctx.keep:
+            g = affine_backward(kind, local, grad_world.contiguous(), check=ctx.check)
+            return None, g, None, None
+        G = _on_device(grad_world.contiguous(), torch.float32, "grad_world", kind.device)
+        g = torch.empty_like(local)
+        _check(tb_tree_scan_affine_backward_reuse(kind, kind.numel(), local.shape[0], local, G, g,
+                                                  ctx.buf, ctx.nb, ctx.status),
+               "tb_tree_scan_affine_backward_reuse")
+        if ctx.check:
+            _check(int(ctx.status.item()), "tb_tree_scan_affine_backward_reuse")
+        ctx.buf = None
+        return None, g, None, None
 
 
 # ----------------------------------------------------- host pipelines

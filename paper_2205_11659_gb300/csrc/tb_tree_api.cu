@@ -24,10 +24,11 @@ constexpr int next_pow2(int x) {
   return p;
 }
 
-// The three counters that must start at zero are adjacent so one memset
-// clears them.
+// What must start at zero is adjacent so one memset clears it: the
+// structure header (a call that rebuilds the joint structure invalidates it
+// first), the look-back words and the two counters.
 struct TreeLayout {
-  size_t lb, counter, xcount, zero_end, jdepth, premin, sufmin, jparent, jend, g_tree, relT, t_base,
+  size_t lb, counter, xcount, hdr, zero_end, jdepth, premin, sufmin, jparent, jend, g_tree, relT, t_base,
       t_link0, t_link1, t_val0, t_val1, t_world, ctree, t_tree, xlist, world, acc, total;
   int TE, TJ, PJ, Jmax;
 };
@@ -48,7 +49,9 @@ TreeLayout tree_layout(int64_t n, bool backward) {
     o = align_up(o + bytes);
     return at;
   };
-  L.lb = 0;
+  L.hdr = 0;  // at a fixed place, whatever n: a later call reads it first
+  o += 16;
+  L.lb = o;
   o += (size_t)TE * 8;
   L.counter = o;
   o += 4;
@@ -87,6 +90,7 @@ TreeWs tree_ws(const TreeLayout& L, void* ws, int64_t n, int J) {
   w.lb = reinterpret_cast<unsigned long long*>(b + L.lb);
   w.counter = reinterpret_cast<unsigned*>(b + L.counter);
   w.xcount = reinterpret_cast<unsigned*>(b + L.xcount);
+  w.hdr = reinterpret_cast<int*>(b + L.hdr);
   w.jdepth = reinterpret_cast<int*>(b + L.jdepth);
   w.premin = reinterpret_cast<int*>(b + L.premin);
   w.sufmin = reinterpret_cast<int*>(b + L.sufmin);
@@ -134,7 +138,7 @@ tb_status prelude(const uint8_t* kind, int64_t n, int J, const TreeLayout& L, vo
   TreeWs w = tree_ws(L, ws, n, J);
   w.status = d_status;
   if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return TB_ERR_CUDA;
-  if (cudaMemsetAsync(b + L.lb, 0, L.zero_end - L.lb, s) != cudaSuccess) return TB_ERR_CUDA;
+  if (cudaMemsetAsync(b + L.hdr, 0, L.zero_end - L.hdr, s) != cudaSuccess) return TB_ERR_CUDA;
   tb_internal::phase_mark(s);
   k_tdepth<<<L.TE, TNT, 0, s>>>(kind, w, d_status);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
@@ -157,10 +161,10 @@ tb_status launch_jstruct(const TreeWs& w, const void* in, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? TB_OK : TB_ERR_CUDA;
 }
 
+// The DOWN scan after its chain input (k_jstruct<M, true> or k_jchain).
 template <class M>
-tb_status launch_down(const TreeWs& w, const void* in, void* out, int32_t* d_status, cudaStream_t s) {
-  tb_status st = launch_jstruct<M, true>(w, in, s);
-  if (st != TB_OK) return st;
+tb_status launch_down_tiles(const TreeWs& w, const void* in, void* out, int32_t* d_status,
+                            cudaStream_t s) {
   tb_internal::phase_mark(s);
   const size_t tsm = down_tiles_smem<M>(w.TJ);
   if (tsm <= kMaxBlockSmem) {
@@ -184,6 +188,13 @@ tb_status launch_down(const TreeWs& w, const void* in, void* out, int32_t* d_sta
   k_down_tile<M><<<w.TJ, TNT, smem, s>>>(w, in, out);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   return TB_OK;
+}
+
+template <class M>
+tb_status launch_down(const TreeWs& w, const void* in, void* out, int32_t* d_status, cudaStream_t s) {
+  tb_status st = launch_jstruct<M, true>(w, in, s);
+  if (st != TB_OK) return st;
+  return launch_down_tiles<M>(w, in, out, d_status, s);
 }
 
 template <class M, class Values, class Finish>
@@ -302,6 +313,43 @@ tb_status tb_tree_scan_affine_backward(const uint8_t* kind, int64_t n, int64_t n
   void* world = b + L.world;
   void* acc = b + L.acc;
   st = launch_down<MonoidAffine>(w, local, world, d_status, s);
+  if (st != TB_OK) return st;
+  st = launch_up<MonoidAffSum>(w, AdjointValues{grad_world, world}, acc,
+                               AdjointFinish{world, grad_local}, s);
+  if (st != TB_OK) return st;
+  tb_internal::phase_mark(s);
+  return TB_OK;
+}
+
+tb_status tb_tree_scan_affine_backward_reuse(const uint8_t* kind, int64_t n, int64_t num_joints,
+                                             const float* local, const float* grad_world,
+                                             float* grad_local, void* ws, size_t ws_bytes,
+                                             int32_t* d_status, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tb_internal::phase_reset();
+  tb_status st = check_common(kind, n, num_joints, ws, d_status);
+  if (st != TB_OK) return st;
+  if (num_joints > 0) {
+    if (local == nullptr || grad_world == nullptr || grad_local == nullptr || !aligned(local, 16) ||
+        !aligned(grad_world, 16) || !aligned(grad_local, 16) || grad_local == local ||
+        grad_local == grad_world)
+      return TB_ERR_INVALID_ARG;
+  }
+  const TreeLayout L = tree_layout(n, true);
+  if (n > 0 && ws_bytes < L.total) return TB_ERR_WORKSPACE;
+  if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return TB_ERR_CUDA;
+  if (n == 0 || num_joints == 0) return TB_OK;
+  unsigned char* b = static_cast<unsigned char*>(ws);
+  TreeWs w = tree_ws(L, ws, n, (int)num_joints);
+  w.status = d_status;
+  // only the subtree-list counter restarts; the structure and its header stay
+  if (cudaMemsetAsync(b + L.xcount, 0, 4, s) != cudaSuccess) return TB_ERR_CUDA;
+  void* world = b + L.world;
+  void* acc = b + L.acc;
+  tb_internal::phase_mark(s);
+  k_jchain<MonoidAffine><<<w.TJ, TNT, 0, s>>>(w, local, d_status);
+  if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
+  st = launch_down_tiles<MonoidAffine>(w, local, world, d_status, s);
   if (st != TB_OK) return st;
   st = launch_up<MonoidAffSum>(w, AdjointValues{grad_world, world}, acc,
                                AdjointFinish{world, grad_local}, s);

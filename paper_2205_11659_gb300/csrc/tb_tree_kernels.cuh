@@ -69,6 +69,7 @@ constexpr int JT = TNT * JC;    // joints per tile
 constexpr int NCH = TNT;        // chunks per tile
 constexpr int NO_CHAIN = -2;   // tile without exported joints
 constexpr int kMaxJumpRounds = 40;
+constexpr int STRUCT_MAGIC = 0x54425354;  // header word of a complete joint structure
 constexpr int ST_INVALID = 1;  // TB_ERR_INVALID_ARG
 
 __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
@@ -208,6 +209,8 @@ struct TreeWs {
   unsigned long long* lb;  // look-back words of k_tdepth, one per element tile
   unsigned* counter;       // tile ticket of k_tdepth
   unsigned* xcount;        // number of entries in xlist
+  int* hdr;                // {STRUCT_MAGIC, n, J} once the joint structure below
+                           // is complete for that stream (0 while it is rebuilt)
   // joint level
   int* jdepth;   // depth of joint r
   int* premin;   // per joint tile: min of jdepth over the tile up to r
@@ -424,6 +427,39 @@ __device__ __forceinline__ int tree_first_le(const int* tree, int P, int x, int 
   return node - P;
 }
 
+// The exported joints of joint tile t (bits xm of each thread's chunk) form
+// one chain: list them in order in shared memory, then one warp folds their
+// input values 32 links at a time into relT; the chain's base (the parent of
+// its first link, first_par in the thread that holds it) goes to t_base.
+template <class M>
+__device__ __forceinline__ void export_chain(const TreeWs& w, const void* in, int t, unsigned xm,
+                                             int first_par, int* s_list, int* s_scri) {
+  using V = typename M::V;
+  const int tid = threadIdx.x, R0 = t * JT;
+  int nx_all;
+  const int off = block_excl_scan<TNW>(popc(xm), 0, OpAdd(), s_scri, &nx_all);
+  {
+    int o = off;
+#pragma unroll
+    for (int i = 0; i < JC; ++i)
+      if (xm & (1u << i)) s_list[o++] = tid * JC + i;
+  }
+  if (xm != 0u && off == 0) w.t_base[t] = first_par;
+  if (nx_all == 0 && tid == 0) w.t_base[t] = NO_CHAIN;
+  __syncthreads();
+  if (warp_id() == 0) {
+    const int lane = lane_id();
+    V carry = M::identity();
+    for (int b = 0; b < nx_all; b += 32) {
+      const int idx = b + lane;
+      V v = idx < nx_all ? M::load(in, R0 + s_list[idx]) : M::identity();
+      v = M::combine(carry, warp_incl_scan(v, MonoidOp<M>()));
+      if (idx < nx_all) M::store(w.relT, R0 + s_list[idx], v);
+      carry = shfl_idx(v, 31);
+    }
+  }
+}
+
 // Parent and subtree end of every joint of the tile; with CHAIN, also the
 // prefix folds of the tile's exported chain (the input of the DOWN scan).
 template <class M, bool CHAIN>
@@ -612,38 +648,40 @@ __global__ void __launch_bounds__(TNT) k_jstruct(TreeWs w, const void* __restric
     if (end[i] > R1) xm |= 1u << i;
   }
   if (CHAIN) {
-    // The exported joints of the tile form one chain: list them in order in
-    // shared memory, then one warp folds the list 32 links at a time.
-    int nx_all;
-    const int off = block_excl_scan<TNW>(popc(xm), 0, OpAdd(), s_scri, &nx_all);
-    {
-      int o = off;
+    int first_par = -1;  // parent of the tile's first exported joint
 #pragma unroll
-      for (int i = 0; i < JC; ++i)
-        if (xm & (1u << i)) s_q[o++] = tid * JC + i;
-    }
-    if (xm != 0u && off == 0) {
-      // the chain's first link; its parent is the chain's base
-      int pv = -1;
+    for (int i = 0; i < JC; ++i)
+      if (i == lowest_set(xm)) first_par = par[i];
+    export_chain<M>(w, in, t, xm, first_par, s_q, s_scri);
+  }
+}
+
+// DOWN input of one joint tile from its joint structure alone (jparent and
+// jend already in the workspace, checked against the header): the prefix
+// folds of the tile's exported chain, as k_jstruct<M, true> computes them.
+template <class M>
+__global__ void __launch_bounds__(TNT) k_jchain(TreeWs w, const void* __restrict__ in, int* status) {
+  __shared__ int s_list[JT];
+  __shared__ int s_scri[TNW + 1];
+  if (*w.status != ST_OK) return;
+  if (w.hdr[0] != STRUCT_MAGIC || w.hdr[1] != w.n || w.hdr[2] != w.J) {
+    if (threadIdx.x == 0) atomic_cas_i32(status, ST_OK, ST_INVALID);
+    return;  // no complete structure for this stream in the workspace
+  }
+  const int t = blockIdx.x, tid = threadIdx.x;
+  const int R0 = t * JT, R1 = R0 + JT;
+  const int cnt = min(JT, w.J - R0);
+  unsigned xm = 0;
+  int first_par = -1;
 #pragma unroll
-      for (int i = 0; i < JC; ++i)
-        if (i == lowest_set(xm)) pv = par[i];
-      w.t_base[t] = pv;
-    }
-    if (nx_all == 0 && tid == 0) w.t_base[t] = NO_CHAIN;
-    __syncthreads();
-    if (warp_id() == 0) {
-      const int lane = lane_id();
-      V carry = M::identity();
-      for (int b = 0; b < nx_all; b += 32) {
-        const int idx = b + lane;
-        V v = idx < nx_all ? M::load(in, R0 + s_q[idx]) : M::identity();
-        v = M::combine(carry, warp_incl_scan(v, MonoidOp<M>()));
-        if (idx < nx_all) M::store(w.relT, R0 + s_q[idx], v);
-        carry = shfl_idx(v, 31);
-      }
+  for (int i = 0; i < JC; ++i) {
+    const int k = tid * JC + i;
+    if (k < cnt && w.jend[R0 + k] > R1) {
+      if (xm == 0u) first_par = w.jparent[R0 + k];
+      xm |= 1u << i;
     }
   }
+  export_chain<M>(w, in, t, xm, first_par, s_list, s_scri);
 }
 
 // ------------------------------------------------------------- DOWN
@@ -661,6 +699,11 @@ __global__ void __launch_bounds__(1024) k_down_tiles(TreeWs w, int* status) {
   using V = typename M::V;
   TB_DYNAMIC_SMEM(smem);
   if (*w.status != ST_OK) return;
+  if (threadIdx.x == 0) {  // the joint structure (k_jstruct) is complete
+    w.hdr[1] = w.n;
+    w.hdr[2] = w.J;
+    w.hdr[0] = STRUCT_MAGIC;
+  }
   const int TJ = w.TJ;
   V* sv = reinterpret_cast<V*>(smem);              // values of buffers 0 and 1
   int* sl = reinterpret_cast<int*>(sv + 2 * TJ);  // links of buffers 0 and 1
@@ -1021,6 +1064,11 @@ template <class M>
 __global__ void __launch_bounds__(1024) k_up_tiles(TreeWs w) {
   using V = typename M::V;
   if (*w.status != ST_OK) return;
+  if (threadIdx.x == 0) {  // the joint structure (k_jstruct) is complete
+    w.hdr[1] = w.n;
+    w.hdr[2] = w.J;
+    w.hdr[0] = STRUCT_MAGIC;
+  }
   const int P = w.PJ;
   for (int t = threadIdx.x; t < P; t += blockDim.x)
     M::store(w.t_tree, P + t,

@@ -30,7 +30,8 @@ def lib():
 def test_header_declares_entry_points():
     names = declared_functions()
     for n in ("tb_workspace_size", "tb_match_parens", "tb_bboxes", "tb_bboxes_batched",
-              "tb_tree_scan", "tb_tree_scan_affine_backward", "tb_set_phase_events",
+              "tb_tree_scan", "tb_tree_scan_affine_backward",
+              "tb_tree_scan_affine_backward_reuse", "tb_set_phase_events",
               "tb_debug_withhold_tile", "tb_version"):
         assert n in names
 
@@ -116,6 +117,15 @@ def test_tree_scan_argument_errors(lib):
     assert bwd(gl=fake) == b.TB_ERR_INVALID_ARG
     assert bwd(local=fake + 8) == b.TB_ERR_INVALID_ARG
     assert bwd(nb=1 << 10) == b.TB_ERR_WORKSPACE
+
+    def bwd_reuse(J=5, local=fake, g=fake + 4096, gl=fake + 8192, nb=big):
+        return lib.tb_tree_scan_affine_backward_reuse(p(fake), 10, J, p(local), p(g), p(gl),
+                                                      p(fake), nb, p(fake), None)
+
+    assert bwd_reuse(J=6) == b.TB_ERR_INVALID_ARG
+    assert bwd_reuse(gl=fake) == b.TB_ERR_INVALID_ARG
+    assert bwd_reuse(g=fake + 4) == b.TB_ERR_INVALID_ARG
+    assert bwd_reuse(nb=1 << 10) == b.TB_ERR_WORKSPACE
 
 
 def test_phase_event_count_limits(lib):

@@ -320,3 +320,92 @@ def test_lookback_timeout_reported_and_recovered():
     assert st == oracle.OK
     assert rel_err(world.cpu().numpy(), ref) < REL_TOL
     assert binding.tb_debug_withhold_tile(-2) == binding.TB_ERR_INVALID_ARG
+
+
+def _forward_into(ws, status, kd, Ld, world):
+    nb = ws.numel()
+    rc = binding.tb_tree_scan(binding.TB_MONOID_AFFINE3X4_F32, binding.TB_DOWN, kd, kd.numel(),
+                              Ld.shape[0], Ld, world, ws, nb, status)
+    assert rc == binding.TB_OK
+
+
+def _reuse_into(ws, status, kd, Ld, Wd, grad):
+    rc = binding.tb_tree_scan_affine_backward_reuse(kd, kd.numel(), Ld.shape[0], Ld, Wd, grad, ws,
+                                                    ws.numel(), status)
+    assert rc == binding.TB_OK
+
+
+def test_backward_reuse_matches_full_backward():
+    """The backward that reads the joint structure a forward left in its
+    workspace gives the full backward's gradients bit for bit."""
+    k, L, W = inputs.skeleton(200_000, 41)
+    kd, Ld, Wd = (torch.from_numpy(a).cuda() for a in (k, L, W))
+    n = k.size
+    ws = torch.empty(binding.tb_workspace_size(binding.TB_OP_TREE_BACKWARD, n), dtype=torch.uint8,
+                     device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    world = torch.empty_like(Ld)
+    grad = torch.empty_like(Ld)
+    _forward_into(ws, status, kd, Ld, world)
+    _reuse_into(ws, status, kd, Ld, Wd, grad)
+    torch.cuda.synchronize()
+    assert int(status.item()) == binding.TB_OK
+    full = binding.affine_backward(kd, Ld, Wd)
+    assert torch.equal(grad.view(torch.int32), full.view(torch.int32))
+    st, ref = oracle.affine_backward(k, L.astype(np.float64), W.astype(np.float64))
+    assert rel_err(grad.cpu().numpy(), ref) < REL_TOL
+    # a second backward on the same workspace (the structure is still there)
+    grad2 = torch.empty_like(Ld)
+    _reuse_into(ws, status, kd, Ld, Wd, grad2)
+    torch.cuda.synchronize()
+    assert int(status.item()) == binding.TB_OK
+    assert torch.equal(grad2.view(torch.int32), full.view(torch.int32))
+
+
+def test_backward_reuse_rejects_a_missing_structure():
+    """After a forward over another joint count, or a failed forward, the
+    reusing backward reports TB_ERR_INVALID_ARG; a fresh forward makes it
+    work again."""
+    k, L, W = inputs.skeleton(30_000, 42)
+    k2, L2, _ = inputs.skeleton(29_000, 43)
+    n = max(k.size, k2.size)
+    ws = torch.empty(binding.tb_workspace_size(binding.TB_OP_TREE_BACKWARD, n), dtype=torch.uint8,
+                     device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    kd, Ld, Wd = (torch.from_numpy(a).cuda() for a in (k, L, W))
+    kd2, Ld2 = torch.from_numpy(k2).cuda(), torch.from_numpy(L2).cuda()
+    grad = torch.empty_like(Ld)
+    _forward_into(ws, status, kd2, Ld2, torch.empty_like(Ld2))
+    _reuse_into(ws, status, kd, Ld, Wd, grad)
+    torch.cuda.synchronize()
+    assert int(status.item()) == binding.TB_ERR_INVALID_ARG
+    kb = k.copy()
+    kb[10] = 9  # a bad kind: the forward fails and leaves no structure
+    _forward_into(ws, status, torch.from_numpy(kb).cuda(), Ld, torch.empty_like(Ld))
+    torch.cuda.synchronize()
+    assert int(status.item()) == binding.TB_ERR_BAD_KIND
+    _reuse_into(ws, status, kd, Ld, Wd, grad)
+    torch.cuda.synchronize()
+    assert int(status.item()) == binding.TB_ERR_INVALID_ARG
+    _forward_into(ws, status, kd, Ld, torch.empty_like(Ld))
+    _reuse_into(ws, status, kd, Ld, Wd, grad)
+    torch.cuda.synchronize()
+    assert int(status.item()) == binding.TB_OK
+    assert torch.equal(grad.view(torch.int32), binding.affine_backward(kd, Ld, Wd).view(torch.int32))
+
+
+def test_tree_transform_keep_structure():
+    """TreeTransform with keep_structure=True gives the same world and
+    gradients as the default."""
+    k, L, W = inputs.skeleton(50_000, 44)
+    kd, Wd = torch.from_numpy(k).cuda(), torch.from_numpy(W).cuda()
+    outs = []
+    for keep in (False, True):
+        local = torch.from_numpy(L).cuda().requires_grad_(True)
+        world = binding.TreeTransform.apply(kd, local, True, keep)
+        (world * Wd).sum().backward()
+        torch.cuda.synchronize()
+        outs.append((world.detach(), local.grad))
+    assert torch.equal(outs[0][0].view(torch.int32), outs[1][0].view(torch.int32))
+    assert torch.equal(outs[0][1].view(torch.int32), outs[1][1].view(torch.int32))
+
