@@ -56,7 +56,7 @@ BWD_BYTES_PER_JOINT = 146  # 2 kinds + 48 local + 48 grad_world read, 48 grad_lo
 NCU_TRAFFIC = {
     # 639.1 MB per launch measured on the 2^24 random walk; the 2^26 entry
     # scales it by the element count (traffic tracks the 41 B/elem).
-    "d035ca4e77b0e1b5": {"rw24": 639.1e6, "rw26": 639.1e6 * 4},
+    "19db189560a25bda": {"rw24": 639.1e6, "rw26": 639.1e6 * 4},
 }
 
 
@@ -90,12 +90,18 @@ def make_workload(name, seed=0):
     raise ValueError(name)
 
 
-def kernel_hash():
+SCENE_SOURCES = ("tb_api.cu", "tb_core.cuh", "tb_prims.cuh", "tb_scene_kernels.cuh")
+TREE_SOURCES = ("tb_core.cuh", "tb_prims.cuh", "tb_tree_api.cu", "tb_tree_kernels.cuh")
+
+
+def kernel_hash(sources=SCENE_SOURCES):
+    """Hash of the CUDA sources a workload's kernels are built from (and of
+    the tuned build parameters), naming the kernels a traffic figure was
+    measured on."""
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2205_11659_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in sources:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     from paper_2205_11659_gb300 import _build
     nt, kpt = _build.tuned_shape()
     if (nt, kpt) != (256, 16):
@@ -579,7 +585,7 @@ def run_tree(args, torch, world, rank, dev):
                     "d2h_bytes_per_step": int(2 * L.nbytes)},
             "gpu_launches": (6 + 6) * K,
             "clocks": clk,
-            "kernel_hash": kernel_hash(),
+            "kernel_hash": kernel_hash(TREE_SOURCES),
         }
         print(json.dumps(line), flush=True)
     return 0

@@ -1103,15 +1103,40 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
 }
 
 // ------------------------------------------------------------------- K4
+// Union tree over the tiles' leaf unions (one block; leaves at [P, 2P)):
+// each warp walks 32 leaves at a time and builds their five lowest levels by
+// shuffles; the levels above come from global memory while a level is wide,
+// then from shared memory.
 __global__ void __launch_bounds__(NT2) k4_union_tree(SceneWs ws) {
-  const int T = ws.T, P = ws.P, tid = threadIdx.x;
+  __shared__ float4 s_top[2 * NT2];
+  const int T = ws.T, P = ws.P, tid = threadIdx.x, lane = lane_id();
   if (*ws.status != ST_OK) return;
   float4* tree = ws.uall_tree;
-  for (int u = tid; u < P; u += NT2) tree[P + u] = u < T ? ws.t_uall[u] : box_empty();
+  const int LP = 31 - __clz(P);
+  for (int r0 = tid - lane; r0 < P; r0 += NT2) {  // warp-uniform: 32 leaves per warp
+    const int u = r0 + lane;
+    float4 v = u < T ? ws.t_uall[u] : box_empty();
+    if (u < P) tree[P + u] = v;
+#pragma unroll
+    for (int l = 1; l <= 5; ++l) {
+      v = box_unite(v, shfl_xor(v, 1 << (l - 1)));
+      if (l <= LP && (lane & ((1 << l) - 1)) == 0 && u < P) tree[(P + u) >> l] = v;
+    }
+  }
   __syncthreads();
-  for (int h = P >> 1; h >= 1; h >>= 1) {
+  int h = P >> 6;
+  for (; h > NT2 / 2; h >>= 1) {
     for (int i = h + tid; i < 2 * h; i += NT2) tree[i] = box_unite(tree[2 * i], tree[2 * i + 1]);
     __syncthreads();
+  }
+  if (h >= 1) {
+    for (int i = 2 * h + tid; i < 4 * h; i += NT2) s_top[i] = tree[i];  // i < 4h <= 2 * NT2
+    __syncthreads();
+    for (int g = h; g >= 1; g >>= 1) {
+      for (int i = g + tid; i < 2 * g; i += NT2) s_top[i] = box_unite(s_top[2 * i], s_top[2 * i + 1]);
+      __syncthreads();
+    }
+    for (int i = 1 + tid; i < 2 * h; i += NT2) tree[i] = s_top[i];
   }
 }
 
