@@ -54,7 +54,9 @@ typedef enum {
   TB_ERR_BAD_KIND = 3,    /* a kind byte above 3                           */
   TB_ERR_WORKSPACE = 4,   /* ws_bytes below tb_workspace_size()            */
   TB_ERR_TIMEOUT = 5,     /* a bounded cross-block wait gave up            */
-  TB_ERR_CUDA = 6         /* a CUDA launch or memset failed                */
+  TB_ERR_CUDA = 6,        /* a CUDA launch or memset failed                */
+  TB_ERR_BOUNDS = 7       /* debug builds only (TB_DEBUG): an index check
+                             failed and the access was skipped            */
 } tb_status;
 
 enum { TB_LEAF = 0, TB_OPEN_CLIP = 1, TB_OPEN_BLEND = 2, TB_CLOSE = 3 };

@@ -72,11 +72,12 @@ def up_to_date(lib=LIB):
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force=False, verbose=False, shape=None, out_dir=None, persistent=None):
+def build(force=False, verbose=False, shape=None, out_dir=None, persistent=None, debug=False):
     """Build the library if needed; returns its path.  shape = (threads per
     block, elements per thread) and persistent override the tuned values and
     out_dir the output folder (the autotuner builds its candidates that
-    way)."""
+    way); debug=True compiles the kernels' index checks in (TB_DEBUG; give it
+    an out_dir of its own)."""
     out_dir = OUT_DIR if out_dir is None else out_dir
     lib_path = os.path.join(out_dir, "libtb.so")
     if not force and up_to_date(lib_path):
@@ -87,7 +88,7 @@ def build(force=False, verbose=False, shape=None, out_dir=None, persistent=None)
     persist = tuned_persistent() if persistent is None else bool(persistent)
     common = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I" + INCLUDE, "-I" + CSRC, "-DTB_NT=%d" % nt, "-DTB_KPT=%d" % kpt,
-                     "-DTB_PERSIST=%d" % int(persist)]
+                     "-DTB_PERSIST=%d" % int(persist), "-DTB_DEBUG=%d" % int(bool(debug))]
     if verbose:
         common += ["-Xptxas", "-v"]
 

@@ -9,8 +9,9 @@ the test suite checks against the oracle) on scenes that span several tiles
 and a ragged tail and on a batch of scenes, times with CUDA events the
 bounding-box pass on a 2^24-element random-walk scene and on a batch of 512
 scenes and the matching-only pass on the same 2^24 scene, and reports every
-candidate.  With --write the fastest correct one goes to tuned_shape.json,
-which the build uses from then on.  Needs a CUDA GPU.
+candidate.  With --write the fastest correct one goes to tuned_shape.json
+(with the device it was measured on), which the build uses from then on.
+Needs a CUDA GPU.
 """
 import argparse
 import json
@@ -153,10 +154,14 @@ def main(argv=None):
         print("no correct candidate", file=sys.stderr)
         return 1
     best = min(ok, key=lambda r: sum(r["ms"].values()))
+    props = torch.cuda.get_device_properties(dev)
     summary = {"threads_per_block": best["threads_per_block"],
                "elements_per_thread": best["elements_per_thread"],
                "persistent": best["persistent"],
                "chosen_by": "autotune.py: fastest correct candidate on rw24 + batch512 + match24",
+               "device": {"name": props.name, "sms": props.multi_processor_count,
+                          "capability": "%d.%d" % (props.major, props.minor),
+                          "cuda_runtime": torch.version.cuda},
                "candidates": results}
     print(json.dumps(summary), flush=True)
     if args.write:

@@ -27,9 +27,10 @@ TB_ERR_BAD_KIND = 3
 TB_ERR_WORKSPACE = 4
 TB_ERR_TIMEOUT = 5
 TB_ERR_CUDA = 6
+TB_ERR_BOUNDS = 7
 STATUS_NAMES = {0: "TB_OK", 1: "TB_ERR_INVALID_ARG", 2: "TB_ERR_UNBALANCED",
                 3: "TB_ERR_BAD_KIND", 4: "TB_ERR_WORKSPACE", 5: "TB_ERR_TIMEOUT",
-                6: "TB_ERR_CUDA"}
+                6: "TB_ERR_CUDA", 7: "TB_ERR_BOUNDS"}
 
 TB_OP_MATCH_PARENS = 0
 TB_OP_BBOXES = 1

@@ -43,7 +43,22 @@ static_assert(KPT == 8 || KPT == 16, "elements per thread must be 8 or 16");
 constexpr int K_LEAF = 0, K_CLIP = 1, K_BLEND = 2, K_CLOSE = 3, K_PAD = 4;
 
 // Status codes (same values as tb_status in tb.h).
-constexpr int ST_OK = 0, ST_UNBALANCED = 2, ST_BAD_KIND = 3, ST_TIMEOUT = 5;
+constexpr int ST_OK = 0, ST_UNBALANCED = 2, ST_BAD_KIND = 3, ST_TIMEOUT = 5, ST_BOUNDS = 7;
+
+// TB_DEBUG: a build whose kernels check the data-dependent indices of their
+// memory accesses (indices read from the workspace or derived from the
+// input) before using them.  A failed check records ST_BOUNDS in the status
+// word and the access is skipped -- no trap, the context stays usable.  In
+// normal builds in_range() is the constant true and the checks vanish.
+#ifndef TB_DEBUG
+#define TB_DEBUG 0
+#endif
+__device__ __forceinline__ bool in_range(long long i, long long lo, long long hi, const int* status) {
+  if (!TB_DEBUG) return true;
+  if (i >= lo && i < hi) return true;
+  atomic_cas_i32(const_cast<int*>(status), ST_OK, ST_BOUNDS);
+  return false;
+}
 
 // Staged boxes are padded by one float4 per chunk so that the 32 lanes of a
 // warp, each reading element i of its own chunk, hit distinct banks.

@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(NTR) k2_segments(SceneWs ws) {
     const int lo = ws.t_lo[u], p = ws.t_ps[u];
     float4 v = box_universe();
     int l = -1;
-    if (lo - 1 >= 0 && p >= 0) {
+    if (lo - 1 >= 0 && p >= 0 && in_range(lo - 1 - ws.t_lo[p], 0, TILE, ws.status)) {
       v = ws.slice_rel[(size_t)p * TILE + (lo - 1 - ws.t_lo[p])];
       l = p;
     }
@@ -513,7 +513,8 @@ __device__ __forceinline__ OutRes out_lookup(const OutCtx& c, const SceneWs& ws,
   while (own >= 0 && c.s_lo[own] > dd) own = c.s_cps[own];
   r.own = own;
   if (own >= 0) {
-    const int op = c.s_spos[own * KPT + (dd - c.s_lo[own])];
+    const int si = own * KPT + (dd - c.s_lo[own]);
+    const int op = in_range(si, 0, TILE, ws.status) ? c.s_spos[si] : 0;
     r.par = c.base + op;
     if (HAS_BOX && want_clip) r.cx = box_isect(c.s_B[own], c.s_box[box_slot(op)]);
   } else {
@@ -522,7 +523,8 @@ __device__ __forceinline__ OutRes out_lookup(const OutCtx& c, const SceneWs& ws,
       r.par = c.s_cidx[m];
       if (HAS_BOX && want_clip) r.cx = c.s_cclip[m];
     } else {
-      const int src = ctx_src_of(ws, c.t, c.ovf != 0, c.s_seg, c.nseg, c.dstart_t - 1 - m, m);
+      int src = ctx_src_of(ws, c.t, c.ovf != 0, c.s_seg, c.nseg, c.dstart_t - 1 - m, m);
+      if (src >= 0 && !in_range(src, 0, (long long)ws.T * TILE, ws.status)) src = -1;
       r.par = src >= 0 ? ws.slice_pos[src] : -1;
       if (HAS_BOX && want_clip && src >= 0)
         r.cx = box_isect(ws.t_B[src / TILE], ws.slice_rel[src]);
@@ -682,7 +684,7 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   float4 ctx_c = box_universe();
   if (ctx_mine) {
     const int src = ctx_src_of(ws, t, ovf, s_seg, nseg, dstart_t - 1 - tid, tid);
-    if (src >= 0) {
+    if (src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status)) {
       ctx_i = ws.slice_pos[src];
       if (HAS_BOX) ctx_c = box_isect(ws.t_B[src / TILE], ws.slice_rel[src]);
     }
@@ -792,7 +794,8 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
         v = s_cclip[m];
       } else {
         const int src = ctx_src_of(ws, t, ovf, s_seg, nseg, dstart_t - 1 - m, m);
-        v = src >= 0 ? box_isect(ws.t_B[src / TILE], ws.slice_rel[src]) : box_universe();
+        v = src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status)
+                ? box_isect(ws.t_B[src / TILE], ws.slice_rel[src]) : box_universe();
       }
       link = -1;
     }
@@ -1005,8 +1008,9 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
       const int eo = BATCHED ? (int)(e - scs) : e;
       while (u >= 0 && s_lo[u] > dd) u = s_cps[u];
       if (u >= 0) {
-        if (a.match) a.match[base + s_spos[u * KPT + (dd - s_lo[u])]] = eo;
-      } else {
+        const int si = u * KPT + (dd - s_lo[u]);
+        if (a.match && in_range(si, 0, TILE, ws.status)) a.match[base + s_spos[si]] = eo;
+      } else if (in_range(-1 - dd, 0, TILE, ws.status)) {
         ws.cpos[(size_t)t * TILE + (-1 - dd)] = e;
         ws.cval[(size_t)t * TILE + (-1 - dd)] = eo;
       }
@@ -1060,12 +1064,13 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
         u = s_cps[u];
       }
       if (u >= 0) {
-        const int op = s_spos[u * KPT + (dd - s_lo[u])];
+        const int si = u * KPT + (dd - s_lo[u]);
+        const int op = in_range(si, 0, TILE, ws.status) ? s_spos[si] : cp;
         const float4 U = box_unite(box_unite(s_box[box_slot(op)], mid), upre);
         s_box[box_slot(op)] = U;
         s_box[box_slot(cp)] = U;
         if (a.match) a.match[base + op] = eo;
-      } else {
+      } else if (in_range(-1 - dd, 0, TILE, ws.status)) {
         const int mm = -1 - dd;
         ws.upre[(size_t)t * TILE + mm] = box_unite(mid, upre);
         ws.cpos[(size_t)t * TILE + mm] = e;
@@ -1182,7 +1187,9 @@ __global__ void __launch_bounds__(NT) k4_cross_tile_unions(K4Args a) {
       src = (s >= 0 && s_seg[s].x >= 0) ? s_seg[s].x * TILE + (d - s_seg[s].y) : -1;
     }
     if (src < 0) continue;  // unbalanced input
+    if (!in_range(src, 0, (long long)ws.T * TILE, ws.status)) continue;
     const int o = ws.slice_pos[src];
+    if (!in_range(o, 0, (long long)ws.T * TILE, ws.status)) continue;
     if (a.match) a.match[o] = ws.cval[(size_t)t * TILE + m];
     if (HAS_BOX) {
       const int u = src / TILE;
@@ -1191,7 +1198,7 @@ __global__ void __launch_bounds__(NT) k4_cross_tile_unions(K4Args a) {
       const int c = ws.cpos[(size_t)t * TILE + m];
       const float4 U = box_unite(box_unite(ws.usuf[src], mid), ws.upre[(size_t)t * TILE + m]);
       a.box_out[o] = U;
-      a.box_out[c] = U;
+      if (in_range(c, 0, (long long)ws.T * TILE, ws.status)) a.box_out[c] = U;
     }
   }
 }

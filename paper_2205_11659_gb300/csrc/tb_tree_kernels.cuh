@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(TNT, 2) k_down_tile(TreeWs w, const void* __re
     const int k = c0 + i;
     if (k < cnt) {
       const int p = s_anc[k];
-      if (p >= R0 + c0) {
+      if (p >= R0 + c0 && in_range(p, R0 + c0, R0 + k, w.status)) {  // parent before k
         s_val[jslot(k)] = M::combine(s_val[jslot(p - R0)], s_val[jslot(k)]);
         s_anc[k] = s_anc[p - R0];
       }
@@ -810,7 +810,9 @@ __global__ void __launch_bounds__(TNT, 2) k_down_tile(TreeWs w, const void* __re
   V m = M::identity();
   if (xm) {
     const int a = s_anc[c0 + lowest_set(xm)];
-    if (a >= R0) {
+    if (!in_range(a, -1, R0 + c0, w.status)) {
+      // (debug builds: an ancestor at or after the chunk; left at the identity)
+    } else if (a >= R0) {
       link = (a - R0) / JC;
       m = s_val[jslot(a - R0)];
     } else if (a >= 0) {
@@ -848,7 +850,9 @@ __global__ void __launch_bounds__(TNT, 2) k_down_tile(TreeWs w, const void* __re
     const int k = c0 + i;
     if (k < cnt && !(xm & (1u << i))) {
       const int a = s_anc[k];
-      if (a >= R0) {
+      if (!in_range(a, -1, R0 + c0, w.status)) {
+        // (debug builds: an ancestor at or after the chunk; left as it is)
+      } else if (a >= R0) {
         s_val[jslot(k)] = M::combine(s_val[jslot(a - R0)], s_val[jslot(k)]);
       } else if (a >= 0) {
         if (a != last_a) {
@@ -1017,11 +1021,17 @@ __global__ void __launch_bounds__(TNT, 2) k_up_tile(TreeWs w, Values values, voi
   for (int k = lim - 1; k >= c0; --k) {
     V acc = s_val[jslot(k)];
     const int stop = min(s_end[k], ce);
-    for (int c = k + 1; c < stop; c = s_end[c]) acc = M::combine(acc, s_val[jslot(c)]);
+    for (int c = k + 1; c < stop; c = s_end[c]) {
+      acc = M::combine(acc, s_val[jslot(c)]);
+      if (!in_range(s_end[c], c + 1, (long long)w.J - R0 + 1, w.status)) break;  // ends lie after the joint
+    }
     s_val[jslot(k)] = acc;
   }
   V tot = M::identity();
-  for (int c = c0; c < lim; c = s_end[c]) tot = M::combine(tot, s_val[jslot(c)]);
+  for (int c = c0; c < lim; c = s_end[c]) {
+    tot = M::combine(tot, s_val[jslot(c)]);
+    if (!in_range(s_end[c], c + 1, (long long)w.J - R0 + 1, w.status)) break;
+  }
   s_tree[NCH + tid] = tot;
   __syncthreads();
   for (int h = NCH / 2; h >= 1; h >>= 1) {
@@ -1037,7 +1047,10 @@ __global__ void __launch_bounds__(TNT, 2) k_up_tile(TreeWs w, Values values, voi
     if (e <= JT) {
       const int c2 = e / JC;
       acc = M::combine(acc, seg_fold<M>(node, NCH, tid + 1, c2 - 1));
-      for (int j = c2 * JC; j < e; j = s_end[j]) acc = M::combine(acc, s_val[jslot(j)]);
+      for (int j = c2 * JC; j < e; j = s_end[j]) {
+        acc = M::combine(acc, s_val[jslot(j)]);
+        if (!in_range(s_end[j], j + 1, (long long)w.J - R0 + 1, w.status)) break;
+      }
     } else {
       acc = M::combine(acc, seg_fold<M>(node, NCH, tid + 1, NCH - 1));
       const unsigned at = atomic_add_u32(w.xcount, 1u);
@@ -1094,8 +1107,10 @@ __global__ void k_up_cross(TreeWs w, Values values, void* __restrict__ out, Fini
   auto node = [tree](int i) { return M::load(tree, i); };
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     const int r = w.xlist[i];
+    if (!in_range(r, 0, w.J, w.status)) continue;
     const int t = r / JT;
     const int e = w.jend[r];
+    if (!in_range(e, r + 1, (long long)w.J + 1, w.status)) continue;
     const int t2 = e / JT;
     V acc = M::load(out, r);
     acc = M::combine(acc, seg_fold<M>(node, w.PJ, t + 1, t2 - 1));
