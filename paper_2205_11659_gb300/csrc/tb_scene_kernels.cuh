@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   // ---- in-chunk structure from the kinds alone (register stack of
   // 4-bit positions): parent position, partner position, masks.
   unsigned long long lpar = 0, lmate = 0;
-  unsigned inside = 0, pairm = 0, openm = 0, closem = 0, leafm = 0;
+  unsigned inside = 0, pairm = 0, openm = 0, closem = 0, leafm = 0, clipm = 0;
   {
     unsigned long long stk = 0;
     int spn = 0;
@@ -654,6 +654,7 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
       }
       if (k == K_CLIP || k == K_BLEND) {
         openm |= 1u << i;
+        if (k == K_CLIP) clipm |= 1u << i;
         stk = (stk << 4) | (unsigned long long)i;
         ++spn;
       } else if (k == K_CLOSE) {
@@ -680,9 +681,7 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   // Chunk stack slice: the k-th unmatched open sits at depth lo_j + k.
   {
     int k = 0;
-#pragma unroll
-    for (int i = 0; i < KPT; ++i)
-      if ((um >> i) & 1u) s_spos[p0 + k++] = (uint16_t)(p0 + i);
+    for (unsigned m = um; m; m &= m - 1) s_spos[p0 + k++] = (uint16_t)(p0 + lowest_set(m));
   }
   const int a_t = s_info[0], dstart_t = s_info[1], nseg = s_info[2];
   const bool ovf = nseg > SEGK;
@@ -712,28 +711,33 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   unsigned long long kpack = 0;  // kinds, 4 bits per element, for the rolled walk
 #pragma unroll
   for (int i = 0; i < KPT; ++i) kpack |= (unsigned long long)kk[i] << (4 * i);
-  unsigned parpair = 0, savem = 0, cl_gin = 0, cl_gpair = 0, cl_gum = 0;
+  unsigned parpair = 0, cl_gin = 0, cl_gpair = 0, cl_gum = 0;
   unsigned long long lA = 0, lB = 0;
 #pragma unroll
   for (int i = 0; i < KPT; ++i) {
-    const unsigned bit = 1u << i;
     const int lp = (int)((lpar >> (4 * i)) & 15ull);
-    const bool pp = (inside & bit) && ((pairm >> lp) & 1u);
-    if (pp) parpair |= bit;
-    if ((openm & pairm & bit) && pp) {
-      savem |= bit;
-      lA |= ((lmate >> (4 * lp)) & 15ull) << (4 * i);
+    if (((inside >> i) & 1u) && ((pairm >> lp) & 1u)) parpair |= 1u << i;
+  }
+  // (the two sparse cases below loop over the set bits of their masks)
+  const unsigned savem = openm & pairm & parpair;
+  for (unsigned m = savem; m; m &= m - 1) {
+    const int i = lowest_set(m);
+    const int lp = (int)((lpar >> (4 * i)) & 15ull);
+    lA |= ((lmate >> (4 * lp)) & 15ull) << (4 * i);
+  }
+  for (unsigned m = closem & inside; m; m &= m - 1) {
+    const int i = lowest_set(m);
+    const int lp = (int)((lpar >> (4 * i)) & 15ull);
+    if (!((inside >> lp) & 1u)) continue;
+    const unsigned bit = 1u << i;
+    const int gp = (int)((lpar >> (4 * lp)) & 15ull);
+    cl_gin |= bit;
+    lA |= (unsigned long long)gp << (4 * i);
+    if ((pairm >> gp) & 1u) {
+      cl_gpair |= bit;
+      lB |= ((lmate >> (4 * gp)) & 15ull) << (4 * i);
     }
-    if ((closem & inside & bit) && ((inside >> lp) & 1u)) {
-      const int gp = (int)((lpar >> (4 * lp)) & 15ull);
-      cl_gin |= bit;
-      lA |= (unsigned long long)gp << (4 * i);
-      if ((pairm >> gp) & 1u) {
-        cl_gpair |= bit;
-        lB |= ((lmate >> (4 * gp)) & 15ull) << (4 * i);
-      }
-      if ((um >> gp) & 1u) cl_gum |= bit;
-    }
+    if ((um >> gp) & 1u) cl_gum |= bit;
   }
 
   if (ctx_mine) {
@@ -746,13 +750,11 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
     // Relative clip of each chunk-slice entry (intersection of the chunk's
     // unmatched clip boxes up to it), stored over that open's staged box.
     float4 acc = box_universe();
-#pragma unroll
-    for (int i = 0; i < KPT; ++i) {
-      if ((um >> i) & 1u) {
-        float4* b = &s_box[box_slot(p0 + i)];
-        if (kk[i] == K_CLIP) acc = box_isect(acc, *b);
-        *b = acc;
-      }
+    for (unsigned m = um; m; m &= m - 1) {
+      const int i = lowest_set(m);
+      float4* b = &s_box[box_slot(p0 + i)];
+      if ((clipm >> i) & 1u) acc = box_isect(acc, *b);
+      *b = acc;
     }
   }
   build_chunk_tree(s_tree, lo_j, OpMin());
