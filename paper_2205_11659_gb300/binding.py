@@ -549,3 +549,86 @@ class HostPipeline:
         for i in range(len(kinds)):
             _check(int(statuses[i]), "%s (scene %d)" % (name, i))
         return outs
+
+
+class TreePipeline:
+    """The affine tree scan and its adjoint over a sequence of skeleton jobs
+    held in pinned host memory, with the copies overlapped: while job i runs
+    (tb_tree_scan, then tb_tree_scan_affine_backward_reuse on the same
+    workspace), job i+1 is copied in and the results of job i-1 are copied
+    out (three CUDA streams, two sets of device buffers, one workspace).
+
+    run(kinds, locals_, grad_worlds, outs): kinds[i] uint8 (n_i,),
+    locals_[i] and grad_worlds[i] float32 (J_i, 3, 4), outs[i] = (world,
+    grad_local) pinned host tensors of shape (J_i, 3, 4).  An entry may
+    repeat a tensor: the copies of consecutive jobs are ordered on their own
+    stream.  Returns after the last result is in host memory and raises
+    TBError if any job's status word is not TB_OK."""
+
+    def __init__(self, n_max, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        dev = self.device
+        self.n_max = int(n_max)
+        j_max = max(self.n_max // 2, 1)
+        self.sets = []
+        for _ in range(2):
+            self.sets.append({
+                "kind": torch.empty(max(self.n_max, 1), dtype=torch.uint8, device=dev),
+                "local": torch.empty(j_max, 3, 4, dtype=torch.float32, device=dev),
+                "grad_world": torch.empty(j_max, 3, 4, dtype=torch.float32, device=dev),
+                "world": torch.empty(j_max, 3, 4, dtype=torch.float32, device=dev),
+                "grad_local": torch.empty(j_max, 3, 4, dtype=torch.float32, device=dev),
+                "status": torch.zeros(2, dtype=torch.int32, device=dev),  # forward, backward
+                "ev_in": torch.cuda.Event(), "ev_comp": torch.cuda.Event(),
+                "ev_out": torch.cuda.Event(), "used": False,
+            })
+        self.ws_bytes = tb_workspace_size(TB_OP_TREE_BACKWARD, max(self.n_max, 1))
+        self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        self.s_in = torch.cuda.Stream(dev)
+        self.s_comp = torch.cuda.Stream(dev)
+        self.s_out = torch.cuda.Stream(dev)
+
+    def run(self, kinds, locals_, grad_worlds, outs):
+        if not (len(kinds) == len(locals_) == len(grad_worlds) == len(outs)):
+            raise ValueError("kinds, locals_, grad_worlds and outs must have the same length")
+        statuses = torch.zeros(len(kinds), 2, dtype=torch.int32).pin_memory()
+        for i, (k_h, l_h, g_h, o_h) in enumerate(zip(kinds, locals_, grad_worlds, outs)):
+            n, J = k_h.numel(), l_h.shape[0]
+            if n > self.n_max:
+                raise ValueError("job %d has %d elements, more than n_max" % (i, n))
+            if tuple(l_h.shape) != (J, 3, 4) or tuple(g_h.shape) != (J, 3, 4):
+                raise ValueError("job %d: local and grad_world must have shape (J, 3, 4)" % i)
+            S = self.sets[i % 2]
+            with torch.cuda.stream(self.s_in):
+                if S["used"]:
+                    self.s_in.wait_event(S["ev_comp"])  # inputs no longer read
+                S["kind"][:n].copy_(k_h, non_blocking=True)
+                S["local"][:J].copy_(l_h, non_blocking=True)
+                S["grad_world"][:J].copy_(g_h, non_blocking=True)
+                S["ev_in"].record(self.s_in)
+            self.s_comp.wait_event(S["ev_in"])
+            if S["used"]:
+                self.s_comp.wait_event(S["ev_out"])  # outputs already copied out
+            _check(tb_tree_scan(TB_MONOID_AFFINE3X4_F32, TB_DOWN, S["kind"], n, J, S["local"],
+                                S["world"], self.ws, self.ws_bytes, S["status"][0:1], self.s_comp),
+                   "tb_tree_scan")
+            _check(tb_tree_scan_affine_backward_reuse(S["kind"], n, J, S["local"], S["grad_world"],
+                                                      S["grad_local"], self.ws, self.ws_bytes,
+                                                      S["status"][1:2], self.s_comp),
+                   "tb_tree_scan_affine_backward_reuse")
+            S["ev_comp"].record(self.s_comp)
+            with torch.cuda.stream(self.s_out):
+                self.s_out.wait_event(S["ev_comp"])
+                o_h[0].copy_(S["world"][:J], non_blocking=True)
+                o_h[1].copy_(S["grad_local"][:J], non_blocking=True)
+                statuses[i].copy_(S["status"], non_blocking=True)
+                S["ev_out"].record(self.s_out)
+            S["used"] = True
+        self.s_out.synchronize()
+        self.s_comp.synchronize()
+        self.s_in.synchronize()
+        for i in range(len(kinds)):
+            _check(int(statuses[i, 0]), "tree job %d (forward)" % i)
+            _check(int(statuses[i, 1]), "tree job %d (backward)" % i)
+        return outs

@@ -409,3 +409,29 @@ def test_tree_transform_keep_structure():
     assert torch.equal(outs[0][0].view(torch.int32), outs[1][0].view(torch.int32))
     assert torch.equal(outs[0][1].view(torch.int32), outs[1][1].view(torch.int32))
 
+
+def test_tree_pipeline_matches_separate_calls():
+    """Skeleton jobs streamed from pinned host memory with overlapped copies
+    give the device calls' world and gradients (a repeated job and a size
+    change included); a bad job raises with its forward status."""
+    jobs = [inputs.skeleton(j, 70 + j) for j in (40_000, 3_000, 40_000, 25_000)]
+    pipe = binding.TreePipeline(max(k.size for k, _, _ in jobs))
+    kinds = [torch.from_numpy(k).pin_memory() for k, _, _ in jobs]
+    locs = [torch.from_numpy(L).pin_memory() for _, L, _ in jobs]
+    gws = [torch.from_numpy(W).pin_memory() for _, _, W in jobs]
+    outs = [(torch.empty(L.shape, dtype=torch.float32).pin_memory(),
+             torch.empty(L.shape, dtype=torch.float32).pin_memory()) for _, L, _ in jobs]
+    pipe.run(kinds, locs, gws, outs)
+    for (k, L, W), (world_h, grad_h) in zip(jobs, outs):
+        kd, Ld, Wd = (torch.from_numpy(a).cuda() for a in (k, L, W))
+        world = binding.tree_scan(binding.TB_MONOID_AFFINE3X4_F32, binding.TB_DOWN, kd, Ld)
+        grad = binding.affine_backward(kd, Ld, Wd)
+        assert torch.equal(world_h.view(torch.int32), world.cpu().view(torch.int32))
+        assert torch.equal(grad_h.view(torch.int32), grad.cpu().view(torch.int32))
+    bad = jobs[1][0].copy()
+    bad[7] = 9
+    kinds[1] = torch.from_numpy(bad).pin_memory()
+    with pytest.raises(binding.TBError) as ei:
+        pipe.run(kinds, locs, gws, outs)
+    assert ei.value.code == binding.TB_ERR_BAD_KIND
+
