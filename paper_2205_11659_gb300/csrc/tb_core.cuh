@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <climits>
 #include <cmath>
+#include <cstring>
 
 #include "tb_prims.cuh"
 
@@ -109,6 +110,37 @@ struct OpIsect { __device__ float4 operator()(float4 a, float4 b) const { return
 struct OpUnite { __device__ float4 operator()(float4 a, float4 b) const { return box_unite(a, b); } };
 
 __device__ __forceinline__ int2 shfl_up(int2 v, int d) { return make_int2(shfl_up(v.x, d), shfl_up(v.y, d)); }
+
+// Shuffles of any other trivially copyable value (a monoid value of the
+// caller's own), 32 bits at a time.  The overloads for the built-in types
+// take precedence.
+template <class T, class F>
+__device__ __forceinline__ T shfl_words(const T& v, F f) {
+  static_assert(sizeof(T) % 4 == 0, "shuffled values are whole 32-bit words");
+  unsigned w[sizeof(T) / 4];
+  memcpy(w, &v, sizeof(T));
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(T) / 4); ++i) w[i] = f(w[i]);
+  T r;
+  memcpy(&r, w, sizeof(T));
+  return r;
+}
+template <class T>
+__device__ __forceinline__ T shfl_up(const T& v, int d) {
+  return shfl_words(v, [d](unsigned x) { return (unsigned)shfl_up((int)x, d); });
+}
+template <class T>
+__device__ __forceinline__ T shfl_down(const T& v, int d) {
+  return shfl_words(v, [d](unsigned x) { return (unsigned)shfl_down((int)x, d); });
+}
+template <class T>
+__device__ __forceinline__ T shfl_xor(const T& v, int m) {
+  return shfl_words(v, [m](unsigned x) { return (unsigned)shfl_xor((int)x, m); });
+}
+template <class T>
+__device__ __forceinline__ T shfl_idx(const T& v, int src) {
+  return shfl_words(v, [src](unsigned x) { return (unsigned)shfl_idx((int)x, src); });
+}
 __device__ __forceinline__ float4 shfl_xor(float4 v, int m) {
   return make_float4(shfl_xor(v.x, m), shfl_xor(v.y, m), shfl_xor(v.z, m), shfl_xor(v.w, m));
 }
