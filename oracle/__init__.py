@@ -14,6 +14,7 @@ tree-structured scenes" (arXiv 2205.11659):
 * :func:`match_parens`   Sec. 2, Fig. 1 -- the strong matching problem.
 * :func:`bboxes`         Sec. 1 and Sec. 6 -- clip intersection down the tree,
   blend union up the tree.
+* :func:`open_positions` Sec. 1.1 -- stream compaction of the opens.
 * :func:`tree_scan_i32`, :func:`tree_scan_box`, :func:`affine_forward`,
   :func:`affine_up` -- Sec. 1 / Sec. 13, any monoid over the tree.
 * :func:`affine_backward` -- adjoint of the root-path transform product.
@@ -65,6 +66,7 @@ def _load():
             lib.orc_match_parens.argtypes = [p, i64, p, p]
             lib.orc_bboxes.argtypes = [p, p, i64, p, p, p]
             lib.orc_bboxes_batched.argtypes = [p, p, p, i64, p, p, p]
+            lib.orc_open_positions.argtypes = [p, i64, p, i64, p]
             lib.orc_tree_scan_i32.argtypes = [i32, p, i64, p, p]
             lib.orc_tree_scan_box.argtypes = [i32, i32, p, i64, p, p]
             lib.orc_affine_forward.argtypes = [p, i64, p, p]
@@ -72,7 +74,8 @@ def _load():
             lib.orc_affine_loss.argtypes = [p, i64, p, p, i64, p]
             lib.orc_affine_backward.argtypes = [p, i64, p, p, p, i64]
             for f in (lib.orc_bic, lib.orc_match_parens, lib.orc_bboxes,
-                      lib.orc_bboxes_batched, lib.orc_tree_scan_i32,
+                      lib.orc_bboxes_batched, lib.orc_open_positions,
+                      lib.orc_tree_scan_i32,
                       lib.orc_tree_scan_box, lib.orc_affine_forward,
                       lib.orc_affine_up, lib.orc_affine_loss,
                       lib.orc_affine_backward):
@@ -142,6 +145,17 @@ def bboxes_batched(kind, box, offsets):
     st = _load().orc_bboxes_batched(_ptr(k), _ptr(b), _ptr(off), off.size - 1,
                                     _ptr(parent), _ptr(match), _ptr(out))
     return st, parent, match, out
+
+
+def open_positions(kind, cap=None):
+    """(status, pos, count): indices of the opens in stream order -- Sec. 1.1.
+    Only the first ``cap`` (default: all) are returned."""
+    k = _kinds(kind)
+    c = ctypes.c_int64()
+    cap = k.size if cap is None else int(cap)
+    pos = np.empty(max(cap, 0), np.int32)
+    st = _load().orc_open_positions(_ptr(k), k.size, _ptr(pos), cap, ctypes.byref(c))
+    return st, pos[:min(cap, c.value)].copy(), c.value
 
 
 def _num_opens(k):

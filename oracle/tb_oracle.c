@@ -15,6 +15,8 @@
  *   orc_bboxes              -- Sec. 1 and Sec. 6: clip = intersection flowing
  *                              down, blend = union flowing up
  *   orc_bboxes_batched      -- orc_bboxes per scene, scene-local indices
+ *   orc_open_positions      -- Sec. 1.1, stream compaction of the clip and
+ *                              blend nodes (the opens), in stream order
  *   orc_tree_scan_*         -- Sec. 1 / Sec. 13, "any monoid" over the tree
  *   orc_affine_*            -- the same stack walk for 3x4 affine transforms
  *                              (root-path products) and their adjoint, fp64
@@ -135,6 +137,26 @@ int orc_match_parens(const uint8_t* kind, int64_t n, int32_t* parent,
   if (st == ORC_OK && sp != 0) st = ORC_UNBALANCED;
   free(stack);
   return st;
+}
+
+/* ------------------------------------------------------------ Sec. 1.1 */
+/* Stream compaction of the opens: the index of every OPEN_CLIP or
+ * OPEN_BLEND element, in stream order (so entry r is the element of the
+ * r-th open, joint r of the tree scans).  Entries r < cap are written;
+ * *count receives the number of opens.  Nesting is not checked. */
+int orc_open_positions(const uint8_t* kind, int64_t n, int32_t* pos, int64_t cap,
+                       int64_t* count) {
+  int st = check_kinds(kind, n);
+  if (st) return st;
+  int64_t r = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (is_open(kind[i])) {
+      if (r < cap) pos[r] = (int32_t)i;
+      ++r;
+    }
+  }
+  *count = r;
+  return ORC_OK;
 }
 
 /* ------------------------------------------------------ Sec. 1, Sec. 6 */

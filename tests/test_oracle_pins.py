@@ -283,6 +283,66 @@ def test_hand_scene():
     assert np.array_equal(p2, par) and np.array_equal(m2, mat) and same_bits(o2, out)
 
 
+# --- stream compaction of the opens (Sec. 1.1) -----------------------------
+
+def test_open_positions_hand_scene():
+    """The opens of the hand-worked scene are its C and B elements; they are
+    also exactly the elements whose printed match lies after them."""
+    g = gold()["hand_scene"]
+    k = kinds_of(g["kinds"])
+    st, pos, count = oracle.open_positions(k)
+    assert st == oracle.OK and count == 3
+    assert list(pos) == [0, 2, 4]
+    assert list(pos) == [i for i, m in enumerate(g["match"]) if m > i]
+
+
+def test_open_positions_closed_form_without_leaves():
+    """Without leaves, an open at i with depth d before it has (i + d) / 2
+    opens before it (opens - closes = d, opens + closes = i), so it is entry
+    (i + d) / 2.  Every balanced string of length <= 12."""
+    for n in range(0, 13, 2):
+        for bits in itertools.product((1, 3), repeat=n):
+            d, ok = 0, True
+            for b in bits:
+                d += 1 if b == 1 else -1
+                ok &= d >= 0
+            if not ok or d != 0:
+                continue
+            k = np.array(bits, np.uint8)
+            st, pos, count = oracle.open_positions(k)
+            assert st == oracle.OK and count == n // 2
+            d = 0
+            for i, b in enumerate(bits):
+                if b == 1:
+                    assert pos[(i + d) // 2] == i
+                    d += 1
+                else:
+                    d -= 1
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_open_positions_index_the_joints(seed):
+    """Entry r is joint r of the tree scans: the stream depth just after
+    that element equals joint r's depth from an ADD DOWN scan of ones."""
+    k, _ = inputs.random_walk_scene(20_000, 90 + seed)
+    st, pos, count = oracle.open_positions(k)
+    assert st == oracle.OK
+    st, dep = oracle.tree_scan_i32(oracle.DOWN, k, np.ones(count, np.int32))
+    assert st == oracle.OK
+    stream_depth = np.cumsum(np.where((k == 1) | (k == 2), 1, np.where(k == 3, -1, 0)))
+    assert np.array_equal(stream_depth[pos], dep)
+    assert np.all(np.diff(pos) > 0)
+
+
+def test_open_positions_cap_and_bad_kind():
+    k, _ = inputs.random_walk_scene(5000, 95)
+    st, full, count = oracle.open_positions(k)
+    st2, part, count2 = oracle.open_positions(k, cap=17)
+    assert st2 == oracle.OK and count2 == count and np.array_equal(part, full[:17])
+    st3, _, _ = oracle.open_positions(np.array([1, 4, 3], np.uint8))
+    assert st3 == oracle.BAD_KIND
+
+
 def test_zero_area_is_empty():
     # a leaf of zero width is empty; a unit-width one is kept
     k = np.array([0, 0, 1, 0, 3], np.uint8)
