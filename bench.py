@@ -41,6 +41,8 @@ WORKLOADS = {
     "rw16": "bbox+paren pass, one random-walk scene, N=2^16 (launch-latency size)",
     "rw24": "bbox+paren pass, one random-walk scene, N=2^24 (profiling size)",
     "match26": "parentheses matching only (parent and match indices), one random-walk scene, N=2^26",
+    "opens26": "stream compaction of the opens (clip and blend nodes) of one random-walk scene, "
+               "N=2^26",
     "skel20": "affine tree scan forward + adjoint, one skeleton of J=2^20 joints (N=2J), depth <= 64",
     "skel20s": "affine tree scan forward + adjoint, one skeleton of J=2^18 joints (profiling size)",
     "skelbatch": "affine tree scan forward + adjoint through TreeTransform, 256 skeletons with "
@@ -54,15 +56,15 @@ BWD_BYTES_PER_JOINT = 146  # 2 kinds + 48 local + 48 grad_world read, 48 grad_lo
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the
 # kernel sources they were taken on; a changed kernel reports null.
 NCU_TRAFFIC = {
-    # 639.4 MB per launch measured on the 2^24 random walk; the 2^26 entry
+    # 639.3 MB per launch measured on the 2^24 random walk; the 2^26 entry
     # scales it by the element count (traffic tracks the 41 B/elem).
-    "60536774250694f4": {"rw24": 639.4e6, "rw26": 639.4e6 * 4},
+    "f213b16c57db5758": {"rw24": 639.3e6, "rw26": 639.3e6 * 4},
 }
 
 
 def make_workload(name, seed=0):
     from paper_2205_11659_gb300 import inputs
-    if name in ("rw26", "match26"):
+    if name in ("rw26", "match26", "opens26"):
         k, b = inputs.random_walk_scene(1 << 26, seed)
         return k, b, None
     if name == "rw24":
@@ -91,6 +93,7 @@ def make_workload(name, seed=0):
 
 
 SCENE_SOURCES = ("tb_api.cu", "tb_core.cuh", "tb_prims.cuh", "tb_scene_kernels.cuh")
+OPEN_SOURCES = ("tb_open_api.cu", "tb_core.cuh", "tb_prims.cuh", "tb_open_kernels.cuh")
 TREE_SOURCES = ("tb_core.cuh", "tb_prims.cuh", "tb_tree_api.cu", "tb_tree_kernels.cuh")
 
 
@@ -247,6 +250,144 @@ def time_oracle(kind, box, offsets, match_only=False, budget_s=12.0, min_runs=1,
             return kind.size * runs / el / 1e9, runs, el
 
 
+def time_oracle_opens(kind, budget_s=12.0, max_runs=50):
+    import oracle
+    oracle.build()
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        assert oracle.open_positions(kind)[0] == oracle.OK
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or runs >= max_runs:
+            return kind.size * runs / el / 1e9, runs, el
+
+
+def run_opens(args, torch, world, rank, dev):
+    """tb_open_positions over the 2^26 random walk: device-timed calls with
+    the kinds resident in HBM (L2 flushed before each), the same call as a
+    CUDA graph, and end to end from pinned host memory."""
+    from paper_2205_11659_gb300 import binding
+    kind, _, _ = make_workload(args.workload, seed=0)
+    n = int(kind.size)
+    k_d = torch.from_numpy(kind).to(dev)
+    cap = n // 2 + 1
+    pos = torch.empty(cap, dtype=torch.int32, device=dev)
+    count = torch.empty(1, dtype=torch.int32, device=dev)
+    nb = binding.tb_workspace_size(binding.TB_OP_OPEN_POSITIONS, n)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        rc = binding.tb_open_positions(k_d, n, pos, cap, count, ws, nb, status, stream)
+        if rc != binding.TB_OK:
+            raise binding.TBError(rc, "bench step")
+
+    flush = L2Flush(torch, dev, kind.nbytes)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert int(status.item()) == binding.TB_OK
+    J = int(count.item())
+    K = args.steps
+    phase = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    for evs in phase:
+        for e in evs:
+            e.record(stream)
+    steps_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(K)]
+    clocks = ClockSampler(dev.index)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(K):
+        flush()
+        steps_ev[i][0].record(stream)
+        binding.tb_set_phase_events(phase[i])
+        step()
+        steps_ev[i][1].record(stream)
+    binding.tb_set_phase_events(None)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_step = job_time_ms(sum(a.elapsed_time(b) for a, b in steps_ev), world, dev) / K
+    assert int(status.item()) == binding.TB_OK and int(count.item()) == J
+    names = ["count", "offsets", "scatter"]
+    phases = {nm: statistics.mean(phase[i][j].elapsed_time(phase[i][j + 1]) for i in range(K))
+              for j, nm in enumerate(names)}
+    value = job_rate(n, world, ms_step)
+
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rcg = binding.tb_open_positions(k_d, n, pos, cap, count, ws, nb, status, None)
+    assert rcg == binding.TB_OK
+    g.replay()
+    torch.cuda.synchronize()
+    graph_ms = timed_each(torch, stream, g.replay, K, flush)
+    del g
+
+    # end to end: kinds from pinned host memory, the call, then the count and
+    # the positions back (the count decides how many positions to copy)
+    kind_h = torch.from_numpy(kind).pin_memory()
+    pos_h = torch.empty(cap, dtype=torch.int32).pin_memory()
+    count_h = torch.empty(1, dtype=torch.int32).pin_memory()
+
+    def e2e_step():
+        k_d.copy_(kind_h, non_blocking=True)
+        step()
+        count_h.copy_(count, non_blocking=True)
+        torch.cuda.synchronize()
+        c = int(count_h[0])
+        pos_h[:c].copy_(pos[:c], non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_step()
+    e2e_steps = max(3, K)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+
+    peak, peak_src = measured_peaks()
+    alg = n + 4 * J  # kinds read once, one int32 per open written
+    achieved = alg / (ms_step * 1e-3) / 1e9
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, runs, el = time_oracle_opens(kind)
+        cpu = {"value": round(v, 4), "unit": "Gelem/s", "cores": 1, "kind": "oracle",
+               "sample": "the full workload (%d elements) x %d runs, %.1f s, single thread"
+                         % (n, runs, el)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "Gelem/s", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "n": n, "opens": J, "seed": 0,
+                       "l2": flush.describe(kind.nbytes),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm",
+                         "kernel": "tb_open_positions (count, offsets, scatter launches)",
+                         "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "algorithmic_bytes_per_launch": int(alg)},
+            "phases_ms": {k: round(v, 4) for k, v in phases.items()},
+            "graph": {"ms_per_step": round(graph_ms, 4),
+                      "value": round(world * n / (graph_ms * 1e-3) / 1e9, 3), "unit": "Gelem/s",
+                      "note": "the same call replayed as one CUDA graph"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(world * n / e2e_s / 1e9, 3), "unit": "Gelem/s",
+                    "h2d_bytes_per_step": int(kind.nbytes), "d2h_bytes_per_step": int(4 + 4 * J),
+                    "how": "copy in, the call, count and positions copied back, one scene at a "
+                           "time"},
+            "gpu_launches": 3 * K,
+            "clocks": clk,
+            "kernel_hash": kernel_hash(OPEN_SOURCES),
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def time_oracle_tree(kind, L, W, budget_s=12.0, max_runs=50):
     import oracle
     oracle.build()
@@ -274,6 +415,8 @@ def run_reference(args):
     def once():
         if args.workload == "match26":
             return oracle.match_parens(kind)[0]
+        if args.workload == "opens26":
+            return oracle.open_positions(kind)[0]
         if offsets is None:
             return oracle.bboxes(kind, box)[0]
         return oracle.bboxes_batched(kind, box, offsets)[0]
@@ -288,7 +431,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Gelem/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8" if args.workload == "opens26" else "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "n": int(kind.size), "seed": 0},
             "cpu_baseline": {"value": round(value, 4), "unit": "Gelem/s", "cores": 1,
                              "kind": "oracle", "sample": sample},
@@ -593,8 +737,9 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     from paper_2205_11659_gb300 import _build, binding
     _build.build()
-    if args.workload in TREE_WORKLOADS:
-        rc = run_tree(args, torch, world, rank, dev)
+    if args.workload in TREE_WORKLOADS or args.workload == "opens26":
+        run = run_tree if args.workload in TREE_WORKLOADS else run_opens
+        rc = run(args, torch, world, rank, dev)
         if world > 1:
             torch.distributed.barrier()
             torch.distributed.destroy_process_group()

@@ -67,7 +67,8 @@ enum {
   TB_OP_BBOXES = 1,
   TB_OP_BBOXES_BATCHED = 2,
   TB_OP_TREE_SCAN = 3,
-  TB_OP_TREE_BACKWARD = 4
+  TB_OP_TREE_BACKWARD = 4,
+  TB_OP_OPEN_POSITIONS = 5
 };
 
 /* Monoids and directions of tb_tree_scan. */
@@ -124,6 +125,21 @@ tb_status tb_bboxes_batched(const uint8_t* kind, const float* box,
                             int64_t n_total, int32_t* parent, int32_t* match,
                             float* box_out, void* ws, size_t ws_bytes,
                             int32_t* d_status, void* stream);
+
+/* Stream compaction of the opens (Sec. 1.1: a renderer keeps just the clip
+ * and blend nodes this way).  pos[r] = the stream index of the r-th open
+ * (OPEN_CLIP or OPEN_BLEND) in stream order, which is the element of joint
+ * r of tb_tree_scan; *d_count = the number of opens (a device int32).
+ *   - pos holds max_opens int32 entries; only r < max_opens are written, so
+ *     a short buffer is safe and *d_count still reports all opens (a
+ *     balanced stream has at most n / 2).
+ *   - Bytes above 3 are reported as TB_ERR_BAD_KIND in d_status (and counted
+ *     as leaves).  Nesting is not checked: any byte stream of kinds works.
+ * Results are exact and deterministic.  Reads kind twice, writes 4 bytes per
+ * open. */
+tb_status tb_open_positions(const uint8_t* kind, int64_t n, int32_t* pos,
+                            int64_t max_opens, int32_t* d_count, void* ws,
+                            size_t ws_bytes, int32_t* d_status, void* stream);
 
 /* Tree scans: the monoid generalisation of Sec. 1 and Sec. 13 (any
  * associative operation with an identity, neither commutative nor

@@ -37,6 +37,7 @@ TB_OP_BBOXES = 1
 TB_OP_BBOXES_BATCHED = 2
 TB_OP_TREE_SCAN = 3
 TB_OP_TREE_BACKWARD = 4
+TB_OP_OPEN_POSITIONS = 5
 
 TB_MONOID_BBOX_ISECT = 0
 TB_MONOID_BBOX_UNION = 1
@@ -85,9 +86,10 @@ def lib():
             L.tb_debug_withhold_tile.restype = i32
             L.tb_tree_scan_affine_backward.argtypes = [p, i64, i64, p, p, p, p, sz, p, p]
             L.tb_tree_scan_affine_backward_reuse.argtypes = [p, i64, i64, p, p, p, p, sz, p, p]
+            L.tb_open_positions.argtypes = [p, i64, p, i64, p, p, sz, p, p]
             for f in (L.tb_match_parens, L.tb_bboxes, L.tb_bboxes_batched, L.tb_set_phase_events,
                       L.tb_bboxes_static_ws, L.tb_tree_scan, L.tb_tree_scan_affine_backward,
-                      L.tb_tree_scan_affine_backward_reuse):
+                      L.tb_tree_scan_affine_backward_reuse, L.tb_open_positions):
                 f.restype = i32
             L.tb_version.argtypes = []
             L.tb_version.restype = ctypes.c_char_p
@@ -134,6 +136,11 @@ def tb_bboxes(kind, box, n, parent, match, box_out, ws, ws_bytes, d_status, stre
     return lib().tb_bboxes(_ptr(kind), _ptr(box), int(n), _ptr(parent), _ptr(match),
                            _ptr(box_out), _ptr(ws), int(ws_bytes), _ptr(d_status),
                            _stream(stream))
+
+
+def tb_open_positions(kind, n, pos, max_opens, d_count, ws, ws_bytes, d_status, stream=None):
+    return lib().tb_open_positions(_ptr(kind), int(n), _ptr(pos), int(max_opens), _ptr(d_count),
+                                   _ptr(ws), int(ws_bytes), _ptr(d_status), _stream(stream))
 
 
 def tb_bboxes_batched(kind, box, offsets, num_scenes, n_total, parent, match, box_out, ws,
@@ -251,6 +258,29 @@ def match_parens(kind, check=True):
     if not kind.is_cuda:
         return parent.cpu(), match.cpu()
     return parent, match
+
+
+def open_positions(kind, max_opens=None, check=True):
+    """Stream indices of the opens, in stream order (int32 tensor), and their
+    count.  max_opens (default n: room for any byte stream) sizes the output.
+    With check the call synchronises, raises on a data error and trims the
+    result to the count (the count is then an int); otherwise it returns the
+    untrimmed buffer and the device count."""
+    dev = kind.device if kind.is_cuda else torch.device("cuda", torch.cuda.current_device())
+    k = _on_device(kind, torch.uint8, "kind", dev)
+    n = k.numel()
+    cap = n if max_opens is None else int(max_opens)
+    pos = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    count = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = workspace(dev)
+    nb = tb_workspace_size(TB_OP_OPEN_POSITIONS, n)
+    _check(tb_open_positions(k, n, pos, cap, count, ws.get(nb), nb, ws.status), "tb_open_positions")
+    if not check:
+        return pos, count
+    check_status(ws, "tb_open_positions")
+    c = int(count.item())
+    pos = pos[:min(c, cap)]
+    return (pos.cpu() if not kind.is_cuda else pos), c
 
 
 def bboxes(kind, box, want_indices=True, check=True, out=None):

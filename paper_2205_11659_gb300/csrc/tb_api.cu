@@ -257,6 +257,8 @@ size_t tb_workspace_size(int op, int64_t n, int64_t num_scenes) {
     case TB_OP_TREE_SCAN:
     case TB_OP_TREE_BACKWARD:
       return tb_internal::tree_ws_bytes(op, n);
+    case TB_OP_OPEN_POSITIONS:
+      return tb_internal::open_ws_bytes(n);
     default:
       return 0;
   }

@@ -1,5 +1,6 @@
 // tb_internal.h -- what the translation units of the library share: the
-// phase-event hook, the look-back test hook and the tree-scan workspace size.
+// phase-event hook, the look-back test hook and the workspace sizes of the
+// operations that live in their own translation units.
 #ifndef TB_INTERNAL_H
 #define TB_INTERNAL_H
 
@@ -23,6 +24,9 @@ int withheld_tile();
 
 // Scratch bytes of the tree scans (op TB_OP_TREE_SCAN or TB_OP_TREE_BACKWARD).
 size_t tree_ws_bytes(int op, int64_t n);
+
+// Scratch bytes of tb_open_positions.
+size_t open_ws_bytes(int64_t n);
 
 }  // namespace tb_internal
 

@@ -32,7 +32,7 @@ def test_header_declares_entry_points():
     for n in ("tb_workspace_size", "tb_match_parens", "tb_bboxes", "tb_bboxes_batched",
               "tb_tree_scan", "tb_tree_scan_affine_backward",
               "tb_tree_scan_affine_backward_reuse", "tb_set_phase_events",
-              "tb_debug_withhold_tile", "tb_version"):
+              "tb_debug_withhold_tile", "tb_version", "tb_open_positions"):
         assert n in names
 
 
@@ -60,6 +60,11 @@ def test_workspace_size(lib):
     assert g2 - t2 >= 2 * 48 * (1 << 19)
     assert b.tb_workspace_size(b.TB_OP_TREE_SCAN, 0) == 0
     assert b.tb_workspace_size(99, 1 << 20) == 0
+    # tile counts and tile offsets: two int32 per tile of 16384 elements
+    o1 = b.tb_workspace_size(b.TB_OP_OPEN_POSITIONS, 1)
+    o2 = b.tb_workspace_size(b.TB_OP_OPEN_POSITIONS, 1 << 26)
+    assert 0 < o1 <= 512 and 2 * 4 * (1 << 12) <= o2 <= 2 * 4 * (1 << 12) + 512
+    assert b.tb_workspace_size(b.TB_OP_OPEN_POSITIONS, 0) == 0
 
 
 def test_argument_errors_before_any_launch(lib):
@@ -84,6 +89,29 @@ def test_argument_errors_before_any_launch(lib):
     assert lib.tb_set_phase_events(None, 0) == b.TB_OK
     assert lib.tb_debug_withhold_tile(-2) == b.TB_ERR_INVALID_ARG
     assert lib.tb_debug_withhold_tile(-1) == b.TB_OK
+
+
+def test_open_positions_argument_errors(lib):
+    from paper_2205_11659_gb300 import binding as b
+    p = ctypes.c_void_p
+    fake, big = 1 << 20, 1 << 40
+
+    def call(kind=fake, n=10, pos=fake, cap=5, count=fake + 64, ws=fake, nb=big, status=fake + 128):
+        return lib.tb_open_positions(p(kind) if kind else None, n, p(pos) if pos else None, cap,
+                                     p(count) if count else None, p(ws) if ws else None, nb,
+                                     p(status) if status else None, None)
+
+    assert call(n=-1) == b.TB_ERR_INVALID_ARG
+    assert call(n=1 << 31) == b.TB_ERR_INVALID_ARG
+    assert call(cap=-1) == b.TB_ERR_INVALID_ARG
+    assert call(kind=0) == b.TB_ERR_INVALID_ARG
+    assert call(kind=fake + 1) == b.TB_ERR_INVALID_ARG
+    assert call(pos=0) == b.TB_ERR_INVALID_ARG          # room for 5 but no buffer
+    assert call(pos=fake + 2) == b.TB_ERR_INVALID_ARG
+    assert call(count=0) == b.TB_ERR_INVALID_ARG
+    assert call(status=0) == b.TB_ERR_INVALID_ARG
+    assert call(ws=0) == b.TB_ERR_INVALID_ARG
+    assert call(nb=8) == b.TB_ERR_WORKSPACE
 
 
 def test_tree_scan_argument_errors(lib):
