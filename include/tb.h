@@ -156,7 +156,9 @@ tb_status tb_open_positions(const uint8_t* kind, int64_t n, int32_t* pos,
  * A stream of several trees (a forest, e.g. skeletons laid end to end) is
  * fine: each tree is scanned on its own.  A wrong num_joints is reported as
  * TB_ERR_INVALID_ARG in d_status; unbalanced streams and bad kinds as in
- * tb_match_parens. */
+ * tb_match_parens.  tb_open_positions gives the element of every joint.
+ * For a monoid other than these four, tb_monoid.cuh (next to this header)
+ * instantiates the same scans for a caller-defined type. */
 tb_status tb_tree_scan(int monoid, int dir, const uint8_t* kind, int64_t n,
                        int64_t num_joints, const void* in, void* out, void* ws,
                        size_t ws_bytes, int32_t* d_status, void* stream);
