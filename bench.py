@@ -60,6 +60,10 @@ NCU_TRAFFIC = {
     # scales it by the element count (traffic tracks the 41 B/elem).
     "f213b16c57db5758": {"rw24": 639.3e6, "rw26": 639.3e6 * 4},
 }
+# The same for one tb_open_positions call (its three launches summed), keyed
+# by the hash of the compaction sources: the kinds read twice, and the part
+# of the positions that already left L2 when the scatter ended.
+OPEN_NCU_TRAFFIC = {"242089a61914018c": {"opens26": 139.3e6}}
 
 
 def make_workload(name, seed=0):
@@ -369,7 +373,9 @@ def run_opens(args, torch, world, rank, dev):
             "roofline": {"bound": "hbm",
                          "kernel": "tb_open_positions (count, offsets, scatter launches)",
                          "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src,
-                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": OPEN_NCU_TRAFFIC.get(kernel_hash(OPEN_SOURCES), {}).get(
+                             args.workload),
                          "algorithmic_bytes_per_launch": int(alg)},
             "phases_ms": {k: round(v, 4) for k, v in phases.items()},
             "graph": {"ms_per_step": round(graph_ms, 4),
