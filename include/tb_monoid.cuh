@@ -8,6 +8,7 @@
  *
  *   struct MyMonoid {
  *     using V = ...;                                   // trivially copyable,
+ *                                                      // a multiple of 4 bytes,
  *                                                      // at most 48 bytes
  *     __device__ static V identity();
  *     __device__ static V combine(const V& a, const V& b);  // a is earlier
@@ -43,6 +44,8 @@ tb_status tree_scan(int dir, const uint8_t* kind, int64_t n, int64_t num_joints,
                     void* out, void* ws, size_t ws_bytes, int32_t* d_status, cudaStream_t stream) {
   static_assert(sizeof(typename M::V) <= launch::kValBytes,
                 "a monoid value may take at most 48 bytes of workspace per joint");
+  static_assert(sizeof(typename M::V) % 4 == 0,
+                "a monoid value is whole 32-bit words (warp shuffles move it word by word)");
   if (dir != TB_DOWN && dir != TB_UP) return TB_ERR_INVALID_ARG;
   tb_status st = launch::check_common(kind, n, num_joints, ws, d_status);
   if (st != TB_OK) return st;

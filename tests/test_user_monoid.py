@@ -27,6 +27,46 @@ def test_header_compiles(tmp_path):
     _nvcc(["-c", SRC, "-o", str(tmp_path / "user.o")])
 
 
+_SIZED = r"""
+#include <cstdint>
+#include "tb_monoid.cuh"
+struct Sized {
+  struct V { ELEM e[COUNT]; };
+  __device__ static V identity() { V v; for (int i = 0; i < COUNT; ++i) v.e[i] = 0; return v; }
+  __device__ static V combine(const V& a, const V& b) {
+    V v; for (int i = 0; i < COUNT; ++i) v.e[i] = a.e[i] + b.e[i]; return v;
+  }
+  __device__ static V load(const void* p, int64_t i) { return static_cast<const V*>(p)[i]; }
+  __device__ static void store(void* p, int64_t i, const V& v) { static_cast<V*>(p)[i] = v; }
+};
+int run(const uint8_t* k, int64_t n, int64_t J, const void* in, void* out, void* ws, size_t nb,
+        int32_t* st) {
+  return tb::tree_scan<Sized>(TB_DOWN, k, n, J, in, out, ws, nb, st, nullptr);
+}
+"""
+
+
+@pytest.mark.parametrize("elem,count,error", [
+    ("unsigned", 3, None),                        # 12 bytes: whole words, under the limit
+    ("unsigned", 13, "at most 48 bytes"),         # 52 bytes: over the workspace slot
+    ("unsigned char", 6, "whole 32-bit words"),   # 6 bytes: not whole words
+])
+def test_value_size_rules(tmp_path, elem, count, error):
+    """The header accepts values of whole 32-bit words up to 48 bytes and
+    rejects others at compile time with a message saying why."""
+    from paper_2205_11659_gb300 import _build
+    src = tmp_path / "sized.cu"
+    src.write_text(_SIZED)
+    cmd = [_build.nvcc()] + _build.ARCH + ["-O1", "-std=c++17", "-I" + os.path.join(ROOT, "include"),
+                                          "-DELEM=" + elem, "-DCOUNT=%d" % count, "-c", str(src),
+                                          "-o", str(tmp_path / "sized.o")]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if error is None:
+        assert r.returncode == 0, r.stderr
+    else:
+        assert r.returncode != 0 and error in r.stderr, r.stderr
+
+
 def test_no_process_wide_launch_state(tmp_path):
     """The launch sequence keeps once-per-kernel flags (shared-memory limit
     raised) in function-local statics.  They must stay private to each
