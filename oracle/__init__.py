@@ -15,6 +15,7 @@ tree-structured scenes" (arXiv 2205.11659):
 * :func:`bboxes`         Sec. 1 and Sec. 6 -- clip intersection down the tree,
   blend union up the tree.
 * :func:`open_positions` Sec. 1.1 -- stream compaction of the opens.
+* :func:`clip_out`       Sec. 9 -- the running clip intersection per element.
 * :func:`tree_scan_i32`, :func:`tree_scan_box`, :func:`affine_forward`,
   :func:`affine_up` -- Sec. 1 / Sec. 13, any monoid over the tree.
 * :func:`affine_backward` -- adjoint of the root-path transform product.
@@ -67,6 +68,7 @@ def _load():
             lib.orc_bboxes.argtypes = [p, p, i64, p, p, p]
             lib.orc_bboxes_batched.argtypes = [p, p, p, i64, p, p, p]
             lib.orc_open_positions.argtypes = [p, i64, p, i64, p]
+            lib.orc_clip_out.argtypes = [p, p, i64, p]
             lib.orc_tree_scan_i32.argtypes = [i32, p, i64, p, p]
             lib.orc_tree_scan_box.argtypes = [i32, i32, p, i64, p, p]
             lib.orc_affine_forward.argtypes = [p, i64, p, p]
@@ -74,7 +76,7 @@ def _load():
             lib.orc_affine_loss.argtypes = [p, i64, p, p, i64, p]
             lib.orc_affine_backward.argtypes = [p, i64, p, p, p, i64]
             for f in (lib.orc_bic, lib.orc_match_parens, lib.orc_bboxes,
-                      lib.orc_bboxes_batched, lib.orc_open_positions,
+                      lib.orc_bboxes_batched, lib.orc_open_positions, lib.orc_clip_out,
                       lib.orc_tree_scan_i32,
                       lib.orc_tree_scan_box, lib.orc_affine_forward,
                       lib.orc_affine_up, lib.orc_affine_loss,
@@ -156,6 +158,17 @@ def open_positions(kind, cap=None):
     pos = np.empty(max(cap, 0), np.int32)
     st = _load().orc_open_positions(_ptr(k), k.size, _ptr(pos), cap, ctypes.byref(c))
     return st, pos[:min(cap, c.value)].copy(), c.value
+
+
+def clip_out(kind, box):
+    """(status, clip): per element the intersection of its box with every clip
+    ancestor's box (Sec. 9); blends pass the clip in force on, a close gets
+    its open's value."""
+    k = _kinds(kind)
+    b = np.ascontiguousarray(box, dtype=np.float32).reshape(-1, 4)
+    out = np.zeros((k.size, 4), np.float32)
+    st = _load().orc_clip_out(_ptr(k), _ptr(b), k.size, _ptr(out))
+    return st, out
 
 
 def _num_opens(k):

@@ -15,6 +15,8 @@
  *   orc_bboxes              -- Sec. 1 and Sec. 6: clip = intersection flowing
  *                              down, blend = union flowing up
  *   orc_bboxes_batched      -- orc_bboxes per scene, scene-local indices
+ *   orc_clip_out            -- Sec. 9, the stack snapshot's running clip
+ *                              intersection, per element
  *   orc_open_positions      -- Sec. 1.1, stream compaction of the clip and
  *                              blend nodes (the opens), in stream order
  *   orc_tree_scan_*         -- Sec. 1 / Sec. 13, "any monoid" over the tree
@@ -231,6 +233,44 @@ int orc_bboxes(const uint8_t* kind, const float* box, int64_t n,
         if (sp > 0) box_union(stack[sp - 1].uni, e->uni, stack[sp - 1].uni);
         break;
       }
+    }
+  }
+  if (sp != 0) st = ORC_UNBALANCED;
+done:
+  free(stack);
+  return st;
+}
+
+/* The clip value of the stack snapshot at every element (Sec. 9: each
+ * entry is the intersection of its element's box with the boxes of all its
+ * clip ancestors).  LEAF and OPEN_CLIP: own box intersected with the clip in
+ * force; OPEN_BLEND: the clip in force (its box is ignored); CLOSE: the value
+ * of the open it closes.  The raw intersection is written, not made
+ * canonical (it is what flows down the clip chain).  Root clip: universe. */
+int orc_clip_out(const uint8_t* kind, const float* box, int64_t n, float* clip_out) {
+  int st = check_kinds(kind, n);
+  if (st) return st;
+  int64_t* stack = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int64_t sp = 0;
+  float universe[4] = {-INFINITY, -INFINITY, INFINITY, INFINITY};
+  st = ORC_OK;
+  for (int64_t i = 0; i < n; ++i) {
+    const float* cur = sp > 0 ? clip_out + 4 * stack[sp - 1] : universe;
+    float* oi = clip_out + 4 * i;
+    switch (kind[i]) {
+      case K_LEAF:
+      case K_OPEN_CLIP:
+        box_isect(box + 4 * i, cur, oi);
+        if (kind[i] == K_OPEN_CLIP) stack[sp++] = i;
+        break;
+      case K_OPEN_BLEND:
+        memcpy(oi, cur, 4 * sizeof(float));
+        stack[sp++] = i;
+        break;
+      case K_CLOSE:
+        if (sp == 0) { st = ORC_UNBALANCED; goto done; }
+        memcpy(oi, clip_out + 4 * stack[--sp], 4 * sizeof(float));
+        break;
     }
   }
   if (sp != 0) st = ORC_UNBALANCED;

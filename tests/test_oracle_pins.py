@@ -343,6 +343,80 @@ def test_open_positions_cap_and_bad_kind():
     assert st3 == oracle.BAD_KIND
 
 
+# --- the running clip per element (Sec. 9 stack snapshot) -------------------
+
+UNIVERSE = np.array([-np.inf, -np.inf, np.inf, np.inf], np.float32)
+
+
+def brute_clip_out(kind, box):
+    """Own box (universe for a blend) intersected with the box of every clip
+    ancestor, found by following brute-force parent links; a close takes its
+    open's value (brute-force match)."""
+    par = brute_parent(kind)
+    mat = brute_match(kind)
+    out = np.zeros((len(kind), 4), np.float32)
+    for i in range(len(kind)):
+        j = mat[i] if kind[i] == 3 else i
+        acc = UNIVERSE.copy() if kind[j] == 2 else box[j].copy()
+        a = par[j]
+        while a >= 0:
+            if kind[a] == 1:
+                acc = isect(acc, box[a])
+            a = par[a]
+        out[i] = acc
+    return out
+
+
+def test_clip_out_hand_scene():
+    """Hand-derived from the scene's definition: the blend passes the outer
+    clip on, node 4's clip is its box cut by node 0's, leaf 5's chain
+    intersection is (210,210,100,100) (empty, written raw), closes repeat
+    their opens."""
+    g = gold()["hand_scene"]
+    k = kinds_of(g["kinds"])
+    box = np.zeros((k.size, 4), np.float32)
+    for i, b in g["boxes"].items():
+        box[int(i)] = b
+    st, c = oracle.clip_out(k, box)
+    assert st == oracle.OK
+    want = [(0, 0, 100, 100), (10, 10, 50, 50), (0, 0, 100, 100), (80, 80, 100, 100),
+            (200, 200, 100, 100), (210, 210, 100, 100), (200, 200, 100, 100),
+            (0, 0, 100, 100), (0, 0, 100, 100), (5, 5, 6, 6)]
+    assert same_bits(c, np.array(want, np.float32))
+
+
+@pytest.mark.parametrize("maker,n,seed", [("rw", 300, 0), ("rw", 1200, 1), ("flat", 800, 2),
+                                          ("chain", 150, 3)])
+def test_clip_out_vs_brute(maker, n, seed):
+    if maker == "rw":
+        k, box = inputs.random_walk_scene(n, seed)
+    elif maker == "flat":
+        k, box = inputs.flat_scene(n, seed)
+    else:
+        k, box = inputs.chain_scene(n, seed)
+    st, c = oracle.clip_out(k, box)
+    assert st == oracle.OK
+    assert same_bits(c, brute_clip_out(k, box))
+
+
+def test_clip_out_agrees_with_leaf_boxes():
+    """A leaf's clip value, made canonical, is its output box of the
+    bounding-box pass; at the root the clip is the element's own box."""
+    k, box = inputs.random_walk_scene(50_000, 7)
+    st, c = oracle.clip_out(k, box)
+    st2, par, _, out = oracle.bboxes(k, box)
+    assert st == st2 == oracle.OK
+    leaves = np.nonzero(k == 0)[0]
+    canon_c = c[leaves].copy()
+    empty = (canon_c[:, 0] >= canon_c[:, 2]) | (canon_c[:, 1] >= canon_c[:, 3])
+    canon_c[empty] = EMPTY
+    assert same_bits(canon_c, out[leaves])
+    roots = np.nonzero((par == -1) & ((k == 0) | (k == 1)))[0]
+    assert same_bits(c[roots], box[roots])
+    st3, _ = oracle.clip_out(np.array([1, 0], np.uint8), np.zeros((2, 4), np.float32))
+    assert st3 == oracle.UNBALANCED
+
+
 def test_zero_area_is_empty():
     # a leaf of zero width is empty; a unit-width one is kept
     k = np.array([0, 0, 1, 0, 3], np.uint8)
