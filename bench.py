@@ -203,10 +203,38 @@ class L2Flush:
             self.buf.fill_(1.0)
 
     def describe(self, input_bytes):
-        if self.active:
-            return ("inputs (%.1f MB) fit in L2: 256 MB written before each timed step, outside "
-                    "its events" % (input_bytes / 1e6))
-        return "inputs (%.2f GB) larger than L2, no flush" % (input_bytes / 1e9)
+        return l2_description(input_bytes)
+
+
+def l2_description(input_bytes):
+    """How the timed steps of a workload with these input bytes treat L2."""
+    if input_bytes <= L2_BYTES:
+        return ("inputs (%.1f MB) fit in L2: 256 MB written before each timed step, outside "
+                "its events" % (input_bytes / 1e6))
+    return "inputs (%.2f GB) larger than L2, no flush" % (input_bytes / 1e9)
+
+
+def parallelism(world):
+    return "replicas" if world > 1 else "single"
+
+
+def scene_config(workload, n, scenes, input_bytes, world):
+    """config of a scene workload's line (both arms print the same)."""
+    return {"workload": WORKLOADS[workload], "n": int(n), "seed": 0, "scenes": int(scenes),
+            "l2": l2_description(input_bytes), "parallelism": parallelism(world)}
+
+
+def opens_config(workload, n, opens, input_bytes, world):
+    return {"workload": WORKLOADS[workload], "n": int(n), "opens": int(opens), "seed": 0,
+            "l2": l2_description(input_bytes), "parallelism": parallelism(world)}
+
+
+def tree_config(workload, n, joints, batched, input_bytes, world):
+    return {"workload": WORKLOADS[workload], "n": int(n), "joints": int(joints), "seed": 0,
+            "step": "one CUDA graph of TreeTransform forward + backward (keep_structure=True)"
+                    if batched else "one CUDA graph of tb_tree_scan (affine DOWN) + "
+                                    "tb_tree_scan_affine_backward_reuse",
+            "l2": l2_description(input_bytes), "parallelism": parallelism(world)}
 
 
 def timed_each(torch, stream, call, K, flush):
@@ -367,9 +395,7 @@ def run_opens(args, torch, world, rank, dev):
             "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "n": n, "opens": J, "seed": 0,
-                       "l2": flush.describe(kind.nbytes),
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": opens_config(args.workload, n, J, kind.nbytes, world),
             "roofline": {"bound": "hbm",
                          "kernel": "tb_open_positions (count, offsets, scatter launches)",
                          "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src,
@@ -439,7 +465,12 @@ def run_reference(args):
             "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "u8" if args.workload == "opens26" else "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "n": int(kind.size), "seed": 0},
+            "config": (opens_config(args.workload, kind.size, int(np.count_nonzero((kind == 1) | (kind == 2))),
+                                    kind.nbytes, world) if args.workload == "opens26" else
+                       scene_config(args.workload, kind.size,
+                                    1 if offsets is None else offsets.size - 1,
+                                    kind.nbytes + (0 if args.workload == "match26" else box.nbytes),
+                                    world)),
             "cpu_baseline": {"value": round(value, 4), "unit": "Gelem/s", "cores": 1,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 4), "unit": "Gelem/s", "h2d_bytes_per_step": 0,
@@ -468,8 +499,9 @@ def run_reference_tree(args, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "n": int(kind.size),
-                       "joints": int(L.shape[0]), "seed": 0},
+            "config": tree_config(args.workload, kind.size, L.shape[0],
+                                  args.workload == "skelbatch", kind.nbytes + L.nbytes + W.nbytes,
+                                  world),
             "cpu_baseline": {"value": round(value, 4), "unit": "Gelem/s", "cores": 1,
                              "kind": "oracle",
                              "sample": "full workload (%d elements) forward + backward per step, "
@@ -691,14 +723,8 @@ def run_tree(args, torch, world, rank, dev):
             "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "n": n, "joints": J, "seed": 0,
-                       "gjoint_per_s": round(world * J / (ms_step * 1e-3) / 1e9, 3),
-                       "step": "one CUDA graph of TreeTransform forward + backward "
-                               "(keep_structure=True)" if batched
-                               else "one CUDA graph of tb_tree_scan (affine DOWN) + "
-                                    "tb_tree_scan_affine_backward_reuse",
-                       "l2": flush.describe(in_bytes),
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": tree_config(args.workload, n, J, batched, in_bytes, world),
+            "gjoint_per_s": round(world * J / (ms_step * 1e-3) / 1e9, 3),
             "roofline": {"bound": "hbm",
                          "kernel": "tb_tree_scan_affine_backward_reuse (all its launches; the joint "
                                    "structure the step's forward left in the workspace)",
@@ -950,10 +976,7 @@ def run_ours(args):
             "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "n": n, "seed": 0,
-                       "scenes": S if S else 1,
-                       "l2": flush.describe(in_bytes),
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": scene_config(args.workload, n, S if S else 1, in_bytes, world),
             "roofline": {"bound": "hbm", "kernel": "k3_tile", "achieved": round(achieved, 1),
                          "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,

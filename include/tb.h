@@ -226,7 +226,7 @@ tb_status tb_set_phase_events(void* const* events, int num_events);
  * process exits), so there is no ws argument.  The caller still passes the
  * inputs and outputs (d_status included).
  *  - n may be at most TB_STATIC_WS_MAX_N; larger n returns TB_ERR_WORKSPACE
- *    without enqueuing anything.
+ *    and a negative n TB_ERR_INVALID_ARG, without enqueuing anything.
  *  - The first call on each device looks up that device's address of the
  *    array (cudaGetSymbolAddress, with that device current); make that first
  *    call before any stream capture.  It allocates nothing, now or later.

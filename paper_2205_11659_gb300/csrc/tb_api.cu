@@ -7,6 +7,7 @@
 #include <mutex>
 
 #include "tb.h"
+#include "tb_device_once.h"
 #include "tb_internal.h"
 #include "tb_scene_kernels.cuh"
 
@@ -135,41 +136,40 @@ bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p
 // (persistent launch), found once per device.
 template <bool HAS_BOX, bool BATCHED>
 cudaError_t k3_resident_blocks(int* out) {
-  constexpr int kMaxDevices = 64;
-  static int cached[kMaxDevices] = {0};
+  static std::atomic<int> cached[kOnceDevices];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < kMaxDevices && cached[dev] > 0) {
-    *out = cached[dev];
-    return cudaSuccess;
+  const bool tracked = dev >= 0 && dev < kOnceDevices;
+  if (tracked) {
+    const int c = cached[dev].load(std::memory_order_relaxed);
+    if (c > 0) {
+      *out = c;
+      return cudaSuccess;
+    }
   }
-  int sms = 0, per_sm = 0;
-  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
+  const int sms = current_device_sms();
+  if (sms <= 0) return cudaErrorInvalidDevice;
+  int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_tile<HAS_BOX, BATCHED>, NT,
                                                     k3_smem_bytes(HAS_BOX));
   if (e != cudaSuccess) return e;
   const int nb = sms * (per_sm > 0 ? per_sm : 1);
-  if (dev < kMaxDevices) cached[dev] = nb;
+  if (tracked) cached[dev].store(nb, std::memory_order_relaxed);
   *out = nb;
   return cudaSuccess;
 }
 
 template <bool HAS_BOX, bool BATCHED>
 cudaError_t launch_k3(const K3Args& a, int T, cudaStream_t s) {
-  static bool attr_set = false;
   constexpr int smem = k3_smem_bytes(HAS_BOX);
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k3_tile<HAS_BOX, BATCHED>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_set{0};
+  cudaError_t e = smem_limit_once(attr_set, k3_tile<HAS_BOX, BATCHED>, smem);
+  if (e != cudaSuccess) return e;
   int grid = T;
   if (PERSIST) {
     int nb = 0;
-    cudaError_t e = k3_resident_blocks<HAS_BOX, BATCHED>(&nb);
+    e = k3_resident_blocks<HAS_BOX, BATCHED>(&nb);
     if (e != cudaSuccess) return e;
     grid = T < nb ? T : nb;
   }
@@ -357,7 +357,8 @@ extern "C" {
 
 tb_status tb_bboxes_static_ws(const uint8_t* kind, const float* box, int64_t n, int32_t* parent,
                               int32_t* match, float* box_out, int32_t* d_status, void* stream) {
-  if (n < 0 || n > TB_STATIC_WS_MAX_N) return TB_ERR_WORKSPACE;
+  if (n < 0) return TB_ERR_INVALID_ARG;
+  if (n > TB_STATIC_WS_MAX_N) return TB_ERR_WORKSPACE;
   const Layout L = scene_layout(n, true);
   if (L.total > kStaticWsBytes) return TB_ERR_WORKSPACE;
   void* ws = nullptr;

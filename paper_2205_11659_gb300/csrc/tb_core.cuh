@@ -364,8 +364,12 @@ struct SegState {
 
 // Starting from the owner S.u of depth S.dtop, follow the ps links (each
 // tile's ps is the owner of the depth just below its own slice) down to
-// depth S.dbot, recording at most SEG_CAP segments.
-__device__ __forceinline__ void seg_collect(SegState& S, const int* t_ps, const int* t_lo) {
+// depth S.dbot, recording at most SEG_CAP segments.  Every segment lowers
+// S.dtop by at least one, so the batches a caller collects until S.done end;
+// a segment that would not (only a workspace inconsistent with itself can
+// produce one) ends the walk at once and records ST_BOUNDS in debug builds.
+__device__ __forceinline__ void seg_collect(SegState& S, const int* t_ps, const int* t_lo,
+                                            const int* status) {
   int n = 0;
   while (n < SEG_CAP && S.dtop >= S.dbot) {
     if (S.dtop < 0 || S.u < 0) {
@@ -379,6 +383,11 @@ __device__ __forceinline__ void seg_collect(SegState& S, const int* t_ps, const 
     }
     int lo_u = t_lo[S.u];
     int lo_s = lo_u > S.dbot ? lo_u : S.dbot;
+    if (lo_s > S.dtop) {
+      if (TB_DEBUG) atomic_cas_i32(const_cast<int*>(status), ST_OK, ST_BOUNDS);
+      S.dtop = S.dbot - 1;
+      break;
+    }
     S.seg_u[n] = S.u;
     S.seg_ulo[n] = lo_u;
     S.seg_lo[n] = lo_s;

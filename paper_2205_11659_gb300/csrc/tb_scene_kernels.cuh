@@ -411,9 +411,10 @@ __device__ __forceinline__ void fill_ctx_overflow(SegState& S, const SceneWs& ws
   }
   __syncthreads();
   for (;;) {
-    if (tid == 0) seg_collect(S, ws.t_ps, ws.t_lo);
+    if (tid == 0) seg_collect(S, ws.t_ps, ws.t_lo, ws.status);
     __syncthreads();
-    const int hi = S.seg_hi[0], lo = S.seg_lo[S.n - 1];
+    const int ns = S.n;
+    const int hi = ns > 0 ? S.seg_hi[0] : 0, lo = ns > 0 ? S.seg_lo[ns - 1] : 1;
     for (int m = dstart - 1 - hi + tid; m <= dstart - 1 - lo; m += NT) {
       const int d = dstart - 1 - m;
       const int s = seg_find(S, d);

@@ -5,11 +5,11 @@
 // and TB_WITHHELD_TILE() (the look-back test hook) before including it.
 //
 // Everything here has internal linkage (an unnamed namespace).  The launch
-// functions remember in function-local statics that a kernel's shared-memory
-// limit was raised; with external linkage those statics become one object
-// per process (GNU unique symbols), so a second shared library built from
-// this header would skip raising the limit for its own copy of a kernel and
-// its launch would fail.
+// functions remember in function-local statics, per device, that a kernel's
+// shared-memory limit was raised (tb_device_once.h); with external linkage
+// those statics become one object per process (GNU unique symbols), so a
+// second shared library built from this header would skip raising the limit
+// for its own copy of a kernel and its launch would fail.
 #ifndef TB_TREE_LAUNCH_CUH
 #define TB_TREE_LAUNCH_CUH
 
@@ -19,6 +19,7 @@
 #include <cstdint>
 
 #include "tb.h"
+#include "tb_device_once.h"
 #include "tb_tree_kernels.cuh"
 
 #ifndef TB_PHASE_MARK
@@ -137,18 +138,17 @@ inline TreeWs tree_ws(const TreeLayout& L, void* ws, int64_t n, int J) {
 
 inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
+// Blocks for a grid-stride kernel over `items`: one per `per_block` items,
+// at most 16 per SM of the current device.
 inline int grid_for(int items, int per_block) {
   const int g = (items + per_block - 1) / per_block;
-  return g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g);
+  const int sms = current_device_sms();
+  const int cap = (sms > 0 ? sms : 1) * 16;
+  return g < 1 ? 1 : (g > cap ? cap : g);
 }
 
 // Largest dynamic shared memory of one block on this architecture (227 KB).
 constexpr size_t kMaxBlockSmem = 227 * 1024;
-
-template <class K>
-cudaError_t allow_smem(K kernel, size_t bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
 
 // Status word, joint depths with the stream checks, tile minima.
 inline tb_status prelude(const uint8_t* kind, int64_t n, int J, const TreeLayout& L, void* ws,
@@ -187,11 +187,9 @@ tb_status launch_down_tiles(const TreeWs& w, const void* in, void* out, int32_t*
   TB_PHASE_MARK(s);
   const size_t tsm = down_tiles_smem<M>(w.TJ);
   if (tsm <= kMaxBlockSmem) {
-    static bool tiles_attr = false;
-    if (!tiles_attr) {
-      if (allow_smem(k_down_tiles<M, true>, kMaxBlockSmem) != cudaSuccess) return TB_ERR_CUDA;
-      tiles_attr = true;
-    }
+    static std::atomic<unsigned long long> tiles_attr{0};
+    if (smem_limit_once(tiles_attr, k_down_tiles<M, true>, kMaxBlockSmem) != cudaSuccess)
+      return TB_ERR_CUDA;
     k_down_tiles<M, true><<<1, 1024, tsm, s>>>(w, d_status);
   } else {
     k_down_tiles<M, false><<<1, 1024, 0, s>>>(w, d_status);
@@ -199,11 +197,8 @@ tb_status launch_down_tiles(const TreeWs& w, const void* in, void* out, int32_t*
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   TB_PHASE_MARK(s);
   constexpr size_t smem = down_tile_smem<M>();
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (allow_smem(k_down_tile<M>, smem) != cudaSuccess) return TB_ERR_CUDA;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_set{0};
+  if (smem_limit_once(attr_set, k_down_tile<M>, smem) != cudaSuccess) return TB_ERR_CUDA;
   k_down_tile<M><<<w.TJ, TNT, smem, s>>>(w, in, out);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   return TB_OK;
@@ -220,11 +215,8 @@ template <class M, class Values, class Finish>
 tb_status launch_up(const TreeWs& w, Values values, void* out, Finish fin, cudaStream_t s) {
   TB_PHASE_MARK(s);
   constexpr size_t smem = up_tile_smem<M>();
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (allow_smem(k_up_tile<M, Values, Finish>, smem) != cudaSuccess) return TB_ERR_CUDA;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_set{0};
+  if (smem_limit_once(attr_set, k_up_tile<M, Values, Finish>, smem) != cudaSuccess) return TB_ERR_CUDA;
   k_up_tile<M, Values, Finish><<<w.TJ, TNT, smem, s>>>(w, values, out, fin);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   TB_PHASE_MARK(s);

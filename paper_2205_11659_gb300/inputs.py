@@ -123,6 +123,20 @@ def scene_boxes(kinds, seed, center_lo=0.0, center_hi=4096.0, leaf_wh=(1.0, 256.
     return out
 
 
+def grid_boxes(kinds, seed, cells=6, cell=8.0):
+    """float32 boxes on a coarse integer grid, for edge cases of the empty-box
+    rule: corners at multiples of ``cell`` in [0, cells * cell], so leaves of
+    zero width or height and clip edges that exactly touch a leaf's edge are
+    common; zeros for blend and close slots."""
+    rng = _rng(seed, 5)
+    n = kinds.size
+    a = rng.integers(0, cells + 1, (n, 2)) * cell
+    w = rng.integers(0, 3, (n, 2)) * cell          # widths/heights 0, cell, 2 cell
+    blk = np.concatenate([a, a + w], axis=1)
+    keep = ((kinds == LEAF) | (kinds == OPEN_CLIP))[:, None]
+    return np.where(keep, blk, 0.0).astype(np.float32)
+
+
 def random_walk_scene(n, seed):
     """(kinds, boxes) of the random-walk workload."""
     k = random_walk_kinds(n, seed)

@@ -168,3 +168,41 @@ def test_tuned_shape_is_a_candidate():
     from paper_2205_11659_gb300 import _build, autotune
     assert _build.tuned_shape() + (_build.tuned_persistent(),) in autotune.CANDIDATES
     assert (256, 16, False) in autotune.CANDIDATES
+
+
+def test_static_scratch_argument_errors(lib):
+    # tb_bboxes_static_ws: host checks come before any CUDA call.
+    from paper_2205_11659_gb300 import binding as b
+    p = ctypes.c_void_p
+    fake = 1 << 20
+    assert lib.tb_bboxes_static_ws(p(fake), p(fake), -1, None, None, p(fake), p(fake), None) \
+        == b.TB_ERR_INVALID_ARG
+    assert lib.tb_bboxes_static_ws(p(fake), p(fake), b.TB_STATIC_WS_MAX_N + 1, None, None, p(fake),
+                                   p(fake), None) == b.TB_ERR_WORKSPACE
+
+
+def _host_sources():
+    d = os.path.join(ROOT, "paper_2205_11659_gb300", "csrc")
+    out = {}
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            src = open(os.path.join(d, f)).read()
+            out[f] = re.sub(r"//[^\n]*", "", src)
+    return out
+
+
+def test_launch_state_is_per_device():
+    """A kernel attribute (the raised shared-memory limit) and the SM count
+    belong to one device.  Launch code keeps them per device ordinal in
+    atomic masks and arrays (tb_device_once.h), never in a process-wide
+    flag, and takes the SM count from the device, not from a literal."""
+    srcs = _host_sources()
+    for f, src in srcs.items():
+        assert not re.search(r"\bstatic\s+bool\b", src), f
+        assert not re.search(r"\bstatic\s+int\s+\w+\s*\[", src), f  # plain per-process caches
+        assert not re.search(r"\b152\b", src), f
+    # every raised shared-memory limit goes through the per-device helper
+    raw = [f for f, src in srcs.items()
+           if "cudaFuncAttributeMaxDynamicSharedMemorySize" in src and f != "tb_device_once.h"]
+    assert not raw, raw
+    assert "smem_limit_once" in srcs["tb_api.cu"] and "smem_limit_once" in srcs["tb_tree_launch.cuh"]

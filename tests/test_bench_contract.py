@@ -31,6 +31,11 @@ def test_reference_line(workload):
         assert key in d, key
     assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
     assert d["config"]["workload"]
+    # the same config keys as the GPU arm's line (built by the same helpers)
+    extra = {"rw16": ("scenes",), "skel20s": ("joints", "step")}[workload]
+    for key in ("n", "seed", "l2", "parallelism") + extra:
+        assert key in d["config"], key
+    assert d["config"]["parallelism"] == "single"
     cpu = d["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == d["value"]
     e2e = d["e2e"]

@@ -266,3 +266,59 @@ def test_withhold_hook_leaves_scene_passes_alone():
     st, op, om, ob = oracle.bboxes(k, b)
     assert np.array_equal(p.cpu().numpy(), op) and np.array_equal(m.cpu().numpy(), om)
     assert same_bits(o.cpu().numpy(), ob)
+
+
+# A clip node A=(0,0,16,16) holding a clip node B=(16,0,32,16) whose raw
+# intersection with A has zero width, two leaves under B (one live box, one of
+# zero width), then under A a leaf touching A's right edge and a live leaf.
+# Every leaf under B and the touching leaf are empty (x0 >= x1 is empty), so
+# node B is empty and node A is the live leaf's box (2,2,6,6).
+_ZERO_KINDS = np.array([1, 1, 0, 0, 3, 0, 0, 3], np.uint8)
+_ZERO_BOXES = np.array([[0, 0, 16, 16], [16, 0, 32, 16], [4, 4, 20, 12], [8, 8, 8, 12],
+                        [0, 0, 0, 0], [16, 2, 24, 10], [2, 2, 6, 6], [0, 0, 0, 0]], np.float32)
+
+
+def _zero_area_scene():
+    """Grid-box random walks with the pattern above placed across a tile
+    boundary (elements 4094..4101), inside a chunk and across a chunk
+    boundary."""
+    starts = [TILE - 2, 2 * TILE + 16 * 7 + 5, 3 * TILE + 16 * 9 - 1]
+    ks, bs, pos = [], [], 0
+    for i, s in enumerate(starts + [None]):
+        length = 3000 if s is None else s - pos
+        k = inputs.random_walk_kinds(length, 40 + i)
+        ks.append(k)
+        bs.append(inputs.grid_boxes(k, 50 + i))
+        pos += length
+        if s is not None:
+            ks.append(_ZERO_KINDS)
+            bs.append(_ZERO_BOXES)
+            pos += _ZERO_KINDS.size
+    return np.concatenate(ks), np.concatenate(bs)
+
+
+def _touching_leaves(kind, box):
+    """Leaves whose raw clipped box has zero width or height exactly."""
+    st, raw = oracle.clip_out(kind, box)
+    assert st == oracle.OK
+    leaf = kind == 0
+    zero = (raw[:, 0] == raw[:, 2]) | (raw[:, 1] == raw[:, 3])
+    return int(np.count_nonzero(leaf & zero))
+
+
+@pytest.mark.parametrize("n", [0, 3 * TILE + 5, 50_000])
+def test_zero_area_rule(n):
+    """Empty is x0 >= x1 or y0 >= y1 (touching edges and zero-width leaves are
+    empty), applied to leaves before any union; bit for bit vs the oracle."""
+    if n == 0:
+        k, b = _zero_area_scene()
+        st, _, _, ob = oracle.bboxes(k, b)
+        empty = np.array([np.inf, np.inf, -np.inf, -np.inf], np.float32)
+        for s in (TILE - 2, 2 * TILE + 16 * 7 + 5, 3 * TILE + 16 * 9 - 1):
+            assert all(same_bits(ob[s + j], empty) for j in (1, 2, 3, 4, 5))
+            assert same_bits(ob[s], np.array([2, 2, 6, 6], np.float32))
+    else:
+        k = inputs.random_walk_kinds(n, 60 + n)
+        b = inputs.grid_boxes(k, 61 + n)
+    assert _touching_leaves(k, b) > 0   # the case separates >= from >
+    assert_bboxes_equal(k, b)

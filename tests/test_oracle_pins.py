@@ -661,3 +661,28 @@ def test_affine_backward_vs_finite_differences():
         fd[idx] = (oracle.affine_loss(k, Lp, W)[1] - oracle.affine_loss(k, Lm, W)[1]) / (2 * h)
     err = np.abs(fd - g).max() / np.abs(g).max()
     assert err < 1e-7, err
+
+
+def test_affine_up_stream_order_with_rotations():
+    """UP folds a joint's own value first, then its descendants' in stream
+    order (Sec. 6.2's contiguous slice; the order matters for a monoid that
+    does not commute, Sec. 13).  With random rotations the 4x4 products do
+    not commute, so a swapped composition fails here."""
+    for seed, (k, L) in enumerate([inputs.skeleton(120, 5, max_depth=10)[:2],
+                                   inputs.skeleton(90, 6, max_depth=40)[:2]]):
+        L = L.astype(np.float64)
+        st, up = oracle.affine_up(k, L)
+        assert st == oracle.OK
+        opens, mat, par, rank = _opens_ranges(k)
+        swapped_differs = False
+        for o in opens:
+            sub = [rank[int(j)] for j in opens if o <= j < mat[o]]  # stream order, o first
+            acc = np.eye(4)
+            rev = np.eye(4)
+            for r in sub:
+                acc = acc @ _hom(L[r])
+                rev = _hom(L[r]) @ rev
+            assert np.allclose(up[rank[int(o)]], acc[:3], rtol=1e-12, atol=1e-12)
+            if len(sub) > 1 and not np.allclose(acc[:3], rev[:3], rtol=1e-6, atol=1e-6):
+                swapped_differs = True
+        assert swapped_differs  # the pin separates the two orders on these inputs

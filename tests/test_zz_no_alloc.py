@@ -5,8 +5,9 @@ per-frame path with a fixed memory budget, a plug-in whose host owns all
 device memory); this entry point takes no workspace and uses the library's
 own fixed scratch array instead.  Here it is called through the C ABI and
 checked, bit for bit (the tolerance of every other box test), against the
-ordinary workspace form tb_bboxes on the same inputs, for two calls in a row:
-the second call runs on the scratch the first one left behind.
+ordinary workspace form tb_bboxes on the same inputs, and directly against the
+CPU oracle, for two calls in a row: the second call runs on the scratch the
+first one left behind.
 
 The file name sorts last so that a run stopping at the first failure has
 already run every other test.
@@ -15,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2205_11659_gb300 import binding, inputs
 
 pytestmark = pytest.mark.gpu
@@ -57,6 +59,10 @@ def test_static_scratch_matches_workspace_form_twice():
         assert np.array_equal(p1, p2)
         assert np.array_equal(m1, m2)
         assert np.array_equal(b1.view(np.uint32), b2.view(np.uint32))
+        st, op, om, ob = oracle.bboxes(kind_np, box_np)
+        assert st == oracle.OK
+        assert np.array_equal(p1, op) and np.array_equal(m1, om)
+        assert np.array_equal(b1.view(np.uint32), ob.view(np.uint32))
 
 
 def test_static_scratch_rejects_sizes_beyond_its_limit():
@@ -65,3 +71,5 @@ def test_static_scratch_rejects_sizes_beyond_its_limit():
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     rc = binding.tb_bboxes_static_ws(k, b, binding.TB_STATIC_WS_MAX_N + 1, None, None, b, st)
     assert rc == binding.TB_ERR_WORKSPACE
+    rc = binding.tb_bboxes_static_ws(k, b, -1, None, None, b, st)
+    assert rc == binding.TB_ERR_INVALID_ARG
