@@ -513,8 +513,11 @@ def run_reference_tree(args, world):
 
 
 def run_tree(args, torch, world, rank, dev):
-    """Skeleton workloads: forward (affine DOWN scan) + adjoint per step."""
+    """Skeleton workloads: forward (affine DOWN scan) + adjoint per step.
+    Returns rank 0's line (None on the other ranks); args.light skips the
+    end-to-end leg and the CPU baseline."""
     from paper_2205_11659_gb300 import binding
+    light = getattr(args, "light", False)
     kind, L, W, eoff, joff = make_workload(args.workload, seed=0)
     n, J = int(kind.size), int(L.shape[0])
     k_d = torch.from_numpy(kind).to(dev)
@@ -696,23 +699,25 @@ def run_tree(args, torch, world, rank, dev):
     # end to end through the public API with pinned host buffers: K jobs
     # streamed through TreePipeline (copies of consecutive jobs overlap the
     # forward + backward; the pipeline's fill and drain are timed)
-    kind_h = torch.from_numpy(kind).pin_memory()
-    L_h = torch.from_numpy(L).pin_memory()
-    W_h = torch.from_numpy(W).pin_memory()
-    out_h = (torch.empty_like(L_h).pin_memory(), torch.empty_like(L_h).pin_memory())
-    e2e_steps = max(3, K)
-    tpipe = binding.TreePipeline(n, dev)
-    tpipe.run([kind_h], [L_h], [W_h], [out_h])
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    tpipe.run([kind_h] * e2e_steps, [L_h] * e2e_steps, [W_h] * e2e_steps, [out_h] * e2e_steps)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    del tpipe
+    e2e_steps, e2e_s = 0, float("nan")
+    if not light:
+        kind_h = torch.from_numpy(kind).pin_memory()
+        L_h = torch.from_numpy(L).pin_memory()
+        W_h = torch.from_numpy(W).pin_memory()
+        out_h = (torch.empty_like(L_h).pin_memory(), torch.empty_like(L_h).pin_memory())
+        e2e_steps = max(3, K)
+        tpipe = binding.TreePipeline(n, dev)
+        tpipe.run([kind_h], [L_h], [W_h], [out_h])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tpipe.run([kind_h] * e2e_steps, [L_h] * e2e_steps, [W_h] * e2e_steps, [out_h] * e2e_steps)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        del tpipe
 
     peak, peak_src = measured_peaks()
     bwd_alg = BWD_BYTES_PER_JOINT * J
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not light:
         v, runs, el = time_oracle_tree(kind, L, W)
         cpu = {"value": round(v, 4), "unit": "Gelem/s", "cores": 1, "kind": "oracle",
                "sample": "the full workload (%d elements) forward + backward x %d runs, %.1f s, "
@@ -744,17 +749,18 @@ def run_tree(args, torch, world, rank, dev):
                           "backward": {k: round(v, 4) for k, v in bph.items()}},
             "per_scene": per_scene,
             "cpu_baseline": cpu,
-            "e2e": {"value": round(world * n / e2e_s / 1e9, 3), "unit": "Gelem/s",
-                    "h2d_bytes_per_step": int(kind.nbytes + L.nbytes + W.nbytes),
-                    "d2h_bytes_per_step": int(2 * L.nbytes), "jobs": e2e_steps,
-                    "how": "TreePipeline: copies of consecutive jobs overlap the forward + "
-                           "structure-reusing backward; fill and drain timed"},
+            "e2e": None if light else {
+                "value": round(world * n / e2e_s / 1e9, 3), "unit": "Gelem/s",
+                "h2d_bytes_per_step": int(kind.nbytes + L.nbytes + W.nbytes),
+                "d2h_bytes_per_step": int(2 * L.nbytes), "jobs": e2e_steps,
+                "how": "TreePipeline: copies of consecutive jobs overlap the forward + "
+                       "structure-reusing backward; fill and drain timed"},
             "gpu_launches": (6 + 6) * K,
             "clocks": clk,
             "kernel_hash": kernel_hash(TREE_SOURCES),
         }
-        print(json.dumps(line), flush=True)
-    return 0
+        return line
+    return None
 
 
 def run_ours(args):
@@ -767,16 +773,69 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    from paper_2205_11659_gb300 import _build, binding
+    from paper_2205_11659_gb300 import _build
     _build.build()
-    if args.workload in TREE_WORKLOADS or args.workload == "opens26":
-        run = run_tree if args.workload in TREE_WORKLOADS else run_opens
-        rc = run(args, torch, world, rank, dev)
+    if args.workload == "opens26":
+        rc = run_opens(args, torch, world, rank, dev)
         if world > 1:
             torch.distributed.barrier()
             torch.distributed.destroy_process_group()
         return rc
+    line = (run_tree if args.workload in TREE_WORKLOADS else measure_scene)(
+        args, torch, world, rank, dev)
+    if line is not None and args.workload == "rw26" and world == 1 and not args.no_sub:
+        line["sub"] = sub_records(args, torch, world, rank, dev)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
 
+
+SUB_WORKLOADS = ("chain24", "flat24", "batched", "skel20", "skelbatch")
+
+
+def sub_records(args, torch, world, rank, dev):
+    """The other configurations of the benchmark, each measured the same way
+    as its own line (device-timed steps with inputs resident in HBM, L2
+    flushed when they would fit in it, clocks sampled) with fewer steps and
+    without the end-to-end leg and CPU baseline; summarised per workload."""
+    out = {}
+    for wl in SUB_WORKLOADS:
+        sub = argparse.Namespace(**vars(args))
+        sub.workload, sub.steps, sub.warmup, sub.light = wl, 10, 3, True
+        sub.no_cpu_baseline = True
+        t0 = time.perf_counter()
+        ln = (run_tree if wl in TREE_WORKLOADS else measure_scene)(sub, torch, world, rank, dev)
+        torch.cuda.empty_cache()
+        if ln is None:
+            continue
+        rec = {"workload": WORKLOADS[wl], "n": ln["config"]["n"], "steps": 10,
+               "ms_per_step": ln["ms_per_step"], "value": ln["value"], "unit": ln["unit"],
+               "roofline": {k: ln["roofline"][k] for k in ("kernel", "achieved", "frac")},
+               "step_roofline_frac": ln["step_roofline_frac"], "l2": ln["config"]["l2"],
+               "clocks": ln["clocks"], "wall_s": round(time.perf_counter() - t0, 1)}
+        if wl in TREE_WORKLOADS:
+            rec.update({"joints": ln["config"]["joints"], "gjoint_per_s": ln["gjoint_per_s"],
+                        "forward_ms": ln["forward_ms"], "backward_reuse_ms": ln["backward_reuse_ms"],
+                        "forward_roofline_frac": ln["forward_roofline_frac"],
+                        "backward_roofline_frac": ln["roofline"]["frac"],
+                        "standalone_backward_roofline_frac": ln["standalone_backward_roofline_frac"]})
+        else:
+            rec.update({"phases_ms": ln["phases_ms"], "graph_value": ln["graph"]["value"]})
+        if ln.get("per_scene"):
+            rec["per_scene"] = ln["per_scene"]
+        out[wl] = rec
+    return out
+
+
+def measure_scene(args, torch, world, rank, dev):
+    """Scene workloads: one full bounding-box (or matching) pass per step.
+    Returns rank 0's line (None on the other ranks); args.light skips the
+    end-to-end leg and the CPU baseline."""
+    from paper_2205_11659_gb300 import binding
+    light = getattr(args, "light", False)
     kind, box, offsets = make_workload(args.workload, seed=0)
     n = int(kind.size)
     k_d = torch.from_numpy(kind).to(dev)
@@ -922,6 +981,51 @@ def run_ours(args):
         del parent2, match2, box2, calls, g
 
     # ---- end to end through the public API with host buffers
+    e2e = None
+    if not light:
+        e2e = scene_e2e(torch, binding, dev, kind, box, offsets, match_only, n, K, world)
+
+    peak, peak_src = measured_peaks()
+    k3_ms = phases["k3_tile"]
+    achieved = bytes_per_elem * n / (k3_ms * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC.get(kernel_hash(), {}).get(args.workload)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not light:
+        v, runs, el = time_oracle(kind, box, offsets, match_only)
+        cpu = {"value": round(v, 4), "unit": "Gelem/s", "cores": 1, "kind": "oracle",
+               "sample": "the full workload (%d elements) x %d runs, %.1f s, single thread"
+                         % (n, runs, el)}
+
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": round(value, 3), "unit": "Gelem/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": scene_config(args.workload, n, S if S else 1, in_bytes, world),
+        "roofline": {"bound": "hbm", "kernel": "k3_tile", "achieved": round(achieved, 1),
+                     "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "algorithmic_bytes_per_launch": bytes_per_elem * n},
+        "step_roofline_frac": round(bytes_per_elem * n / (ms_step * 1e-3) / 1e9 / peak, 4),
+        "phases_ms": {k: round(v, 4) for k, v in phases.items()},
+        "graph": {"ms_per_step": round(graph_step_ms, 4),
+                  "value": round(world * n / (graph_step_ms * 1e-3) / 1e9, 3),
+                  "unit": "Gelem/s", "note": "the same step replayed as one CUDA graph"},
+        "per_scene": per_scene,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": (6 if match_only else 8) * K,
+        "clocks": clk,
+        "kernel_hash": kernel_hash(),
+    }
+
+
+def scene_e2e(torch, binding, dev, kind, box, offsets, match_only, n, K, world):
+    """The scene metric end to end through the public API: inputs copied from
+    pinned host memory and outputs copied back inside the timed region."""
     kind_h = torch.from_numpy(kind).pin_memory()
     box_h = torch.from_numpy(box).pin_memory()
     off_h = torch.from_numpy(offsets) if offsets is not None else None
@@ -957,52 +1061,12 @@ def run_ours(args):
         e2e_s = (time.perf_counter() - t0) / e2e_steps
     h2d = kind.nbytes + (0 if match_only else box.nbytes) + (offsets.nbytes if offsets is not None else 0)
     d2h = 4 * n + 4 * n + (0 if match_only else 16 * n)
-
-    peak, peak_src = measured_peaks()
-    k3_ms = phases["k3_tile"]
-    achieved = bytes_per_elem * n / (k3_ms * 1e-3) / 1e9
-    traffic = NCU_TRAFFIC.get(kernel_hash(), {}).get(args.workload)
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, runs, el = time_oracle(kind, box, offsets, match_only)
-        cpu = {"value": round(v, 4), "unit": "Gelem/s", "cores": 1, "kind": "oracle",
-               "sample": "the full workload (%d elements) x %d runs, %.1f s, single thread"
-                         % (n, runs, el)}
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": round(value, 3), "unit": "Gelem/s", "n_gpus": world,
-            "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": scene_config(args.workload, n, S if S else 1, in_bytes, world),
-            "roofline": {"bound": "hbm", "kernel": "k3_tile", "achieved": round(achieved, 1),
-                         "peak": peak, "peak_source": peak_src, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "algorithmic_bytes_per_launch": bytes_per_elem * n},
-            "step_roofline_frac": round(bytes_per_elem * n / (ms_step * 1e-3) / 1e9 / peak, 4),
-            "phases_ms": {k: round(v, 4) for k, v in phases.items()},
-            "graph": {"ms_per_step": round(graph_step_ms, 4),
-                      "value": round(world * n / (graph_step_ms * 1e-3) / 1e9, 3),
-                      "unit": "Gelem/s", "note": "the same step replayed as one CUDA graph"},
-            "per_scene": per_scene,
-            "cpu_baseline": cpu,
-            "e2e": {"value": round(world * n / e2e_s / 1e9, 3), "unit": "Gelem/s",
-                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                    "scenes": e2e_steps,
-                    "how": ("HostPipeline: copies of consecutive scenes overlap the pass; fill and "
-                            "drain timed" if offsets is None else
-                            "bboxes_batched_host: copies in, the batched pass, copies out")},
-            "gpu_launches": (6 if match_only else 8) * K,
-            "clocks": clk,
-            "kernel_hash": kernel_hash(),
-        }
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.barrier()
-        torch.distributed.destroy_process_group()
-    return 0
+    return {"value": round(world * n / e2e_s / 1e9, 3), "unit": "Gelem/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "scenes": e2e_steps,
+            "how": ("HostPipeline: copies of consecutive scenes overlap the pass; fill and "
+                    "drain timed" if offsets is None else
+                    "bboxes_batched_host: copies in, the batched pass, copies out")}
 
 
 def main():
@@ -1013,6 +1077,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rw26", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="rw26 only: skip the sub-records of the other configurations")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

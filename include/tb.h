@@ -126,6 +126,26 @@ tb_status tb_bboxes_batched(const uint8_t* kind, const float* box,
                             float* box_out, void* ws, size_t ws_bytes,
                             int32_t* d_status, void* stream);
 
+/* tb_bboxes (offsets == NULL) or tb_bboxes_batched (offsets and num_scenes
+ * as there) that also writes, per element, the running clip intersection of
+ * the stack snapshot (Sec. 9: each entry of the snapshot is its element's box
+ * intersected with the boxes of all its clip ancestors):
+ *   LEAF, OPEN_CLIP:  own box intersected with the clip in force (the
+ *                     intersection of all its OPEN_CLIP ancestors' boxes);
+ *   OPEN_BLEND:       the clip in force (its own box is ignored);
+ *   CLOSE:            the value of the open it closes.
+ * The clip in force at a root is the universe (-inf, -inf, +inf, +inf).  The
+ * raw intersection is written (x0 >= x1 or y0 >= y1 when empty, not the
+ * canonical empty box): it is what flows down the clip chain.  clip_out holds
+ * n float4 (16-byte aligned, must not alias other buffers); it may not be
+ * NULL when n > 0 (TB_ERR_INVALID_ARG).  Everything else, including the
+ * workspace (tb_workspace_size(TB_OP_BBOXES, n)), is as in tb_bboxes. */
+tb_status tb_bboxes_clip(const uint8_t* kind, const float* box,
+                         const int64_t* offsets, int64_t num_scenes, int64_t n,
+                         int32_t* parent, int32_t* match, float* box_out,
+                         float* clip_out, void* ws, size_t ws_bytes,
+                         int32_t* d_status, void* stream);
+
 /* Stream compaction of the opens (Sec. 1.1: a renderer keeps just the clip
  * and blend nodes this way).  pos[r] = the stream index of the r-th open
  * (OPEN_CLIP or OPEN_BLEND) in stream order, which is the element of joint

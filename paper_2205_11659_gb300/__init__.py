@@ -7,6 +7,7 @@ seeded synthetic scenes and skeletons.
 """
 from .binding import (  # noqa: F401
     HostPipeline, TBError, TreePipeline, TreeTransform, affine_backward, bboxes, bboxes_batched,
+    bboxes_clip, tb_bboxes_clip,
     match_parens, open_positions, tb_bboxes, tb_bboxes_batched, tb_match_parens, tb_open_positions,
     tb_set_phase_events, tb_tree_scan,
     tb_tree_scan_affine_backward, tb_tree_scan_affine_backward_reuse, tb_version,

@@ -87,9 +87,11 @@ def lib():
             L.tb_tree_scan_affine_backward.argtypes = [p, i64, i64, p, p, p, p, sz, p, p]
             L.tb_tree_scan_affine_backward_reuse.argtypes = [p, i64, i64, p, p, p, p, sz, p, p]
             L.tb_open_positions.argtypes = [p, i64, p, i64, p, p, sz, p, p]
+            L.tb_bboxes_clip.argtypes = [p, p, p, i64, i64, p, p, p, p, p, sz, p, p]
             for f in (L.tb_match_parens, L.tb_bboxes, L.tb_bboxes_batched, L.tb_set_phase_events,
                       L.tb_bboxes_static_ws, L.tb_tree_scan, L.tb_tree_scan_affine_backward,
-                      L.tb_tree_scan_affine_backward_reuse, L.tb_open_positions):
+                      L.tb_tree_scan_affine_backward_reuse, L.tb_open_positions,
+                      L.tb_bboxes_clip):
                 f.restype = i32
             L.tb_version.argtypes = []
             L.tb_version.restype = ctypes.c_char_p
@@ -148,6 +150,13 @@ def tb_bboxes_batched(kind, box, offsets, num_scenes, n_total, parent, match, bo
     return lib().tb_bboxes_batched(_ptr(kind), _ptr(box), _ptr(offsets), int(num_scenes),
                                    int(n_total), _ptr(parent), _ptr(match), _ptr(box_out),
                                    _ptr(ws), int(ws_bytes), _ptr(d_status), _stream(stream))
+
+
+def tb_bboxes_clip(kind, box, offsets, num_scenes, n, parent, match, box_out, clip_out, ws,
+                   ws_bytes, d_status, stream=None):
+    return lib().tb_bboxes_clip(_ptr(kind), _ptr(box), _ptr(offsets), int(num_scenes), int(n),
+                                _ptr(parent), _ptr(match), _ptr(box_out), _ptr(clip_out),
+                                _ptr(ws), int(ws_bytes), _ptr(d_status), _stream(stream))
 
 
 def tb_bboxes_static_ws(kind, box, n, parent, match, box_out, d_status, stream=None):
@@ -310,6 +319,34 @@ def bboxes(kind, box, want_indices=True, check=True, out=None):
     if host:
         return tuple(None if t is None else t.cpu() for t in (parent, match, box_out))
     return parent, match, box_out
+
+
+def bboxes_clip(kind, box, offsets=None, want_indices=True, check=True):
+    """(parent, match, box_out, clip_out): bboxes (offsets None) or
+    bboxes_batched, plus per element the running clip intersection (Sec. 9)."""
+    host = not kind.is_cuda
+    dev = torch.device("cuda", torch.cuda.current_device()) if host else kind.device
+    k = _on_device(kind, torch.uint8, "kind", dev)
+    b = _on_device(box, torch.float32, "box", dev).reshape(-1, 4)
+    off = None if offsets is None else _on_device(offsets, torch.int64, "offsets", dev)
+    n = k.numel()
+    if b.shape[0] != n:
+        raise ValueError("box must have shape (n, 4)")
+    S = 0 if off is None else off.numel() - 1
+    parent = torch.empty(n, dtype=torch.int32, device=dev) if want_indices else None
+    match = torch.empty(n, dtype=torch.int32, device=dev) if want_indices else None
+    box_out = torch.empty(n, 4, dtype=torch.float32, device=dev)
+    clip_out = torch.empty(n, 4, dtype=torch.float32, device=dev)
+    ws = workspace(dev)
+    nb = tb_workspace_size(TB_OP_BBOXES, n)
+    _check(tb_bboxes_clip(k, b, off, S, n, parent, match, box_out, clip_out, ws.get(nb), nb,
+                          ws.status), "tb_bboxes_clip")
+    if check:
+        check_status(ws, "tb_bboxes_clip")
+    res = (parent, match, box_out, clip_out)
+    if host:
+        return tuple(None if t is None else t.cpu() for t in res)
+    return res
 
 
 def bboxes_batched(kind, box, offsets, want_indices=True, check=True):

@@ -134,7 +134,7 @@ bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p
 
 // Blocks of the main pass that are resident on the current device at once
 // (persistent launch), found once per device.
-template <bool HAS_BOX, bool BATCHED>
+template <bool HAS_BOX, bool BATCHED, bool CLIP>
 cudaError_t k3_resident_blocks(int* out) {
   static std::atomic<int> cached[kOnceDevices];
   int dev = 0;
@@ -151,7 +151,7 @@ cudaError_t k3_resident_blocks(int* out) {
   const int sms = current_device_sms();
   if (sms <= 0) return cudaErrorInvalidDevice;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_tile<HAS_BOX, BATCHED>, NT,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_tile<HAS_BOX, BATCHED, CLIP>, NT,
                                                     k3_smem_bytes(HAS_BOX));
   if (e != cudaSuccess) return e;
   const int nb = sms * (per_sm > 0 ? per_sm : 1);
@@ -160,20 +160,20 @@ cudaError_t k3_resident_blocks(int* out) {
   return cudaSuccess;
 }
 
-template <bool HAS_BOX, bool BATCHED>
+template <bool HAS_BOX, bool BATCHED, bool CLIP = false>
 cudaError_t launch_k3(const K3Args& a, int T, cudaStream_t s) {
   constexpr int smem = k3_smem_bytes(HAS_BOX);
   static std::atomic<unsigned long long> attr_set{0};
-  cudaError_t e = smem_limit_once(attr_set, k3_tile<HAS_BOX, BATCHED>, smem);
+  cudaError_t e = smem_limit_once(attr_set, k3_tile<HAS_BOX, BATCHED, CLIP>, smem);
   if (e != cudaSuccess) return e;
   int grid = T;
   if (PERSIST) {
     int nb = 0;
-    e = k3_resident_blocks<HAS_BOX, BATCHED>(&nb);
+    e = k3_resident_blocks<HAS_BOX, BATCHED, CLIP>(&nb);
     if (e != cudaSuccess) return e;
     grid = T < nb ? T : nb;
   }
-  k3_tile<HAS_BOX, BATCHED><<<grid, NT, smem, s>>>(a);
+  k3_tile<HAS_BOX, BATCHED, CLIP><<<grid, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -191,7 +191,8 @@ cudaError_t launch_k2(const SceneWs& w, cudaStream_t s) {
 template <bool HAS_BOX>
 tb_status run_scene(const uint8_t* kind, const float* box, int64_t n, int32_t* parent,
                     int32_t* match, float* box_out, const int64_t* offsets, int64_t num_scenes,
-                    void* ws, size_t ws_bytes, int32_t* d_status, void* stream) {
+                    void* ws, size_t ws_bytes, int32_t* d_status, void* stream,
+                    float* clip_out = nullptr) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (n < 0 || n > kMaxN || d_status == nullptr) return TB_ERR_INVALID_ARG;
   if (!aligned(d_status, 4)) return TB_ERR_INVALID_ARG;
@@ -203,6 +204,7 @@ tb_status run_scene(const uint8_t* kind, const float* box, int64_t n, int32_t* p
       return TB_ERR_INVALID_ARG;
     if (!HAS_BOX && (parent == nullptr || match == nullptr)) return TB_ERR_INVALID_ARG;
     if ((parent && !aligned(parent, 4)) || (match && !aligned(match, 4))) return TB_ERR_INVALID_ARG;
+    if (clip_out && !aligned(clip_out, 16)) return TB_ERR_INVALID_ARG;
     if (offsets != nullptr && (num_scenes < 1 || num_scenes > INT_MAX - 1 || !aligned(offsets, 8)))
       return TB_ERR_INVALID_ARG;
   }
@@ -226,8 +228,13 @@ tb_status run_scene(const uint8_t* kind, const float* box, int64_t n, int32_t* p
   phase_mark(s);
   const int vec_out = (!parent || aligned(parent, 16)) && (!match || aligned(match, 16));
   K3Args a3{kind, reinterpret_cast<const float4*>(box), (int)n, parent, match,
-            reinterpret_cast<float4*>(box_out), offsets, (int)num_scenes, vec_out, w, d_status};
-  cudaError_t e = offsets ? launch_k3<HAS_BOX, true>(a3, L.T, s) : launch_k3<HAS_BOX, false>(a3, L.T, s);
+            reinterpret_cast<float4*>(box_out), offsets, (int)num_scenes, vec_out, w, d_status,
+            reinterpret_cast<float4*>(clip_out)};
+  cudaError_t e;
+  if (HAS_BOX && clip_out)
+    e = offsets ? launch_k3<HAS_BOX, true, true>(a3, L.T, s) : launch_k3<HAS_BOX, false, true>(a3, L.T, s);
+  else
+    e = offsets ? launch_k3<HAS_BOX, true>(a3, L.T, s) : launch_k3<HAS_BOX, false>(a3, L.T, s);
   if (e != cudaSuccess) return TB_ERR_CUDA;
   phase_mark(s);
   if (HAS_BOX) {
@@ -287,6 +294,17 @@ tb_status tb_bboxes_batched(const uint8_t* kind, const float* box, const int64_t
   g_phase_next = 0;
   return run_scene<true>(kind, box, n_total, parent, match, box_out, offsets, num_scenes, ws,
                          ws_bytes, d_status, stream);
+}
+
+tb_status tb_bboxes_clip(const uint8_t* kind, const float* box, const int64_t* offsets,
+                         int64_t num_scenes, int64_t n, int32_t* parent, int32_t* match,
+                         float* box_out, float* clip_out, void* ws, size_t ws_bytes,
+                         int32_t* d_status, void* stream) {
+  if (clip_out == nullptr && n > 0) return TB_ERR_INVALID_ARG;
+  if (offsets != nullptr && num_scenes < 1) return TB_ERR_INVALID_ARG;
+  g_phase_next = 0;
+  return run_scene<true>(kind, box, n, parent, match, box_out, offsets,
+                         offsets ? num_scenes : 0, ws, ws_bytes, d_status, stream, clip_out);
 }
 
 tb_status tb_set_phase_events(void* const* events, int num_events) {

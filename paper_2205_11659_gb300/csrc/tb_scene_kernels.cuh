@@ -465,6 +465,7 @@ struct K3Args {
   int vec_out;             // parent/match are 16-byte aligned
   SceneWs ws;
   int* status;
+  float4* clip_out;        // nullable: per element, the clip intersection in force (Sec. 9)
 };
 
 constexpr int CTXC = 32;      // top entries of the tile context cached in shared memory
@@ -472,7 +473,7 @@ constexpr int SOFF_CAP = 64;  // scene offsets of one tile staged in shared memo
 
 // Dynamic shared memory of k3_tile.
 __host__ __device__ constexpr int k3_smem_bytes(bool has_box) {
-  return (has_box ? (BOX_SMEM_LEN * 16 + 2 * NT * 16 + NT * 16) : 0) + TILE * 2 + NT * 4 +
+  return (has_box ? (BOX_SMEM_LEN * 16 + 2 * NT * 16 + NT * 16) : 0) + TILE * 4 + NT * 4 +
          2 * NT * 4 + NT * 4 + 2 * NT * 4;
 }
 
@@ -502,7 +503,7 @@ __device__ __forceinline__ T chunk_range(const T* tree, int l, int r, T ident, O
 struct OutCtx {
   const int* s_lo;
   const int* s_cps;
-  const uint16_t* s_spos;
+  const int* s_spos;
   const float4* s_B;
   const float4* s_box;
   const int* s_cidx;
@@ -553,7 +554,7 @@ __device__ __forceinline__ OutRes out_lookup(const OutCtx& c, const SceneWs& ws,
 // tile through K3_TILE_DONE (a return, or a break to the next ticket).  The
 // matching-only pass is held to 64 registers a thread so that 1024 threads
 // per SM stay resident.
-template <bool HAS_BOX, bool BATCHED>
+template <bool HAS_BOX, bool BATCHED, bool CLIP = false>
 __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a) {
   TB_DYNAMIC_SMEM(smem);
   __shared__ int s_scr[NW + 1];
@@ -597,10 +598,10 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   unsigned char* sp = smem;
   float4* s_box = reinterpret_cast<float4*>(sp);
   float4* s_val = s_box + BOX_SMEM_LEN;  // 2*NT: pointer jumping, then the union tree
-  float4* s_span = s_val + 2 * NT;       // NT: union of the chunks skipped by each cps link
+  float4* s_span = s_val + 2 * NT;       // NT: union of the chunks (cps(x), x]
   if (HAS_BOX) sp += BOX_SMEM_LEN * 16 + 2 * NT * 16 + NT * 16;
-  uint16_t* s_spos = reinterpret_cast<uint16_t*>(sp);
-  sp += TILE * 2;
+  int* s_spos = reinterpret_cast<int*>(sp);  // chunk slices; entries parked for the walk
+  sp += TILE * 4;
   int* s_lo = reinterpret_cast<int*>(sp);
   sp += NT * 4;
   int* s_tree = reinterpret_cast<int*>(sp);
@@ -642,7 +643,7 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   // ---- in-chunk structure from the kinds alone (register stack of
   // 4-bit positions): parent position, partner position, masks.
   unsigned long long lpar = 0, lmate = 0;
-  unsigned inside = 0, pairm = 0, openm = 0, closem = 0, leafm = 0, clipm = 0;
+  unsigned inside = 0, pairm = 0, openm = 0, closem = 0, clipm = 0;
   {
     unsigned long long stk = 0;
     int spn = 0;
@@ -667,8 +668,6 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
           pairm |= (1u << i) | (1u << o);
           lmate |= ((unsigned long long)o << (4 * i)) | ((unsigned long long)i << (4 * o));
         }
-      } else if (k == K_LEAF) {
-        leafm |= 1u << i;
       }
     }
   }
@@ -682,7 +681,7 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   // Chunk stack slice: the k-th unmatched open sits at depth lo_j + k.
   {
     int k = 0;
-    for (unsigned m = um; m; m &= m - 1) s_spos[p0 + k++] = (uint16_t)(p0 + lowest_set(m));
+    for (unsigned m = um; m; m &= m - 1) s_spos[p0 + k++] = p0 + lowest_set(m);
   }
   const int a_t = s_info[0], dstart_t = s_info[1], nseg = s_info[2];
   const bool ovf = nseg > SEGK;
@@ -700,45 +699,6 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
       ctx_i = ws.slice_pos[src];
       if (HAS_BOX) ctx_c = box_isect(ws.t_B[src / TILE], ws.slice_rel[src]);
     }
-  }
-
-  // ---- per-element lookups for the walk, from the chunk structure alone
-  //   parpair: the parent is an in-chunk open whose close is also in the chunk
-  //   for such an open with such a parent, lA = the parent's close slot (the
-  //   parent's partial union is parked there while the child is open)
-  //   for an in-chunk close: lA = gp, its open's parent; lB = gp's close
-  //   slot; whether gp is in the chunk (cl_gin), matched in it (cl_gpair),
-  //   or one of its unmatched opens (cl_gum)
-  unsigned long long kpack = 0;  // kinds, 4 bits per element, for the rolled walk
-#pragma unroll
-  for (int i = 0; i < KPT; ++i) kpack |= (unsigned long long)kk[i] << (4 * i);
-  unsigned parpair = 0, cl_gin = 0, cl_gpair = 0, cl_gum = 0;
-  unsigned long long lA = 0, lB = 0;
-#pragma unroll
-  for (int i = 0; i < KPT; ++i) {
-    const int lp = (int)((lpar >> (4 * i)) & 15ull);
-    if (((inside >> i) & 1u) && ((pairm >> lp) & 1u)) parpair |= 1u << i;
-  }
-  // (the two sparse cases below loop over the set bits of their masks)
-  const unsigned savem = openm & pairm & parpair;
-  for (unsigned m = savem; m; m &= m - 1) {
-    const int i = lowest_set(m);
-    const int lp = (int)((lpar >> (4 * i)) & 15ull);
-    lA |= ((lmate >> (4 * lp)) & 15ull) << (4 * i);
-  }
-  for (unsigned m = closem & inside; m; m &= m - 1) {
-    const int i = lowest_set(m);
-    const int lp = (int)((lpar >> (4 * i)) & 15ull);
-    if (!((inside >> lp) & 1u)) continue;
-    const unsigned bit = 1u << i;
-    const int gp = (int)((lpar >> (4 * lp)) & 15ull);
-    cl_gin |= bit;
-    lA |= (unsigned long long)gp << (4 * i);
-    if ((pairm >> gp) & 1u) {
-      cl_gpair |= bit;
-      lB |= ((lmate >> (4 * gp)) & 15ull) << (4 * i);
-    }
-    if ((um >> gp) & 1u) cl_gum |= bit;
   }
 
   if (ctx_mine) {
@@ -794,7 +754,6 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   oc.base = base;
 
   int cur = 0;
-  float4 Bx = box_universe();
   if (HAS_BOX) {
     // Clip in force below each chunk's slice: B(j) = B(cps) * v(j), folded
     // by pointer jumping (Sec. 6.1) with the tile context at the roots.
@@ -831,7 +790,6 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
       cur ^= 1;
       if (!any) break;
     }
-    Bx = s_val[cur * NT + tid];
   }
   oc.s_B = s_val + cur * NT;
 
@@ -861,21 +819,68 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   const int64_t sc_start0 = sc_start, sc_next0 = sc_next;
   const int sc0c = sc;
 
-  // ---- the walk over the chunk's elements.  The clip of the innermost
-  // open is kept in top_clip; shared memory is written for later readers and
-  // read back only when a close returns to an older open.  Element i+1's box
-  // is loaded during element i: no store of element i can target slot i+1
-  // (a parked union goes to a close beyond the current open's own close).
-  float4 bcur = box_universe();
-  if (HAS_BOX) bcur = s_box[box_slot(p0)];
-  int D = ds;     // tile-relative depth before the current element
-  int own = cq;   // chunk owning depth D-1 when the parent is outside the chunk
-  float4 cur_acc = box_empty();  // union so far of the innermost in-chunk pair
-  float4 pre = box_empty();      // union of the chunk's leaves so far
-  float4 top_clip = box_universe();
-  int o_dd = INT_MIN, o_par = -1;  // last looked-up outside parent (depth, index, clip)
-  float4 o_cx = box_universe();
+  // ---- the stack entries below the chunk start that the chunk reaches:
+  // entry m (m = 0 .. a_j) sits at tile-relative depth ds - 1 - m.  Entry 0
+  // is the parent of the chunk's first elements at its base level; entry m
+  // (m >= 1) becomes the parent of the base level after the chunk's m-th
+  // unmatched close (which matches entry m - 1).  Entry 0 stays in
+  // registers; for m >= 1 the index is parked in s_spos[p0 + KPT - m] (above
+  // the chunk's slice: a_j + (slice length) <= KPT) and the clip in the box
+  // slot of that m-th unmatched close (its own box is never read).  All
+  // lookups run here, before the walk, so that the walk below has no
+  // data-dependent loop.  (The slice entries and relative clips they read
+  // are not written again until after the walk.)
+  // An entry's clip is looked up only when an element other than an
+  // unmatched close follows in its span, or when clip_out is written (an
+  // unmatched close repeats the clip of the entry it closes).
+  constexpr bool clip_all = HAS_BOX && CLIP;
+  int par0;
+  float4 clip0 = box_universe();
+  {
+    const OutRes r0 = out_lookup<HAS_BOX>(oc, ws, ds - 1, clip_all || !(xcl & 1u), cq);
+    par0 = r0.par;
+    clip0 = r0.cx;
+    int own = r0.own;
+    unsigned xm = xcl;
+    for (int m = 1; m <= a_j; ++m) {
+      const int c = lowest_set(xm);  // the m-th unmatched close
+      xm &= xm - 1;
+      const int want = clip_all || (c + 1 < KPT && !((xcl >> (c + 1)) & 1u));
+      const OutRes r = out_lookup<HAS_BOX>(oc, ws, ds - 1 - m, want, own);
+      own = r.own;
+      s_spos[p0 + KPT - m] = r.par;
+      if (HAS_BOX) s_box[box_slot(p0 + c)] = r.cx;
+    }
+  }
+
+  // ---- the walk over the chunk's elements, the same instruction sequence
+  // for every kind (selects and predicated shared-memory accesses instead of
+  // branches, so that the lanes of a warp, whose elements differ in kind,
+  // stay converged).  State: the clip in force (clip_top) and the union of
+  // the leaves so far under the innermost open of the chunk (acc; at the
+  // base level, all leaves of the chunk so far).  An open matched in the
+  // chunk parks acc in its own box slot and the clip in force before it in
+  // its close's slot; its close reads both back, writes the pair's union at
+  // both ends and folds it into the restored acc.  An unmatched close keeps
+  // the running union of the chunk's leaves in its slot (the part of its
+  // pair's union that lies in this chunk) and takes the next entry parked
+  // above.  An unmatched open also keeps acc in its slot (the leaves since
+  // the previous unmatched open, or since the chunk start) and starts a new
+  // acc; its clip is its relative clip, read from the same slot, meet the
+  // clip in force.  Every slot is written with the same value, `own`, so
+  // the store needs no select on the kind.  The other chunks' lookups above
+  // read relative clips from those slots: the barrier first.
+  __syncthreads();
+  unsigned long long kpack = 0;  // kinds, 4 bits per element
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) kpack |= (unsigned long long)kk[i] << (4 * i);
+  int x_par = par0;   // parent of the base level
+  int x_m = 0;        // unmatched closes so far
+  float4 clip_top = clip0;
+  float4 acc = box_empty();
+  int D = ds;         // tile-relative depth before the current element (batched check)
   int4 pg = make_int4(-1, -1, -1, -1), mg = make_int4(-1, -1, -1, -1);
+  const int bp0 = base + p0;
 #pragma unroll 1
   for (int g = 0; g < KPT / 4; ++g) {
     // the group's 4-bit fields, so that the element loop below shifts by
@@ -883,120 +888,78 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
     const unsigned gk = (unsigned)(kpack >> (16 * g)) & 0xffffu;
     const unsigned gpar = (unsigned)(lpar >> (16 * g)) & 0xffffu;
     const unsigned gmate = (unsigned)(lmate >> (16 * g)) & 0xffffu;
-    const unsigned gA = (unsigned)(lA >> (16 * g)) & 0xffffu;
-    const unsigned gB = (unsigned)(lB >> (16 * g)) & 0xffffu;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i = 4 * g + q;
-    const int k = (int)((gk >> (4 * q)) & 15u);
-    const unsigned bit = 1u << i;
-    const int p = p0 + i;
-    const int e = base + p;
-    float4 bnext = bcur;
-    if (HAS_BOX && i + 1 < KPT) bnext = s_box[box_slot(p + 1)];
-    int par_i = -1, mat_i = -1;
-    if (k != K_PAD) {
-      if (BATCHED) {
+    for (int q = 0; q < 4; ++q) {
+      const int i = 4 * g + q;
+      const int k = (int)((gk >> (4 * q)) & 15u);
+      const int p = p0 + i;
+      const bool in_c = (inside >> i) & 1u;
+      const bool pr = (pairm >> i) & 1u;
+      const int lp = (int)((gpar >> (4 * q)) & 15u);
+      const int pt = (int)((gmate >> (4 * q)) & 15u);
+      const bool is_leaf = k == K_LEAF, is_close = k == K_CLOSE;
+      const bool is_open = k == K_CLIP || k == K_BLEND;
+      const bool is_uc = is_close && !pr;
+      int par_i = in_c ? bp0 + lp : x_par;
+      int mat_i = pr ? bp0 + pt : (is_close ? par_i : -1);
+      if (HAS_BOX) {
+        const int sp_own = box_slot(p), sp_pt = box_slot(p0 + pt);
+        const float4 b = s_box[sp_own];
+        const bool mc = is_close && pr;
+        float4 r = box_empty();
+        if (mc) r = s_box[sp_pt];  // acc parked by the open
+        const float4 iv = box_isect(b, clip_top);
+        const float4 lf = box_canon(iv);
+        // the raw running intersection: own box meet the clip in force for a
+        // leaf or clip open, the clip in force for a blend, the value of the
+        // open it closes for a close (the clip in force inside that open)
+        if (CLIP && k < K_PAD) a.clip_out[bp0 + i] = (is_leaf || k == K_CLIP) ? iv : clip_top;
+        if (k < K_PAD) s_box[sp_own] = is_leaf ? lf : acc;
+        if (pr) s_box[sp_pt] = is_open ? clip_top : acc;
+        const float4 y = is_leaf ? lf : r;
+        acc = is_open ? box_empty() : box_unite(acc, y);
+        clip_top = (k == K_CLIP) ? iv : (is_close ? b : clip_top);
+      }
+      if (is_uc) {
+        ++x_m;
+        x_par = s_spos[p0 + KPT - x_m];
+      }
+      if (BATCHED && k != K_PAD) {
+        const int e = bp0 + i;
         while (e >= sc_next && sc < a.num_scenes - 1) {
           ++sc;
           sc_start = a.offsets[sc];
           sc_next = a.offsets[sc + 1];
         }
         if (e == sc_start && dstart_t + D != 0) atomic_cas_i32(a.status, ST_OK, ST_UNBALANCED);
-      }
-      const int lp = (int)((gpar >> (4 * q)) & 15u);
-      int par = base + p0 + lp;
-      float4 cx = top_clip;
-      if (!(inside & bit)) {
-        // Parent is the entry at depth D-1 of the stack at the chunk start.
-        // Consecutive elements at the chunk's base level share it, so the
-        // last one looked up is kept; a close needs only its index.
-        const int dd = D - 1;
-        if (dd != o_dd) {
-          const int want_clip = HAS_BOX && k != K_CLOSE;
-          const OutRes r = out_lookup<HAS_BOX>(oc, ws, dd, want_clip, own);
-          own = r.own;
-          o_par = r.par;
-          o_cx = r.cx;
-          o_dd = (want_clip || !HAS_BOX) ? dd : INT_MIN;
-        }
-        par = o_par;
-        cx = o_cx;
-      }
-      par_i = par;
-      if (pairm & bit) mat_i = base + p0 + (int)((gmate >> (4 * q)) & 15u);
-      else if (k == K_CLOSE) mat_i = par;
-      if (HAS_BOX) {
-        float4* b = &s_box[box_slot(p)];
-        const float4 iv = box_isect(bcur, cx);
-        if (k == K_LEAF) {
-          const float4 out = box_canon(iv);
-          *b = out;
-          pre = box_unite(pre, out);
-          if (parpair & bit) cur_acc = box_unite(cur_acc, out);
-        } else if (k == K_CLOSE) {
-          if (inside & bit) {
-            // in-chunk pair: write its union at both ends, return to the
-            // enclosing open's clip and partial union
-            const float4 U = cur_acc;
-            s_box[box_slot(p0 + lp)] = U;
-            *b = U;
-            cur_acc = box_empty();
-            if (cl_gin & bit) {
-              const int gp = (int)((gA >> (4 * q)) & 15u);
-              const float4 g = s_box[box_slot(p0 + gp)];
-              top_clip = (cl_gum & bit) ? box_isect(Bx, g) : g;
-              if (cl_gpair & bit)
-                cur_acc = box_unite(s_box[box_slot(p0 + (int)((gB >> (4 * q)) & 15u))], U);
-            }
-          } else {
-            *b = pre;  // matches an open before the chunk: everything before it is inside
-          }
-        } else {  // open
-          float4 clip;
-          if (um & bit) {
-            clip = box_isect(Bx, bcur);  // chunk-slice entry: B(j) * relative clip
-          } else {
-            clip = (k == K_CLIP) ? iv : cx;
-            *b = clip;  // read back when a close returns to this open
-          }
-          top_clip = clip;
-          if (savem & bit) s_box[box_slot(p0 + (int)((gA >> (4 * q)) & 15u))] = cur_acc;
-          if (pairm & bit) cur_acc = box_empty();
-        }
-      }
-      if (BATCHED) {
         if (par_i >= 0) par_i = (int)(par_i - sc_start);
         if (mat_i >= 0) mat_i = (int)(mat_i - sc_start);
+        D += kind_delta(k);
       }
-      D += kind_delta(k);
+      if (q == 0) { pg.x = par_i; mg.x = mat_i; }
+      if (q == 1) { pg.y = par_i; mg.y = mat_i; }
+      if (q == 2) { pg.z = par_i; mg.z = mat_i; }
+      if (q == 3) { pg.w = par_i; mg.w = mat_i; }
     }
-    bcur = bnext;
-    if (q == 0) { pg.x = par_i; mg.x = mat_i; }
-    if (q == 1) { pg.y = par_i; mg.y = mat_i; }
-    if (q == 2) { pg.z = par_i; mg.z = mat_i; }
-    if (q == 3) { pg.w = par_i; mg.w = mat_i; }
-    if (q == 3) {
-      // parent / match of four elements (opens matched outside the chunk get
-      // -1 here; their close writes the real value later)
-      const int e4 = e - 3;
-      if (a.vec_out && e4 + 4 <= a.n) {
-        if (a.parent) *reinterpret_cast<int4*>(a.parent + e4) = pg;
-        if (a.match) *reinterpret_cast<int4*>(a.match + e4) = mg;
-      } else {
-        const int pa[4] = {pg.x, pg.y, pg.z, pg.w};
-        const int ma[4] = {mg.x, mg.y, mg.z, mg.w};
+    // parent / match of four elements (opens matched outside the chunk get
+    // -1 here; their close writes the real value later)
+    const int e4 = bp0 + 4 * g;
+    if (a.vec_out && e4 + 4 <= a.n) {
+      if (a.parent) *reinterpret_cast<int4*>(a.parent + e4) = pg;
+      if (a.match) *reinterpret_cast<int4*>(a.match + e4) = mg;
+    } else {
+      const int pa[4] = {pg.x, pg.y, pg.z, pg.w};
+      const int ma[4] = {mg.x, mg.y, mg.z, mg.w};
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          if (e4 + r < a.n) {
-            if (a.parent) a.parent[e4 + r] = pa[r];
-            if (a.match) a.match[e4 + r] = ma[r];
-          }
+      for (int r = 0; r < 4; ++r) {
+        if (e4 + r < a.n) {
+          if (a.parent) a.parent[e4 + r] = pa[r];
+          if (a.match) a.match[e4 + r] = ma[r];
         }
       }
     }
   }
-  }
+
   __syncthreads();  // every walk has finished; relative clips are no longer read
 
   if (!HAS_BOX) {
@@ -1034,35 +997,44 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   }
 
   // ---- unions across chunks (and the partial unions of cross-tile pairs)
-  // Union of the chunk's leaves after each unmatched open: everything after
-  // it in the chunk is inside it.
-  float4 run = box_empty();
-#pragma unroll
-  for (int i = KPT - 1; i >= 0; --i) {
-    if ((leafm >> i) & 1u) run = box_unite(run, s_box[box_slot(p0 + i)]);
-    if ((um >> i) & 1u) s_box[box_slot(p0 + i)] = run;
+  // Union of the chunk's leaves after each unmatched open (everything after
+  // it in the chunk is inside it): the walk left in each unmatched open's
+  // slot the leaves between it and the previous one (or the chunk start),
+  // and acc holds the leaves after the last one; fold them from the back.
+  // What remains is the union of all the chunk's leaves.
+  float4 run = acc;
+  for (unsigned m = um; m; m &= ~(1u << (31 - __clz(m)))) {
+    float4* sl = &s_box[box_slot(p0 + 31 - __clz(m))];
+    const float4 part = *sl;
+    *sl = run;
+    run = box_unite(part, run);
   }
   const int later_lo = block_excl_suffix_min(lo_j, s_scr);
   const float4 rest = block_excl_suffix(run, box_empty(), OpUnite(), s_fscr);  // later chunks
   float4* s_ut = s_val;  // union tree over the chunks' leaf unions
   build_chunk_tree(s_ut, run, OpUnite());
-  // span(x) = union of the chunks (cps(x), x]: what a close gains when its
-  // open's owner moves one cps link down
-  s_span[tid] = chunk_range(s_ut, cps + 1, tid, box_empty(), OpUnite());
-  float4 mid = xcl ? chunk_range(s_ut, cq + 1, tid - 1, box_empty(), OpUnite()) : box_empty();
+  // span(x) = union of the chunks (cps(x), x]: what a close's union gains
+  // when the entry it closes lies in the slice of the chunk below x's
+  s_span[tid] = tree_range(s_ut, NT, cps + 1, tid, box_empty(), OpUnite());
   __syncthreads();
   {
-    // Closes matching an open of an earlier chunk: union = the open's chunk
-    // after it + whole chunks in between + this chunk before the close.
-    int u = cq;
+    // Closes matching an open of an earlier chunk or tile; the m-th closes
+    // entry m (its index parked above, entry 0's in par0): union = the open's
+    // chunk after it + the whole chunks in between + this chunk before the
+    // close (Sec. 6.2).  Entry m + 1 encloses entry m, so the unions nest and
+    // accumulate: U(m+1) = U(m) + usuf(open m+1) + upre(close m+1), plus
+    // span(owner of entry m) when the owner steps down a chunk (entry m sat
+    // at the bottom of its chunk's slice, so the next owner is that chunk's
+    // cps; below the tile start the tile's own leaves before the close are
+    // all that is needed here).
     int64_t scs = sc_start0, scn = sc_next0;
     int scx = sc0c;
-    unsigned m = xcl;
-    while (m) {
-      const int i = lowest_set(m);
-      m &= m - 1;
-      const unsigned below = (1u << i) - 1u;
-      const int dd = ds + popc(openm & below) - popc(closem & below) - 1;
+    float4 U = box_empty();
+    int u_prev = -1;
+    unsigned m_cl = xcl;
+    for (int m = 0; m_cl; ++m) {
+      const int i = lowest_set(m_cl);
+      m_cl &= m_cl - 1;
       const int cp = p0 + i;
       const int e = base + cp;
       if (BATCHED) {
@@ -1073,24 +1045,25 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
         }
       }
       const int eo = BATCHED ? (int)(e - scs) : e;
-      const float4 upre = s_box[box_slot(cp)];
-      while (u >= 0 && s_lo[u] > dd) {
-        mid = box_unite(mid, s_span[u]);
-        u = s_cps[u];
-      }
-      if (u >= 0) {
-        const int si = u * KPT + (dd - s_lo[u]);
-        const int op = in_range(si, 0, TILE, ws.status) ? s_spos[si] : cp;
-        const float4 U = box_unite(box_unite(s_box[box_slot(op)], mid), upre);
+      const int idx = m == 0 ? par0 : s_spos[p0 + KPT - m];
+      const bool in_t = idx >= base && idx < base + TILE;
+      const int u = in_t ? (idx - base) / KPT : -1;
+      if (m == 0) U = tree_range(s_ut, NT, u + 1, tid - 1, box_empty(), OpUnite());
+      else if (u != u_prev && in_range(u_prev, 0, NT, ws.status)) U = box_unite(U, s_span[u_prev]);
+      U = box_unite(U, s_box[box_slot(cp)]);  // this chunk before the close
+      if (in_t) {
+        const int op = idx - base;
+        U = box_unite(U, s_box[box_slot(op)]);  // the open's chunk after it
         s_box[box_slot(op)] = U;
         s_box[box_slot(cp)] = U;
-        if (a.match) a.match[base + op] = eo;
-      } else if (in_range(-1 - dd, 0, TILE, ws.status)) {
-        const int mm = -1 - dd;
-        ws.upre[(size_t)t * TILE + mm] = box_unite(mid, upre);
+        if (a.match) a.match[idx] = eo;
+      } else if (in_range(m - ds, 0, TILE, ws.status)) {
+        const int mm = m - ds;  // below the tile start: its k4 pass finishes the pair
+        ws.upre[(size_t)t * TILE + mm] = U;
         ws.cpos[(size_t)t * TILE + mm] = e;
         ws.cval[(size_t)t * TILE + mm] = eo;
       }
+      u_prev = u;
     }
   }
   // Opens left unmatched at the tile end: union over the rest of the tile.

@@ -322,3 +322,14 @@ def test_zero_area_rule(n):
         b = inputs.grid_boxes(k, 61 + n)
     assert _touching_leaves(k, b) > 0   # the case separates >= from >
     assert_bboxes_equal(k, b)
+
+
+@pytest.mark.parametrize("n", [3 * TILE + 5, 200_003, 1 << 22])
+def test_wide_scene_unions(n):
+    """Small leaves spread over a wide area under clips that cover it all: a
+    node's union depends on every descendant (random-walk scenes on the 4096
+    square saturate to nearly the whole square), so a union that drops or
+    adds a part shows."""
+    k = inputs.random_walk_kinds(n, 900 + n)
+    b = inputs.scene_boxes(k, 901 + n, center_hi=1e6, leaf_wh=(1.0, 4.0), clip_wh=(1.5e6, 3e6))
+    assert_bboxes_equal(k, b)
