@@ -65,6 +65,16 @@ def tuned_persistent():
     return False
 
 
+def tuned_matcher():
+    """In-tile matcher of the matching-only pass: 0 = the chunk walk (default),
+    1 = the binary search over a tree of depths (Fig. "core")."""
+    import json
+    if os.path.exists(SHAPE_FILE):
+        with open(SHAPE_FILE) as f:
+            return int(json.load(f).get("matcher", 0))
+    return 0
+
+
 def up_to_date(lib=LIB):
     if not os.path.exists(lib):
         return False
@@ -72,12 +82,14 @@ def up_to_date(lib=LIB):
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force=False, verbose=False, shape=None, out_dir=None, persistent=None, debug=False):
+def build(force=False, verbose=False, shape=None, out_dir=None, persistent=None, debug=False,
+          matcher=None):
     """Build the library if needed; returns its path.  shape = (threads per
     block, elements per thread) and persistent override the tuned values and
     out_dir the output folder (the autotuner builds its candidates that
     way); debug=True compiles the kernels' index checks in (TB_DEBUG; give it
-    an out_dir of its own)."""
+    an out_dir of its own); matcher selects the in-tile matcher of the
+    matching-only pass (tuned_matcher())."""
     out_dir = OUT_DIR if out_dir is None else out_dir
     lib_path = os.path.join(out_dir, "libtb.so")
     if not force and up_to_date(lib_path):
@@ -86,9 +98,11 @@ def build(force=False, verbose=False, shape=None, out_dir=None, persistent=None,
     exe = nvcc()
     nt, kpt = tuned_shape() if shape is None else shape
     persist = tuned_persistent() if persistent is None else bool(persistent)
+    match_kind = tuned_matcher() if matcher is None else int(matcher)
     common = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I" + INCLUDE, "-I" + CSRC, "-DTB_NT=%d" % nt, "-DTB_KPT=%d" % kpt,
-                     "-DTB_PERSIST=%d" % int(persist), "-DTB_DEBUG=%d" % int(bool(debug))]
+                     "-DTB_PERSIST=%d" % int(persist), "-DTB_DEBUG=%d" % int(bool(debug)),
+              "-DTB_MATCHER=%d" % match_kind]
     if verbose:
         common += ["-Xptxas", "-v"]
 

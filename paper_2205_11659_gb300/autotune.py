@@ -24,9 +24,11 @@ import numpy as np
 
 from . import _build
 
-# (threads per block, elements per thread, persistent main pass)
-CANDIDATES = [(256, 16, False), (256, 16, True), (256, 8, False), (128, 16, False),
-              (512, 8, False)]
+# (threads per block, elements per thread, persistent main pass, in-tile
+# matcher of the matching-only pass: 0 = chunk walk, 1 = binary search over a
+# tree of depths, Fig. "core")
+CANDIDATES = [(256, 16, False, 0), (256, 16, True, 0), (256, 8, False, 0), (128, 16, False, 0),
+              (512, 8, False, 0), (128, 16, False, 1), (256, 16, False, 1)]
 
 
 def _time_calls(call, reps):
@@ -66,9 +68,10 @@ def evaluate(cand, scenes, checks, reference):
     the outputs differ from the reference."""
     import torch
     from . import binding
-    nt, kpt, persist = cand
-    lib_path = _build.build(shape=(nt, kpt), persistent=persist,
-                            out_dir=os.path.join(_build.OUT_DIR, "tune_%d_%d_%d" % (nt, kpt, persist)))
+    nt, kpt, persist, matcher = cand
+    lib_path = _build.build(shape=(nt, kpt), persistent=persist, matcher=matcher,
+                            out_dir=os.path.join(_build.OUT_DIR, "tune_%d_%d_%d_%d"
+                                                 % (nt, kpt, persist, matcher)))
     saved = _build.LIB
     binding._lib = None
     _build.LIB = lib_path
@@ -136,7 +139,7 @@ def main(argv=None):
         kk, bx = inputs.random_walk_scene(n, seed)
         checks.append((kk, bx, None))
     checks.append(inputs.batched_scenes(64, 4, 4.0, 14.0))
-    current = _build.tuned_shape() + (_build.tuned_persistent(),)
+    current = _build.tuned_shape() + (_build.tuned_persistent(), _build.tuned_matcher())
     order = [current] + [c for c in CANDIDATES if c != current]
     reference = None
     results = []
@@ -146,7 +149,8 @@ def main(argv=None):
         if reference is None:
             reference = outs  # the current build, which the tests check against the oracle
         results.append({"threads_per_block": cand[0], "elements_per_thread": cand[1],
-                        "persistent": bool(cand[2]), "correct": ms is not None, "ms": ms,
+                        "persistent": bool(cand[2]), "matcher": cand[3],
+                        "correct": ms is not None, "ms": ms,
                         "seconds": round(time.time() - t0, 1)})
         print(json.dumps(results[-1]), flush=True)
     ok = [r for r in results if r["correct"]]
@@ -158,6 +162,7 @@ def main(argv=None):
     summary = {"threads_per_block": best["threads_per_block"],
                "elements_per_thread": best["elements_per_thread"],
                "persistent": best["persistent"],
+               "matcher": best["matcher"],
                "chosen_by": "autotune.py: fastest correct candidate on rw24 + batch512 + match24",
                "device": {"name": props.name, "sms": props.multi_processor_count,
                           "capability": "%d.%d" % (props.major, props.minor),

@@ -162,6 +162,11 @@ cudaError_t k3_resident_blocks(int* out) {
 
 template <bool HAS_BOX, bool BATCHED, bool CLIP = false>
 cudaError_t launch_k3(const K3Args& a, int T, cudaStream_t s) {
+  if (TB_MATCHER == 1 && !HAS_BOX && !BATCHED) {
+    // the binary-search form of the matching-only pass (an autotuner candidate)
+    k3_search<<<T, NT, k3s_smem_bytes(), s>>>(a);
+    return cudaGetLastError();
+  }
   constexpr int smem = k3_smem_bytes(HAS_BOX);
   static std::atomic<unsigned long long> attr_set{0};
   cudaError_t e = smem_limit_once(attr_set, k3_tile<HAS_BOX, BATCHED, CLIP>, smem);
@@ -177,13 +182,50 @@ cudaError_t launch_k3(const K3Args& a, int T, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Blocks of k2_jump that are resident on the current device at once (the
+// most a cooperative launch may use), found once per device.
+cudaError_t k2_jump_max_blocks(int* out) {
+  static std::atomic<int> cached[kOnceDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool tracked = dev >= 0 && dev < kOnceDevices;
+  if (tracked) {
+    const int c = cached[dev].load(std::memory_order_relaxed);
+    if (c > 0) {
+      *out = c;
+      return cudaSuccess;
+    }
+  }
+  const int sms = current_device_sms();
+  if (sms <= 0) return cudaErrorInvalidDevice;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2_jump, NTJ, 0);
+  if (e != cudaSuccess) return e;
+  const int nb = sms * (per_sm > 0 ? per_sm : 1);
+  if (tracked) cached[dev].store(nb, std::memory_order_relaxed);
+  *out = nb;
+  return cudaSuccess;
+}
+
 template <bool HAS_BOX>
 cudaError_t launch_k2(const SceneWs& w, cudaStream_t s) {
   const int g = (w.T + NTR - 1) / NTR;
   k2_links<<<g, NTR, 0, s>>>(w);
   k2_segments<HAS_BOX><<<g, NTR, 0, s>>>(w);
-  if (HAS_BOX) k2_jump<<<1, NT2, 0, s>>>(w);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !HAS_BOX) return e;
+  int maxb = 0;
+  e = k2_jump_max_blocks(&maxb);
+  if (e != cudaSuccess) return e;
+  const int want = (w.T + NTJ - 1) / NTJ;
+  const int blocks = want < maxb ? want : maxb;
+  int rounds = 1;
+  while ((1 << (rounds - 1)) < w.T) ++rounds;  // ceil(log2 T) + 1
+  SceneWs wa = w;
+  void* args[] = {&wa, &rounds};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k2_jump), dim3(blocks),
+                                     dim3(NTJ), args, 0, s);
 }
 
 // The whole matching / bounding-box pass over one stream (a single scene

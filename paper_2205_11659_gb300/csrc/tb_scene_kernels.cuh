@@ -32,6 +32,8 @@
 #ifndef TB_SCENE_KERNELS_CUH
 #define TB_SCENE_KERNELS_CUH
 
+#include <cooperative_groups.h>
+
 #include "tb_core.cuh"
 
 namespace tb {
@@ -330,50 +332,36 @@ __global__ void __launch_bounds__(NTR) k2_segments(SceneWs ws) {
   }
 }
 
-// B(u) = B(ps(u)) * v(u) is a fold along the ps chain: pointer jumping in
-// one block, each round doubling the covered chain length (Sec. 6.1).  The
-// loads of a round are issued in batches of KB tiles per thread.
-constexpr int K2_KB = 4;
-__global__ void __launch_bounds__(NT2) k2_jump(SceneWs ws) {
-  const int T = ws.T, tid = threadIdx.x;
-  if (*ws.status != ST_OK) return;  // no pass running now writes it: uniform
+// B(u) = B(ps(u)) * v(u) is a fold along the ps chain: pointer jumping,
+// each round doubling the covered chain length (Sec. 6.1), by all the
+// blocks of a cooperative launch with a grid-wide barrier between rounds.
+// `rounds` covers the longest possible chain (ceil(log2 T) + 1); the rounds
+// after the chains have closed copy their values unchanged.  The link and
+// value arrays are read past L1 (ld.cg): another block wrote them in the
+// previous round.
+constexpr int NTJ = 256;
+__global__ void __launch_bounds__(NTJ) k2_jump(SceneWs ws, int rounds) {
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  const int T = ws.T;
+  if (*ws.status != ST_OK) return;  // no kernel running now writes it: the whole grid returns
+  const int nthr = gridDim.x * NTJ;
   int cur = 0;
-  for (int round = 0; round < 40; ++round) {
-    bool any = false;
-    for (int u0 = tid; u0 < T; u0 += NT2 * K2_KB) {
-      int l[K2_KB], nl[K2_KB];
-      float4 v[K2_KB], pv[K2_KB];
-#pragma unroll
-      for (int b = 0; b < K2_KB; ++b) {
-        const int u = u0 + b * NT2;
-        l[b] = -1;
-        if (u < T) {
-          l[b] = ws.t_link[cur][u];
-          v[b] = ws.t_val[cur][u];
-        }
+  for (int r = 0; r < rounds; ++r) {
+    for (int u = blockIdx.x * NTJ + threadIdx.x; u < T; u += nthr) {
+      const int l = __ldcg(ws.t_link[cur] + u);
+      float4 v = __ldcg(ws.t_val[cur] + u);
+      int nl = -1;
+      if (l >= 0 && in_range(l, 0, T, ws.status)) {
+        v = box_isect(__ldcg(ws.t_val[cur] + l), v);
+        nl = __ldcg(ws.t_link[cur] + l);
       }
-#pragma unroll
-      for (int b = 0; b < K2_KB; ++b) {
-        nl[b] = -1;
-        if (l[b] >= 0) {
-          pv[b] = ws.t_val[cur][l[b]];
-          nl[b] = ws.t_link[cur][l[b]];
-        }
-      }
-#pragma unroll
-      for (int b = 0; b < K2_KB; ++b) {
-        const int u = u0 + b * NT2;
-        if (u < T) {
-          ws.t_val[cur ^ 1][u] = l[b] >= 0 ? box_isect(pv[b], v[b]) : v[b];
-          ws.t_link[cur ^ 1][u] = nl[b];
-          any |= nl[b] >= 0;
-        }
-      }
+      __stcg(ws.t_val[cur ^ 1] + u, v);
+      __stcg(ws.t_link[cur ^ 1] + u, nl);
     }
     cur ^= 1;
-    if (!block_or(any)) break;
+    grid.sync();
   }
-  for (int u = tid; u < T; u += NT2) ws.t_B[u] = ws.t_val[cur][u];
+  for (int u = blockIdx.x * NTJ + threadIdx.x; u < T; u += nthr) ws.t_B[u] = __ldcg(ws.t_val[cur] + u);
 }
 
 // ----------------------------------------------------- tile context helpers
@@ -450,6 +438,73 @@ __device__ __forceinline__ void build_chunk_tree(T* tree, T leaf, Op op) {
     }
   }
   __syncthreads();
+}
+
+// For the cross-chunk unions of the main pass, with two barriers: the
+// lowest depth of the later chunks of the tile (*later_lo), the union of the
+// later chunks' leaves (*rest), and the union tree over the chunks' leaf
+// unions (leaves at [NT, 2NT)).  Inside each warp by shuffles, across the NW
+// warps from their aggregates (s_wlo, s_wrun: NW + 1 entries each).
+__device__ __forceinline__ void chunk_suffixes_and_union_tree(int lo, float4 run, float4* tree,
+                                                              int* s_wlo, float4* s_wrun,
+                                                              int* later_lo, float4* rest) {
+  const int tid = threadIdx.x, lane = lane_id(), w = warp_id();
+  int smin = lo;
+  float4 sun = run;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = shfl_down(smin, d);
+    const float4 yu = shfl_down(sun, d);
+    if (lane + d < 32) {
+      smin = smin < y ? smin : y;
+      sun = box_unite(sun, yu);
+    }
+  }
+  float4 v = run;
+  tree[NT + tid] = v;
+#pragma unroll
+  for (int g = 2; g <= 32; g <<= 1) {
+    v = box_unite(v, shfl_xor(v, g >> 1));
+    if ((lane & (g - 1)) == 0) tree[NT / g + tid / g] = v;
+  }
+  if (lane == 0) {
+    s_wlo[w] = smin;
+    s_wrun[w] = sun;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    // top of the union tree: NW warp nodes at [NW, 2NW)
+    float4 x = tid < NW ? tree[NW + tid] : tree[NW];
+#pragma unroll
+    for (int g = 2; g <= NW; g <<= 1) {
+      x = box_unite(x, shfl_xor(x, g >> 1));
+      if (tid < NW && (tid & (g - 1)) == 0) tree[NW / g + tid / g] = x;
+    }
+    // exclusive suffix over the warps, in place (the warp after the last
+    // holds the identities)
+    if (tid == 0) {
+      int am = INT_MAX;
+      float4 au = box_empty();
+      for (int i = NW - 1; i >= 0; --i) {
+        const int xm = s_wlo[i];
+        const float4 xu = s_wrun[i];
+        s_wlo[i] = am;
+        s_wrun[i] = au;
+        am = am < xm ? am : xm;
+        au = box_unite(xu, au);
+      }
+    }
+  }
+  __syncthreads();
+  int exm = shfl_down(smin, 1);
+  float4 exu = shfl_down(sun, 1);
+  if (lane == 31) {
+    exm = INT_MAX;
+    exu = box_empty();
+  }
+  const int am = s_wlo[w];
+  *later_lo = exm < am ? exm : am;
+  *rest = box_unite(exu, s_wrun[w]);
 }
 
 // ------------------------------------------------------------------- K3
@@ -617,6 +672,33 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
     s_info[2] = ws.t_nseg[t];
   }
   if (tid < SEGK) s_seg[tid] = ws.t_seg[(size_t)t * SEGK + tid];
+  // The tile context's top CTXC entries are the longest chain of dependent
+  // loads (tile info, owner segments, slice entry, clips): warp 0 issues them
+  // first, reading the tile info and segments itself, so that they overlap
+  // the kinds-only work below (a tile whose segment list overflowed takes
+  // the slower path further down instead).
+  int ctx_i = -1;
+  float4 ctx_c = box_universe();
+  bool ctx_early = false;
+  if (tid < CTXC) {
+    const int a0 = ws.t_a[t], d0 = ws.t_dstart[t], ns0 = ws.t_nseg[t];
+    ctx_early = ns0 <= SEGK;
+    if (ctx_early && tid <= a0) {
+      const int gd = d0 - 1 - tid;
+      int src = -1;
+      for (int i = 0; i < ns0; ++i) {
+        const int4 sg = ws.t_seg[(size_t)t * SEGK + i];
+        if (gd >= sg.z && gd <= sg.w) {
+          src = sg.x >= 0 ? sg.x * TILE + (gd - sg.y) : -1;
+          break;
+        }
+      }
+      if (src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status)) {
+        ctx_i = ws.slice_pos[src];
+        if (HAS_BOX) ctx_c = box_isect(ws.t_B[src / TILE], ws.slice_rel[src]);
+      }
+    }
+  }
   if (BATCHED && tid < 2) {
     // scene of the tile's first (tid 0) and last (tid 1) element
     const int64_t e = base + (tid == 0 ? 0 : cnt - 1);
@@ -686,14 +768,12 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   const int a_t = s_info[0], dstart_t = s_info[1], nseg = s_info[2];
   const bool ovf = nseg > SEGK;
 
-  // ---- tile context: the top CTXC entries of the stack below the tile
-  // start, loaded into registers now and stored to shared memory after the
-  // register work below, so that their latency overlaps it
+  // ---- tile context of a tile whose owner segments overflowed (the other
+  // tiles loaded it at the start): the sources of every depth below the tile
+  // start, then the top CTXC entries as above
   if (ovf) fill_ctx_overflow(S, ws, t, dstart_t, a_t + 1, s_seg);
   const bool ctx_mine = tid < CTXC && tid <= a_t;
-  int ctx_i = -1;
-  float4 ctx_c = box_universe();
-  if (ctx_mine) {
+  if (ctx_mine && !ctx_early) {
     const int src = ctx_src_of(ws, t, ovf, s_seg, nseg, dstart_t - 1 - tid, tid);
     if (src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status)) {
       ctx_i = ws.slice_pos[src];
@@ -881,6 +961,11 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   int D = ds;         // tile-relative depth before the current element (batched check)
   int4 pg = make_int4(-1, -1, -1, -1), mg = make_int4(-1, -1, -1, -1);
   const int bp0 = base + p0;
+  // the next element's slot is loaded one element ahead; the only store of
+  // an element that can hit the next slot is an open's parked clip when its
+  // close follows at once, and that value is forwarded instead
+  float4 bnext = box_universe();
+  if (HAS_BOX) bnext = s_box[box_slot(p0)];
 #pragma unroll 1
   for (int g = 0; g < KPT / 4; ++g) {
     // the group's 4-bit fields, so that the element loop below shifts by
@@ -904,7 +989,8 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
       int mat_i = pr ? bp0 + pt : (is_close ? par_i : -1);
       if (HAS_BOX) {
         const int sp_own = box_slot(p), sp_pt = box_slot(p0 + pt);
-        const float4 b = s_box[sp_own];
+        const float4 b = bnext;
+        if (i + 1 < KPT) bnext = s_box[box_slot(p + 1)];
         const bool mc = is_close && pr;
         float4 r = box_empty();
         if (mc) r = s_box[sp_pt];  // acc parked by the open
@@ -916,13 +1002,16 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
         if (CLIP && k < K_PAD) a.clip_out[bp0 + i] = (is_leaf || k == K_CLIP) ? iv : clip_top;
         if (k < K_PAD) s_box[sp_own] = is_leaf ? lf : acc;
         if (pr) s_box[sp_pt] = is_open ? clip_top : acc;
+        if (is_open && pr && pt == i + 1) bnext = clip_top;
         const float4 y = is_leaf ? lf : r;
         acc = is_open ? box_empty() : box_unite(acc, y);
         clip_top = (k == K_CLIP) ? iv : (is_close ? b : clip_top);
       }
-      if (is_uc) {
-        ++x_m;
-        x_par = s_spos[p0 + KPT - x_m];
+      {
+        // after an unmatched close the base level takes the next parked entry
+        x_m += is_uc ? 1 : 0;
+        const int nx = s_spos[p0 + KPT - (x_m > 0 ? x_m : 1)];
+        x_par = is_uc ? nx : x_par;
       }
       if (BATCHED && k != K_PAD) {
         const int e = bp0 + i;
@@ -1009,10 +1098,10 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
     *sl = run;
     run = box_unite(part, run);
   }
-  const int later_lo = block_excl_suffix_min(lo_j, s_scr);
-  const float4 rest = block_excl_suffix(run, box_empty(), OpUnite(), s_fscr);  // later chunks
   float4* s_ut = s_val;  // union tree over the chunks' leaf unions
-  build_chunk_tree(s_ut, run, OpUnite());
+  int later_lo;
+  float4 rest;           // union of the later chunks' leaves
+  chunk_suffixes_and_union_tree(lo_j, run, s_ut, s_scr, s_fscr, &later_lo, &rest);
   // span(x) = union of the chunks (cps(x), x]: what a close's union gains
   // when the entry it closes lies in the slice of the chunk below x's
   s_span[tid] = tree_range(s_ut, NT, cps + 1, tid, box_empty(), OpUnite());
@@ -1093,6 +1182,109 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   }
 #endif
 #undef K3_TILE_DONE
+}
+
+// ---------------------------------------------------- K3, search matcher
+// The matching-only main pass as the paper's binary-search form (Sec. 5,
+// Fig. "core"): instead of walking a stack per chunk, every element finds
+// its parent by the up/down search over a tree of the tile's depths.  With
+// d(p) the depth before element p (relative to the tile start), the parent
+// of p is the last q < p with d(q) <= d(p) - 1 (the innermost open still
+// open at p); a close's match is its parent, an open's match is written by
+// its close.  When no such q lies in the tile the parent is the tile-context
+// entry -d(p) (element 0 has depth 0, so then d(p) <= 0).  Single scenes
+// only (the batched pass keeps the walk).  An alternative the autotuner
+// builds and times (TB_MATCHER = 1), not the tuned default.
+#ifndef TB_MATCHER
+#define TB_MATCHER 0
+#endif
+
+__host__ __device__ constexpr int k3s_smem_bytes() { return 2 * TILE * 4; }
+
+__global__ void __launch_bounds__(NT) k3_search(K3Args a) {
+  TB_DYNAMIC_SMEM(smem);
+  __shared__ int s_scr[NW + 1];
+  __shared__ int s_cidx[CTXC];
+  __shared__ int4 s_seg[SEGK];
+  __shared__ int s_info[4];
+  __shared__ SegState S;
+  const int tid = threadIdx.x, t = blockIdx.x;
+  const int base = t * TILE, cnt = min(TILE, a.n - base), p0 = tid * KPT;
+  const SceneWs& ws = a.ws;
+  int* s_tree = reinterpret_cast<int*>(smem);  // min tree of depths, leaves at [TILE, 2 TILE)
+  if (tid == 0) {
+    s_info[0] = ws.t_a[t];
+    s_info[1] = ws.t_dstart[t];
+    s_info[2] = ws.t_nseg[t];
+    s_info[3] = *a.status;  // an error of the earlier passes: the block stops (below)
+  }
+  if (tid < SEGK) s_seg[tid] = ws.t_seg[(size_t)t * SEGK + tid];
+  uint8_t kk[KPT];
+  load_kinds(a.kind, a.n, base + p0, kk);
+  int rel[KPT];
+  int r = 0;
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) {
+    rel[i] = r;  // depth before element i, relative to the chunk start
+    r += kk[i] == K_PAD ? 0 : kind_delta(kk[i]);
+  }
+  int tot;
+  const int ds = block_excl_scan(r, 0, OpAdd(), s_scr, &tot);  // barriers: s_info visible
+  const int a_t = s_info[0], dstart_t = s_info[1], nseg = s_info[2];
+  if (s_info[3] != ST_OK) return;  // the same value for every thread: the whole block returns
+  const bool ovf = nseg > SEGK;
+#pragma unroll
+  for (int i = 0; i < KPT; ++i)
+    s_tree[TILE + p0 + i] = p0 + i < cnt ? ds + rel[i] : INT_MAX;
+  if (ovf) fill_ctx_overflow(S, ws, t, dstart_t, a_t + 1, s_seg);
+  if (tid < CTXC && tid <= a_t) {
+    const int src = ctx_src_of(ws, t, ovf, s_seg, nseg, dstart_t - 1 - tid, tid);
+    s_cidx[tid] = src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status) ? ws.slice_pos[src] : -1;
+  }
+  __syncthreads();
+  for (int h = TILE / 2; h >= 1; h >>= 1) {
+    for (int i = h + tid; i < 2 * h; i += NT) s_tree[i] = min(s_tree[2 * i], s_tree[2 * i + 1]);
+    __syncthreads();
+  }
+  // one element per thread and round, consecutive threads on consecutive
+  // elements (coalesced stores)
+  for (int i = 0; i < KPT; ++i) {
+    const int p = i * NT + tid;
+    if (p >= cnt) break;
+    const int e = base + p;
+    const int k = a.kind[e] > 3 ? K_LEAF : a.kind[e];
+    const int d = s_tree[TILE + p];
+    const int q = tree_last_le(s_tree, TILE, p, d - 1);
+    int par;
+    if (q >= 0) {
+      par = base + q;
+    } else {
+      const int m = -d;  // tile-context entry of depth d - 1
+      if (m < CTXC) {
+        par = m <= a_t ? s_cidx[m] : -1;
+      } else {
+        const int src = ctx_src_of(ws, t, ovf, s_seg, nseg, dstart_t - 1 - m, m);
+        par = src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status) ? ws.slice_pos[src] : -1;
+      }
+    }
+    a.parent[e] = par;
+    a.match[e] = k == K_CLOSE ? par : -1;
+  }
+  __syncthreads();  // the opens' placeholders are written before their closes' matches
+  for (int i = 0; i < KPT; ++i) {
+    const int p = i * NT + tid;
+    if (p >= cnt) break;
+    const int e = base + p;
+    if (a.kind[e] != K_CLOSE) continue;
+    const int d = s_tree[TILE + p];
+    const int q = tree_last_le(s_tree, TILE, p, d - 1);
+    if (q >= 0) {
+      a.match[base + q] = e;
+    } else if (in_range(-d, 0, TILE, ws.status)) {
+      ws.cpos[(size_t)t * TILE + (-d)] = e;
+      ws.cval[(size_t)t * TILE + (-d)] = e;
+    }
+  }
 }
 
 // ------------------------------------------------------------------- K4

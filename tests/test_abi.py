@@ -166,8 +166,9 @@ def test_phase_event_count_limits(lib):
 
 def test_tuned_shape_is_a_candidate():
     from paper_2205_11659_gb300 import _build, autotune
-    assert _build.tuned_shape() + (_build.tuned_persistent(),) in autotune.CANDIDATES
-    assert (256, 16, False) in autotune.CANDIDATES
+    assert _build.tuned_shape() + (_build.tuned_persistent(), _build.tuned_matcher()) \
+        in autotune.CANDIDATES
+    assert (256, 16, False, 0) in autotune.CANDIDATES and (128, 16, False, 1) in autotune.CANDIDATES
 
 
 def test_static_scratch_argument_errors(lib):

@@ -333,3 +333,36 @@ def test_wide_scene_unions(n):
     k = inputs.random_walk_kinds(n, 900 + n)
     b = inputs.scene_boxes(k, 901 + n, center_hi=1e6, leaf_wh=(1.0, 4.0), clip_wh=(1.5e6, 3e6))
     assert_bboxes_equal(k, b)
+
+
+def test_graph_capture_replays_the_pass():
+    """The whole pass (its cooperative launch included) captured in a CUDA
+    graph and replayed gives the plain call's outputs, on new inputs too."""
+    k1, b1 = inputs.random_walk_scene(5 * TILE + 3, 41)
+    k2, b2 = inputs.random_walk_scene(5 * TILE + 3, 42)
+    kd = torch.from_numpy(k1).cuda()
+    bd = torch.from_numpy(b1).cuda()
+    n = k1.size
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    match = torch.empty(n, dtype=torch.int32, device="cuda")
+    out = torch.empty(n, 4, dtype=torch.float32, device="cuda")
+    nb = binding.tb_workspace_size(binding.TB_OP_BBOXES, n)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        assert binding.tb_bboxes(kd, bd, n, parent, match, out, ws, nb, st, s) == binding.TB_OK
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rc = binding.tb_bboxes(kd, bd, n, parent, match, out, ws, nb, st, None)
+    assert rc == binding.TB_OK
+    for k, b in ((k1, b1), (k2, b2)):
+        kd.copy_(torch.from_numpy(k))
+        bd.copy_(torch.from_numpy(b))
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(st.item()) == binding.TB_OK
+        s_, op, om, ob = oracle.bboxes(k, b)
+        assert np.array_equal(parent.cpu().numpy(), op) and np.array_equal(match.cpu().numpy(), om)
+        assert same_bits(out.cpu().numpy(), ob)
