@@ -242,7 +242,7 @@ tb_status tb_set_phase_events(void* const* events, int num_events);
  * counterpart; it is an interface convenience.
  *
  * Same results as tb_bboxes, but the scratch is a file-scope device array of
- * the library (9 MiB, held by every GPU that loads the library until the
+ * the library (5 MiB, held by every GPU that loads the library until the
  * process exits), so there is no ws argument.  The caller still passes the
  * inputs and outputs (d_status included).
  *  - n may be at most TB_STATIC_WS_MAX_N; larger n returns TB_ERR_WORKSPACE

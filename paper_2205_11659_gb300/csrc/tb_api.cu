@@ -31,8 +31,9 @@ constexpr int next_pow2(int x) {
 struct Layout {
   size_t counter, t_a, t_b, t_tot, t_dstart, t_lo, t_ps, t_q, lo_tree, t_link0, t_link1, t_val0,
       t_val1, t_B, t_uall, uall_tree, slice_pos, slice_rel, usuf, upre, cpos, cval, t_seg, t_nseg,
-      t_cont, ctx_src, total;
+      t_cont, ctx_src, t_boff, t_aoff, total;
   int T, P;
+  int64_t cap;
 };
 
 constexpr Layout scene_layout(int64_t n, bool has_box) {
@@ -41,7 +42,12 @@ constexpr Layout scene_layout(int64_t n, bool has_box) {
   const int P = next_pow2(T > 0 ? T : 1);
   L.T = T;
   L.P = P;
-  const size_t t4 = (size_t)T * 4, t16 = (size_t)T * 16, slots = (size_t)T * TILE;
+  // Slots of the tiles' slices (unmatched opens) and of their closes that
+  // match earlier tiles: at most n / 2 of each in a balanced stream (every
+  // one pairs with a distinct element of the other side).
+  const int64_t cap = n / 2 + 1;
+  L.cap = cap;
+  const size_t t4 = (size_t)T * 4, t16 = (size_t)T * 16, slots = (size_t)cap;
   size_t o = 0;
   auto take = [&o](size_t bytes) {
     const size_t at = o;
@@ -63,7 +69,9 @@ constexpr Layout scene_layout(int64_t n, bool has_box) {
   L.t_seg = take((size_t)T * SEGK * 16);
   L.t_nseg = take(t4);
   L.t_cont = take((size_t)T * 8);
-  L.ctx_src = take((size_t)T * (TILE + 1) * 4);
+  L.ctx_src = take(((size_t)cap + T) * 4);
+  L.t_boff = take(t4);
+  L.t_aoff = take(t4);
   if (has_box) {
     L.t_link0 = take(t4);
     L.t_link1 = take(t4);
@@ -99,6 +107,9 @@ SceneWs scene_ws(const Layout& L, void* ws, bool has_box) {
   w.t_nseg = reinterpret_cast<int*>(b + L.t_nseg);
   w.t_cont = reinterpret_cast<int2*>(b + L.t_cont);
   w.ctx_src = reinterpret_cast<int*>(b + L.ctx_src);
+  w.t_boff = reinterpret_cast<int*>(b + L.t_boff);
+  w.t_aoff = reinterpret_cast<int*>(b + L.t_aoff);
+  w.slot_cap = L.cap;
   if (has_box) {
     w.t_link[0] = reinterpret_cast<int*>(b + L.t_link0);
     w.t_link[1] = reinterpret_cast<int*>(b + L.t_link1);
@@ -386,7 +397,7 @@ int withheld_tile() { return g_withhold; }
 // the module image: every GPU that loads the library holds it until exit.
 namespace {
 
-constexpr size_t kStaticWsBytes = (size_t)9 << 20;  // 9 MiB
+constexpr size_t kStaticWsBytes = (size_t)5 << 20;  // 5 MiB
 static_assert(scene_layout(TB_STATIC_WS_MAX_N, true).total <= kStaticWsBytes,
               "the static scratch must hold the workspace of TB_STATIC_WS_MAX_N elements");
 

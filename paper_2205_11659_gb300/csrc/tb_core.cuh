@@ -307,16 +307,24 @@ __device__ __forceinline__ T tree_range(const T* tree, int P, int l, int r, T id
 //                lo <= t_dstart - 1), -1 if none
 //   t_B          clip in force at depth t_lo - 1 at the tile start
 //   t_uall       union of all canonical leaf boxes of the tile
-// Per tile and slot s < TILE (slot s = depth t_lo + s):
+// Per tile and slot s < t_b (slot s = depth t_lo + s), at t_boff[t] + s in
+// the open-side arrays (a tile's range is taken from a counter when its
+// summary is written; slot_cap entries in all, enough for any balanced
+// stream):
 //   slice_pos    global index of the tile's unmatched open at that depth
 //                (the tile's stack slice, Sec. 7.1)
 //   slice_rel    intersection of the clip boxes of the slice up to slot s
 //   usuf         union of the tile's leaves after that open
-// Per tile and m < t_a (the close that pops depth t_dstart - 1 - m):
+// A slice entry is named by its "source" u * TILE + s (owner tile u, slot
+// s); slice_at() turns that into the array index.
+// Per tile and m < t_a (the close that pops depth t_dstart - 1 - m), at
+// t_aoff[t] + m in the close-side arrays (t_aoff = exclusive scan of t_a):
 //   upre         union of the tile's leaves before that close
 //   cpos         global index of that close
+// ctx_src rows (tiles whose owner segments overflow) hold t_a + 1 sources
+// from t_aoff[t] + t.
 struct SceneWs {
-  unsigned* counter;  // [1]: tile ticket of the persistent main pass
+  unsigned* counter;  // [1]: tile ticket of the persistent main pass; [2]: slice slots taken
   int* t_a;
   int* t_b;
   int* t_tot;         // per tile: depth change over the tile
@@ -341,10 +349,20 @@ struct SceneWs {
   int4* t_seg;       // per tile SEGK owner segments of the stack at its start
   int* t_nseg;       // segment count, or SEGK + 1 when the chain continues
   int2* t_cont;      // continuation (owner, depth) when t_nseg = SEGK + 1
-  int* ctx_src;      // per tile (TILE + 1): context sources, for tiles whose chain overflows
+  int* ctx_src;      // per tile (t_a + 1): context sources, for tiles whose chain overflows
+  int* t_boff;       // per tile: first open-side slot of its slice (-1: none taken)
+  int* t_aoff;       // per tile: first close-side slot
+  long long slot_cap;  // open-side and close-side slots available
   int T;
   int P;
 };
+
+// Array index of slice entry `src` (owner tile * TILE + slot); debug builds
+// check it (and read entry 0 instead of an index outside the arrays).
+__device__ __forceinline__ long long slice_at(const SceneWs& ws, int src) {
+  const long long i = (long long)ws.t_boff[src / TILE] + (src % TILE);
+  return in_range(i, 0, ws.slot_cap, ws.status) ? i : 0;
+}
 
 // Owner segments precomputed per tile by the tile-level resolve: segment j
 // of tile t is {owner tile u (-1 below the root), u's lowest depth, lowest

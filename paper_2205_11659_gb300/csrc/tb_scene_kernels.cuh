@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
   __shared__ int s_scr[NW + 1];
   __shared__ int2 s_scr2[NW + 1];
   __shared__ float4 s_fscr[NW + 1];
+  __shared__ int s_boff;
   const int tid = threadIdx.x;
   const int t = blockIdx.x;
   const int base = t * TILE, p0 = tid * KPT;
@@ -99,13 +100,14 @@ __global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
   uint8_t kk[KPT];
   if (load_kinds(a.kind, a.n, base + p0, kk)) atomic_cas_i32(a.status, ST_OK, ST_BAD_KIND);
 
-  // Chunk depth profile relative to the chunk start.
-  int rr[KPT];
+  // Chunk depth profile relative to the chunk start (the kinds are kept
+  // packed, 4 bits each, to hold fewer registers while the scans run).
+  unsigned long long kp = 0;
   int r = 0, mn = 0, mn_after = INT_MAX;
 #pragma unroll
   for (int i = 0; i < KPT; ++i) {
+    kp |= (unsigned long long)kk[i] << (4 * i);
     r += kind_delta(kk[i]);
-    rr[i] = r;
     mn = mn < r ? mn : r;
     mn_after = mn_after < r ? mn_after : r;
   }
@@ -118,12 +120,25 @@ __global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
   const int tile_lo = tot2.y;
   const int a_t = -tile_lo;  // Bic(tile).a: closes that pop below the tile start
   const int b_t = tot + a_t;  // Bic(tile).b: opens left unmatched at the tile end
-  const int suf_after = block_excl_suffix_min(ds + mn_after, s_scr);
   if (tid == 0) {
     a.ws.t_a[t] = a_t;
     a.ws.t_b[t] = b_t;
     a.ws.t_tot[t] = tot;
+    // slots of the tile's slice in the open-side arrays, taken from a
+    // counter (the order of the tiles' ranges does not matter); a balanced
+    // stream needs at most slot_cap of them (every unmatched open has its
+    // own close in a later tile), so running out means an unbalanced one
+    int off = (int)atomic_add_u32(a.ws.counter + 2, (unsigned)b_t);
+    if ((long long)off + b_t > a.ws.slot_cap) {
+      atomic_cas_i32(a.status, ST_OK, ST_UNBALANCED);
+      off = -1;
+    }
+    a.ws.t_boff[t] = off;
+    s_boff = off;
   }
+  const int suf_after = block_excl_suffix_min(ds + mn_after, s_scr);  // (its barriers publish s_boff)
+  const int boff = s_boff;
+  if (boff < 0) return;  // the same value for the whole block
 
   // The tile's stack slice: an open is unmatched in the tile when the depth
   // never comes back below its level before the tile ends.  Its slot is its
@@ -135,26 +150,23 @@ __global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
   int first_slot = 0;
   {
     int suf = suf_after;
+    int A = ds + r;  // depth after element i, walking back from the chunk end
 #pragma unroll
     for (int i = KPT - 1; i >= 0; --i) {
-      const int A = ds + rr[i];
+      const int k = (int)((kp >> (4 * i)) & 15ull);
       suf = suf < A ? suf : A;
-      if (kk[i] == K_CLIP) clipm |= 1u << i;
-      if (kind_open(kk[i]) && A <= suf) {
+      if (k == K_CLIP) clipm |= 1u << i;
+      if (kind_open(k) && A <= suf) {
         umt |= 1u << i;
         first_slot = A - 1 + a_t;
       }
+      A -= k == K_PAD ? 0 : kind_delta(k);
     }
   }
-  int* slice_pos = a.ws.slice_pos + (size_t)t * TILE;
-  if (HAS_BOX) {
+  int* slice_pos = a.ws.slice_pos + boff;
+  {
     int slot = first_slot;
     for (unsigned m = umt; m; m &= m - 1, ++slot) slice_pos[slot] = base + p0 + lowest_set(m);
-  } else {
-    // (the matching-only pass measured slightly faster with the unrolled form)
-#pragma unroll
-    for (int i = 0; i < KPT; ++i)
-      if ((umt >> i) & 1u) slice_pos[ds + rr[i] - 1 + a_t] = base + p0 + i;
   }
 
   if (HAS_BOX) {
@@ -165,7 +177,7 @@ __global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
       loc = box_isect(loc, ld_nc_f4(a.box + base + p0 + lowest_set(m)));
     float4 tot4;
     float4 acc = block_excl_scan(loc, box_universe(), OpIsect(), s_fscr, &tot4);
-    float4* slice_rel = a.ws.slice_rel + (size_t)t * TILE;
+    float4* slice_rel = a.ws.slice_rel + boff;
     int slot = first_slot;
     for (unsigned m = umt; m; m &= m - 1, ++slot) {
       const int i = lowest_set(m);
@@ -189,6 +201,7 @@ constexpr int NT2 = 1024;
 __global__ void __launch_bounds__(NT2) k1_tile_prefix(SceneWs ws, int* status) {
   constexpr int NWP = NT2 / 32;
   __shared__ int s_w[NWP];
+  __shared__ int s_wa[NWP];
   __shared__ int s_top[2 * NT2];
   const int T = ws.T, P = ws.P, tid = threadIdx.x, lane = lane_id(), wid = warp_id();
   int* tree = ws.lo_tree;
@@ -198,26 +211,38 @@ __global__ void __launch_bounds__(NT2) k1_tile_prefix(SceneWs ws, int* status) {
   const int rounds = base < P ? span / 32 : 0;  // warp-uniform
   // the warp's total depth change (RB rounds of loads in flight at a time)
   constexpr int RB = 4;
-  int sum = 0;
+  int sum = 0, suma = 0;
   for (int r0 = 0; r0 < rounds; r0 += RB) {
 #pragma unroll
     for (int k = 0; k < RB; ++k) {
       const int t = base + (r0 + k) * 32 + lane;
-      if (r0 + k < rounds && t < T) sum += __ldg(ws.t_tot + t);
+      if (r0 + k < rounds && t < T) {
+        sum += __ldg(ws.t_tot + t);
+        suma += __ldg(ws.t_a + t);
+      }
     }
   }
 #pragma unroll
-  for (int m = 16; m >= 1; m >>= 1) sum += shfl_xor(sum, m);
-  if (lane == 0) s_w[wid] = sum;
+  for (int m = 16; m >= 1; m >>= 1) {
+    sum += shfl_xor(sum, m);
+    suma += shfl_xor(suma, m);
+  }
+  if (lane == 0) {
+    s_w[wid] = sum;
+    s_wa[wid] = suma;
+  }
   __syncthreads();
   if (wid == 0) {
     const int v = s_w[lane];
     const int incl = warp_incl_scan(v, OpAdd());
     s_w[lane] = incl - v;  // exclusive prefix of the warps
     if (lane == NWP - 1 && incl != 0) atomic_cas_i32(status, ST_OK, ST_UNBALANCED);  // ends above 0
+    const int va0 = s_wa[lane];
+    s_wa[lane] = warp_incl_scan(va0, OpAdd()) - va0;
   }
   __syncthreads();
   int carry = s_w[wid];
+  int carry_a = s_wa[wid];  // offsets of the tiles' unmatched closes in the close-side arrays
   bool bad = false;
   for (int r0 = 0; r0 < rounds; r0 += RB) {
     int vt[RB], va[RB];
@@ -234,15 +259,18 @@ __global__ void __launch_bounds__(NT2) k1_tile_prefix(SceneWs ws, int* status) {
         const int t = base + (r0 + k) * 32 + lane;
         const int incl = warp_incl_scan(vt[k], OpAdd());
         const int excl = carry + incl - vt[k];
+        const int incla = warp_incl_scan(va[k], OpAdd());
         int v = 0x7f7f7f7f;  // past the last tile: above any depth
         if (t < T) {
           v = excl - va[k];
           ws.t_dstart[t] = excl;
           ws.t_lo[t] = v;
+          ws.t_aoff[t] = carry_a + incla - va[k];
           bad |= v < 0;  // a close pops below the root
         }
         if (t < P) tree[P + t] = v;
         carry += shfl_idx(incl, 31);
+        carry_a += shfl_idx(incla, 31);
 #pragma unroll
         for (int l = 1; l <= 5; ++l) {
           v = min(v, shfl_xor(v, 1 << (l - 1)));
@@ -324,7 +352,7 @@ __global__ void __launch_bounds__(NTR) k2_segments(SceneWs ws) {
     float4 v = box_universe();
     int l = -1;
     if (lo - 1 >= 0 && p >= 0 && in_range(lo - 1 - ws.t_lo[p], 0, TILE, ws.status)) {
-      v = ws.slice_rel[(size_t)p * TILE + (lo - 1 - ws.t_lo[p])];
+      v = ws.slice_rel[slice_at(ws, p * TILE + (lo - 1 - ws.t_lo[p]))];
       l = p;
     }
     ws.t_val[0][u] = v;
@@ -369,7 +397,7 @@ __global__ void __launch_bounds__(NTJ) k2_jump(SceneWs ws, int rounds) {
 // m = dstart - 1 - gd, at the start of tile t; -1 below the root.
 __device__ __forceinline__ int ctx_src_of(const SceneWs& ws, int t, bool ovf, const int4* seg,
                                           int nseg, int gd, int m) {
-  if (ovf) return (m >= 0 && m <= TILE) ? ws.ctx_src[(size_t)t * (TILE + 1) + m] : -1;
+  if (ovf) return (m >= 0 && m <= ws.t_a[t]) ? ws.ctx_src[(size_t)ws.t_aoff[t] + t + m] : -1;
   const int s = segk_find(seg, nseg, gd);
   if (s < 0 || seg[s].x < 0) return -1;
   return seg[s].x * TILE + (gd - seg[s].y);
@@ -382,7 +410,7 @@ __device__ __forceinline__ int ctx_src_of(const SceneWs& ws, int t, bool ovf, co
 __device__ __forceinline__ void fill_ctx_overflow(SegState& S, const SceneWs& ws, int t,
                                                   int dstart, int count, const int4* seg) {
   const int tid = threadIdx.x;
-  int* row = ws.ctx_src + (size_t)t * (TILE + 1);
+  int* row = ws.ctx_src + (size_t)ws.t_aoff[t] + t;
   const int covered_lo = seg[SEGK - 1].z;
   for (int m = tid; m < count; m += NT) {
     const int d = dstart - 1 - m;
@@ -594,9 +622,9 @@ __device__ __forceinline__ OutRes out_lookup(const OutCtx& c, const SceneWs& ws,
     } else {
       int src = ctx_src_of(ws, c.t, c.ovf != 0, c.s_seg, c.nseg, c.dstart_t - 1 - m, m);
       if (src >= 0 && !in_range(src, 0, (long long)ws.T * TILE, ws.status)) src = -1;
-      r.par = src >= 0 ? ws.slice_pos[src] : -1;
+      r.par = src >= 0 ? ws.slice_pos[slice_at(ws, src)] : -1;
       if (HAS_BOX && want_clip && src >= 0)
-        r.cx = box_isect(ws.t_B[src / TILE], ws.slice_rel[src]);
+        r.cx = box_isect(ws.t_B[src / TILE], ws.slice_rel[slice_at(ws, src)]);
     }
   }
   return r;
@@ -694,8 +722,9 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
         }
       }
       if (src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status)) {
-        ctx_i = ws.slice_pos[src];
-        if (HAS_BOX) ctx_c = box_isect(ws.t_B[src / TILE], ws.slice_rel[src]);
+        const long long si = slice_at(ws, src);
+        ctx_i = ws.slice_pos[si];
+        if (HAS_BOX) ctx_c = box_isect(ws.t_B[src / TILE], ws.slice_rel[si]);
       }
     }
   }
@@ -776,8 +805,9 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   if (ctx_mine && !ctx_early) {
     const int src = ctx_src_of(ws, t, ovf, s_seg, nseg, dstart_t - 1 - tid, tid);
     if (src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status)) {
-      ctx_i = ws.slice_pos[src];
-      if (HAS_BOX) ctx_c = box_isect(ws.t_B[src / TILE], ws.slice_rel[src]);
+      const long long si = slice_at(ws, src);
+      ctx_i = ws.slice_pos[si];
+      if (HAS_BOX) ctx_c = box_isect(ws.t_B[src / TILE], ws.slice_rel[si]);
     }
   }
 
@@ -849,7 +879,7 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
       } else {
         const int src = ctx_src_of(ws, t, ovf, s_seg, nseg, dstart_t - 1 - m, m);
         v = src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status)
-                ? box_isect(ws.t_B[src / TILE], ws.slice_rel[src]) : box_universe();
+                ? box_isect(ws.t_B[src / TILE], ws.slice_rel[slice_at(ws, src)]) : box_universe();
       }
       link = -1;
     }
@@ -1077,9 +1107,9 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
       if (u >= 0) {
         const int si = u * KPT + (dd - s_lo[u]);
         if (a.match && in_range(si, 0, TILE, ws.status)) a.match[base + s_spos[si]] = eo;
-      } else if (in_range(-1 - dd, 0, TILE, ws.status)) {
-        ws.cpos[(size_t)t * TILE + (-1 - dd)] = e;
-        ws.cval[(size_t)t * TILE + (-1 - dd)] = eo;
+      } else if (in_range(-1 - dd, 0, a_t, ws.status)) {
+        ws.cpos[(size_t)ws.t_aoff[t] + (-1 - dd)] = e;
+        ws.cval[(size_t)ws.t_aoff[t] + (-1 - dd)] = eo;
       }
     }
     K3_TILE_DONE;
@@ -1146,11 +1176,11 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
         s_box[box_slot(op)] = U;
         s_box[box_slot(cp)] = U;
         if (a.match) a.match[idx] = eo;
-      } else if (in_range(m - ds, 0, TILE, ws.status)) {
-        const int mm = m - ds;  // below the tile start: its k4 pass finishes the pair
-        ws.upre[(size_t)t * TILE + mm] = U;
-        ws.cpos[(size_t)t * TILE + mm] = e;
-        ws.cval[(size_t)t * TILE + mm] = eo;
+      } else if (in_range(m - ds, 0, a_t, ws.status)) {
+        const size_t mm = (size_t)ws.t_aoff[t] + (m - ds);  // below the tile start: k4 finishes the pair
+        ws.upre[mm] = U;
+        ws.cpos[mm] = e;
+        ws.cval[mm] = eo;
       }
       u_prev = u;
     }
@@ -1163,7 +1193,7 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
       const int i = lowest_set(m);
       m &= m - 1;
       if (dd < later_lo)
-        ws.usuf[(size_t)t * TILE + dd + a_t] = box_unite(s_box[box_slot(p0 + i)], rest);
+        ws.usuf[(size_t)ws.t_boff[t] + dd + a_t] = box_unite(s_box[box_slot(p0 + i)], rest);
       ++dd;
     }
   }
@@ -1239,7 +1269,7 @@ __global__ void __launch_bounds__(NT) k3_search(K3Args a) {
   if (ovf) fill_ctx_overflow(S, ws, t, dstart_t, a_t + 1, s_seg);
   if (tid < CTXC && tid <= a_t) {
     const int src = ctx_src_of(ws, t, ovf, s_seg, nseg, dstart_t - 1 - tid, tid);
-    s_cidx[tid] = src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status) ? ws.slice_pos[src] : -1;
+    s_cidx[tid] = src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status) ? ws.slice_pos[slice_at(ws, src)] : -1;
   }
   __syncthreads();
   for (int h = TILE / 2; h >= 1; h >>= 1) {
@@ -1264,7 +1294,7 @@ __global__ void __launch_bounds__(NT) k3_search(K3Args a) {
         par = m <= a_t ? s_cidx[m] : -1;
       } else {
         const int src = ctx_src_of(ws, t, ovf, s_seg, nseg, dstart_t - 1 - m, m);
-        par = src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status) ? ws.slice_pos[src] : -1;
+        par = src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status) ? ws.slice_pos[slice_at(ws, src)] : -1;
       }
     }
     a.parent[e] = par;
@@ -1280,9 +1310,9 @@ __global__ void __launch_bounds__(NT) k3_search(K3Args a) {
     const int q = tree_last_le(s_tree, TILE, p, d - 1);
     if (q >= 0) {
       a.match[base + q] = e;
-    } else if (in_range(-d, 0, TILE, ws.status)) {
-      ws.cpos[(size_t)t * TILE + (-d)] = e;
-      ws.cval[(size_t)t * TILE + (-d)] = e;
+    } else if (in_range(-d, 0, a_t, ws.status)) {
+      ws.cpos[(size_t)ws.t_aoff[t] + (-d)] = e;
+      ws.cval[(size_t)ws.t_aoff[t] + (-d)] = e;
     }
   }
 }
@@ -1361,22 +1391,24 @@ __global__ void __launch_bounds__(NT) k4_cross_tile_unions(K4Args a) {
     const int d = dstart - 1 - m;
     int src, s = -1;
     if (ovf) {
-      src = ws.ctx_src[(size_t)t * (TILE + 1) + m];
+      src = ws.ctx_src[(size_t)ws.t_aoff[t] + t + m];
     } else {
       s = segk_find(s_seg, nseg, d);
       src = (s >= 0 && s_seg[s].x >= 0) ? s_seg[s].x * TILE + (d - s_seg[s].y) : -1;
     }
     if (src < 0) continue;  // unbalanced input
     if (!in_range(src, 0, (long long)ws.T * TILE, ws.status)) continue;
-    const int o = ws.slice_pos[src];
+    const long long si = slice_at(ws, src);
+    const int o = ws.slice_pos[si];
     if (!in_range(o, 0, (long long)ws.T * TILE, ws.status)) continue;
-    if (a.match) a.match[o] = ws.cval[(size_t)t * TILE + m];
+    const size_t cm = (size_t)ws.t_aoff[t] + m;
+    if (a.match) a.match[o] = ws.cval[cm];
     if (HAS_BOX) {
       const int u = src / TILE;
       const float4 mid = ovf ? tree_range(ws.uall_tree, ws.P, u + 1, t - 1, box_empty(), OpUnite())
                              : s_mid[s];
-      const int c = ws.cpos[(size_t)t * TILE + m];
-      const float4 U = box_unite(box_unite(ws.usuf[src], mid), ws.upre[(size_t)t * TILE + m]);
+      const int c = ws.cpos[cm];
+      const float4 U = box_unite(box_unite(ws.usuf[si], mid), ws.upre[cm]);
       a.box_out[o] = U;
       if (in_range(c, 0, (long long)ws.T * TILE, ws.status)) a.box_out[c] = U;
     }

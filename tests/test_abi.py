@@ -51,8 +51,14 @@ def test_workspace_size(lib):
     m2 = b.tb_workspace_size(b.TB_OP_MATCH_PARENS, 1 << 20)
     assert 0 < s1 < s2 and 0 < m2 < s2
     assert b.tb_workspace_size(b.TB_OP_BBOXES_BATCHED, 1 << 20, 7) == s2
-    # workspace grows linearly in the number of tiles
+    # workspace grows linearly in n
     assert b.tb_workspace_size(b.TB_OP_BBOXES, 1 << 22) < 4.5 * s2
+    # slots for the unmatched elements a balanced stream can have (n / 2 per
+    # side), not for every element of every tile: below the 41 bytes per
+    # element of the pass's own inputs and outputs
+    big = 1 << 26
+    assert b.tb_workspace_size(b.TB_OP_BBOXES, big) < 33 * big
+    assert b.tb_workspace_size(b.TB_OP_MATCH_PARENS, big) < 9 * big
     t2 = b.tb_workspace_size(b.TB_OP_TREE_SCAN, 1 << 20)
     g2 = b.tb_workspace_size(b.TB_OP_TREE_BACKWARD, 1 << 20)
     assert m2 < t2 < g2

@@ -166,6 +166,19 @@ def test_error_statuses():
     kk = np.array([1, 0, 0, 3, 1, 0, 3, 0], np.uint8)
     off = np.array([0, 6, 8], np.int64)
     assert status_of(kk, inputs.scene_boxes(kk, 0), off) == binding.TB_ERR_UNBALANCED
+    # more unmatched opens than a balanced stream can have: the slice slots
+    # (sized for balanced streams) run out, which is reported, not overrun
+    for kk in (np.ones(40_001, np.uint8), np.full(40_001, 2, np.uint8),
+               np.concatenate([np.ones(30_000, np.uint8), np.full(10_000, 3, np.uint8)])):
+        assert status_of(kk, inputs.scene_boxes(kk, 3)) == binding.TB_ERR_UNBALANCED
+        try:
+            binding.match_parens(torch.from_numpy(kk).cuda())
+        except binding.TBError as e:
+            assert e.code == binding.TB_ERR_UNBALANCED
+        else:
+            raise AssertionError("unbalanced stream accepted by the matching pass")
+    assert status_of(np.full(40_001, 3, np.uint8), np.zeros((40_001, 4), np.float32)) \
+        == binding.TB_ERR_UNBALANCED
     # a clean call after errors still works
     assert_bboxes_equal(k, b)
 
