@@ -31,7 +31,7 @@ constexpr int next_pow2(int x) {
 struct Layout {
   size_t counter, t_a, t_b, t_tot, t_dstart, t_lo, t_ps, t_q, lo_tree, t_link0, t_link1, t_val0,
       t_val1, t_B, t_uall, uall_tree, slice_pos, slice_rel, usuf, upre, cpos, cval, t_seg, t_nseg,
-      t_cont, ctx_src, t_boff, t_aoff, total;
+      t_cont, ctx_src, t_boff, t_aoff, t_segb, total;
   int T, P;
   int64_t cap;
 };
@@ -67,6 +67,7 @@ constexpr Layout scene_layout(int64_t n, bool has_box) {
   L.cpos = take(slots * 4);
   L.cval = take(slots * 4);
   L.t_seg = take((size_t)T * SEGK * 16);
+  L.t_segb = take((size_t)T * SEGK * 4);
   L.t_nseg = take(t4);
   L.t_cont = take((size_t)T * 8);
   L.ctx_src = take(((size_t)cap + T) * 4);
@@ -104,6 +105,7 @@ SceneWs scene_ws(const Layout& L, void* ws, bool has_box) {
   w.cpos = reinterpret_cast<int*>(b + L.cpos);
   w.cval = reinterpret_cast<int*>(b + L.cval);
   w.t_seg = reinterpret_cast<int4*>(b + L.t_seg);
+  w.t_segb = reinterpret_cast<int*>(b + L.t_segb);
   w.t_nseg = reinterpret_cast<int*>(b + L.t_nseg);
   w.t_cont = reinterpret_cast<int2*>(b + L.t_cont);
   w.ctx_src = reinterpret_cast<int*>(b + L.ctx_src);

@@ -347,6 +347,8 @@ struct SceneWs {
   int* cpos;
   int* cval;         // per tile and m: value match[open] receives (scene-local close)
   int4* t_seg;       // per tile SEGK owner segments of the stack at its start
+  int* t_segb;       // per tile and segment: t_boff[owner] - owner's lowest depth (array
+                     // index of the slice entry at global depth d = d + this)
   int* t_nseg;       // segment count, or SEGK + 1 when the chain continues
   int2* t_cont;      // continuation (owner, depth) when t_nseg = SEGK + 1
   int* ctx_src;      // per tile (t_a + 1): context sources, for tiles whose chain overflows

@@ -337,6 +337,7 @@ __global__ void __launch_bounds__(NTR) k2_segments(SceneWs ws) {
     }
     const int lo_o = ws.t_lo[own];
     const int lo_s = lo_o > dbot ? lo_o : dbot;
+    ws.t_segb[(size_t)u * SEGK + n] = ws.t_boff[own] - lo_o;
     seg[n++] = make_int4(own, lo_o, lo_s, dtop);
     dtop = lo_s - 1;
     own = ws.t_ps[own];
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(NTR) k2_segments(SceneWs ws) {
     float4 v = box_universe();
     int l = -1;
     if (lo - 1 >= 0 && p >= 0 && in_range(lo - 1 - ws.t_lo[p], 0, TILE, ws.status)) {
-      v = ws.slice_rel[slice_at(ws, p * TILE + (lo - 1 - ws.t_lo[p]))];
+      v = ws.slice_rel[(size_t)ws.t_boff[p] + (lo - 1 - ws.t_lo[p])];
       l = p;
     }
     ws.t_val[0][u] = v;
@@ -401,6 +402,27 @@ __device__ __forceinline__ int ctx_src_of(const SceneWs& ws, int t, bool ovf, co
   const int s = segk_find(seg, nseg, gd);
   if (s < 0 || seg[s].x < 0) return -1;
   return seg[s].x * TILE + (gd - seg[s].y);
+}
+
+// The stack entry at global depth gd, m = dstart - 1 - gd, at the start of
+// tile t: its owner tile *u and its index *idx in the open-side arrays;
+// false below the root.  segb holds the segments' index bases (t_segb).
+__device__ __forceinline__ bool ctx_entry(const SceneWs& ws, int t, bool ovf, const int4* seg,
+                                          const int* segb, int nseg, int gd, int m, int* u,
+                                          long long* idx) {
+  if (ovf) {
+    const int src = ctx_src_of(ws, t, true, seg, nseg, gd, m);
+    if (src < 0 || !in_range(src, 0, (long long)ws.T * TILE, ws.status)) return false;
+    *u = src / TILE;
+    *idx = slice_at(ws, src);
+    return true;
+  }
+  const int s = segk_find(seg, nseg, gd);
+  if (s < 0 || seg[s].x < 0) return false;
+  *u = seg[s].x;
+  const long long i = (long long)gd + segb[s];
+  *idx = in_range(i, 0, ws.slot_cap, ws.status) ? i : 0;
+  return true;
 }
 
 // For a tile whose owner chain has more than SEGK segments: writes the
@@ -592,6 +614,7 @@ struct OutCtx {
   const int* s_cidx;
   const float4* s_cclip;
   const int4* s_seg;
+  const int* s_segb;
   int nseg, ovf, t, dstart_t, base;
 };
 struct OutRes {
@@ -620,11 +643,12 @@ __device__ __forceinline__ OutRes out_lookup(const OutCtx& c, const SceneWs& ws,
       r.par = c.s_cidx[m];
       if (HAS_BOX && want_clip) r.cx = c.s_cclip[m];
     } else {
-      int src = ctx_src_of(ws, c.t, c.ovf != 0, c.s_seg, c.nseg, c.dstart_t - 1 - m, m);
-      if (src >= 0 && !in_range(src, 0, (long long)ws.T * TILE, ws.status)) src = -1;
-      r.par = src >= 0 ? ws.slice_pos[slice_at(ws, src)] : -1;
-      if (HAS_BOX && want_clip && src >= 0)
-        r.cx = box_isect(ws.t_B[src / TILE], ws.slice_rel[slice_at(ws, src)]);
+      int u;
+      long long idx;
+      const bool found = ctx_entry(ws, c.t, c.ovf != 0, c.s_seg, c.s_segb, c.nseg,
+                                   c.dstart_t - 1 - m, m, &u, &idx);
+      r.par = found ? ws.slice_pos[idx] : -1;
+      if (HAS_BOX && want_clip && found) r.cx = box_isect(ws.t_B[u], ws.slice_rel[idx]);
     }
   }
   return r;
@@ -642,6 +666,7 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   TB_DYNAMIC_SMEM(smem);
   __shared__ int s_scr[NW + 1];
   __shared__ int4 s_seg[SEGK];
+  __shared__ int s_segb[SEGK];
   __shared__ int s_info[3];
   __shared__ int s_stop;
   __shared__ int s_cidx[CTXC];
@@ -699,7 +724,10 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
     s_info[1] = ws.t_dstart[t];
     s_info[2] = ws.t_nseg[t];
   }
-  if (tid < SEGK) s_seg[tid] = ws.t_seg[(size_t)t * SEGK + tid];
+  if (tid < SEGK) {
+    s_seg[tid] = ws.t_seg[(size_t)t * SEGK + tid];
+    s_segb[tid] = ws.t_segb[(size_t)t * SEGK + tid];
+  }
   // The tile context's top CTXC entries are the longest chain of dependent
   // loads (tile info, owner segments, slice entry, clips): warp 0 issues them
   // first, reading the tile info and segments itself, so that they overlap
@@ -713,18 +741,19 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
     ctx_early = ns0 <= SEGK;
     if (ctx_early && tid <= a0) {
       const int gd = d0 - 1 - tid;
-      int src = -1;
+      int u = -1;
+      long long si = 0;
       for (int i = 0; i < ns0; ++i) {
         const int4 sg = ws.t_seg[(size_t)t * SEGK + i];
         if (gd >= sg.z && gd <= sg.w) {
-          src = sg.x >= 0 ? sg.x * TILE + (gd - sg.y) : -1;
+          u = sg.x;
+          si = (long long)gd + ws.t_segb[(size_t)t * SEGK + i];
           break;
         }
       }
-      if (src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status)) {
-        const long long si = slice_at(ws, src);
+      if (u >= 0 && in_range(si, 0, ws.slot_cap, ws.status)) {
         ctx_i = ws.slice_pos[si];
-        if (HAS_BOX) ctx_c = box_isect(ws.t_B[src / TILE], ws.slice_rel[si]);
+        if (HAS_BOX) ctx_c = box_isect(ws.t_B[u], ws.slice_rel[si]);
       }
     }
   }
@@ -796,6 +825,9 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   }
   const int a_t = s_info[0], dstart_t = s_info[1], nseg = s_info[2];
   const bool ovf = nseg > SEGK;
+  // first close-side and open-side slots of the tile, read once (the stores
+  // into the slot arrays would otherwise make the compiler reload them)
+  const size_t aoff_t = (size_t)ws.t_aoff[t], boff_t = (size_t)ws.t_boff[t];
 
   // ---- tile context of a tile whose owner segments overflowed (the other
   // tiles loaded it at the start): the sources of every depth below the tile
@@ -803,11 +835,11 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   if (ovf) fill_ctx_overflow(S, ws, t, dstart_t, a_t + 1, s_seg);
   const bool ctx_mine = tid < CTXC && tid <= a_t;
   if (ctx_mine && !ctx_early) {
-    const int src = ctx_src_of(ws, t, ovf, s_seg, nseg, dstart_t - 1 - tid, tid);
-    if (src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status)) {
-      const long long si = slice_at(ws, src);
+    int u;
+    long long si;
+    if (ctx_entry(ws, t, ovf, s_seg, s_segb, nseg, dstart_t - 1 - tid, tid, &u, &si)) {
       ctx_i = ws.slice_pos[si];
-      if (HAS_BOX) ctx_c = box_isect(ws.t_B[src / TILE], ws.slice_rel[si]);
+      if (HAS_BOX) ctx_c = box_isect(ws.t_B[u], ws.slice_rel[si]);
     }
   }
 
@@ -857,6 +889,7 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   oc.s_cidx = s_cidx;
   oc.s_cclip = s_cclip;
   oc.s_seg = s_seg;
+  oc.s_segb = s_segb;
   oc.nseg = nseg;
   oc.ovf = ovf;
   oc.t = t;
@@ -877,9 +910,10 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
       if (m < CTXC) {
         v = s_cclip[m];
       } else {
-        const int src = ctx_src_of(ws, t, ovf, s_seg, nseg, dstart_t - 1 - m, m);
-        v = src >= 0 && in_range(src, 0, (long long)ws.T * TILE, ws.status)
-                ? box_isect(ws.t_B[src / TILE], ws.slice_rel[slice_at(ws, src)]) : box_universe();
+        int u;
+        long long si;
+        v = ctx_entry(ws, t, ovf, s_seg, s_segb, nseg, dstart_t - 1 - m, m, &u, &si)
+                ? box_isect(ws.t_B[u], ws.slice_rel[si]) : box_universe();
       }
       link = -1;
     }
@@ -1108,8 +1142,8 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
         const int si = u * KPT + (dd - s_lo[u]);
         if (a.match && in_range(si, 0, TILE, ws.status)) a.match[base + s_spos[si]] = eo;
       } else if (in_range(-1 - dd, 0, a_t, ws.status)) {
-        ws.cpos[(size_t)ws.t_aoff[t] + (-1 - dd)] = e;
-        ws.cval[(size_t)ws.t_aoff[t] + (-1 - dd)] = eo;
+        ws.cpos[aoff_t + (-1 - dd)] = e;
+        ws.cval[aoff_t + (-1 - dd)] = eo;
       }
     }
     K3_TILE_DONE;
@@ -1177,7 +1211,7 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
         s_box[box_slot(cp)] = U;
         if (a.match) a.match[idx] = eo;
       } else if (in_range(m - ds, 0, a_t, ws.status)) {
-        const size_t mm = (size_t)ws.t_aoff[t] + (m - ds);  // below the tile start: k4 finishes the pair
+        const size_t mm = aoff_t + (m - ds);  // below the tile start: k4 finishes the pair
         ws.upre[mm] = U;
         ws.cpos[mm] = e;
         ws.cval[mm] = eo;
@@ -1193,7 +1227,7 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
       const int i = lowest_set(m);
       m &= m - 1;
       if (dd < later_lo)
-        ws.usuf[(size_t)ws.t_boff[t] + dd + a_t] = box_unite(s_box[box_slot(p0 + i)], rest);
+        ws.usuf[boff_t + dd + a_t] = box_unite(s_box[box_slot(p0 + i)], rest);
       ++dd;
     }
   }
@@ -1366,6 +1400,7 @@ struct K4Args {
 template <bool HAS_BOX>
 __global__ void __launch_bounds__(NT) k4_cross_tile_unions(K4Args a) {
   __shared__ int4 s_seg[SEGK];
+  __shared__ int s_segb[SEGK];
   __shared__ float4 s_mid[SEGK];
   __shared__ int s_nseg;
   const SceneWs& ws = a.ws;
@@ -1373,10 +1408,11 @@ __global__ void __launch_bounds__(NT) k4_cross_tile_unions(K4Args a) {
   const int a_t = ws.t_a[t];
   if (a_t == 0 || *ws.status != ST_OK) return;
   const int dstart = ws.t_dstart[t];
+  const size_t aoff_t = (size_t)ws.t_aoff[t];
   if (tid == 0) s_nseg = ws.t_nseg[t];
   if (tid < SEGK) {
-    const int4 sg = ws.t_seg[(size_t)t * SEGK + tid];
-    s_seg[tid] = sg;
+    s_seg[tid] = ws.t_seg[(size_t)t * SEGK + tid];
+    s_segb[tid] = ws.t_segb[(size_t)t * SEGK + tid];
   }
   __syncthreads();
   const int nseg = s_nseg;
@@ -1389,22 +1425,15 @@ __global__ void __launch_bounds__(NT) k4_cross_tile_unions(K4Args a) {
   __syncthreads();
   for (int m = tid; m < a_t; m += NT) {
     const int d = dstart - 1 - m;
-    int src, s = -1;
-    if (ovf) {
-      src = ws.ctx_src[(size_t)ws.t_aoff[t] + t + m];
-    } else {
-      s = segk_find(s_seg, nseg, d);
-      src = (s >= 0 && s_seg[s].x >= 0) ? s_seg[s].x * TILE + (d - s_seg[s].y) : -1;
-    }
-    if (src < 0) continue;  // unbalanced input
-    if (!in_range(src, 0, (long long)ws.T * TILE, ws.status)) continue;
-    const long long si = slice_at(ws, src);
+    int u;
+    long long si;
+    if (!ctx_entry(ws, t, ovf, s_seg, s_segb, nseg, d, m, &u, &si)) continue;  // unbalanced input
+    const int s = ovf ? -1 : segk_find(s_seg, nseg, d);
     const int o = ws.slice_pos[si];
     if (!in_range(o, 0, (long long)ws.T * TILE, ws.status)) continue;
-    const size_t cm = (size_t)ws.t_aoff[t] + m;
+    const size_t cm = aoff_t + m;
     if (a.match) a.match[o] = ws.cval[cm];
     if (HAS_BOX) {
-      const int u = src / TILE;
       const float4 mid = ovf ? tree_range(ws.uall_tree, ws.P, u + 1, t - 1, box_empty(), OpUnite())
                              : s_mid[s];
       const int c = ws.cpos[cm];
