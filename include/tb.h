@@ -76,8 +76,15 @@ typedef enum {
   TB_MONOID_BBOX_ISECT = 0,   /* float4 boxes, intersection, identity (-inf,-inf,+inf,+inf) */
   TB_MONOID_BBOX_UNION = 1,   /* float4 boxes, union, identity (+inf,+inf,-inf,-inf) */
   TB_MONOID_ADD_I32 = 2,      /* int32, addition modulo 2^32, identity 0 */
-  TB_MONOID_AFFINE3X4_F32 = 3 /* 12 floats, row-major [R | t] (x -> R x + t),
+  TB_MONOID_AFFINE3X4_F32 = 3, /* 12 floats, row-major [R | t] (x -> R x + t),
                                  composition A*B = apply B then A, identity [I | 0] */
+  TB_MONOID_RIGID_F32 = 4      /* 8 floats (qx, qy, qz, qw, tx, ty, tz, unused): rotation
+                                 by the unit quaternion q then translation t,
+                                 x -> q x q* + t; composition A*B = apply B then A =
+                                 (qA qB, tA + qA tB qA*) with Hamilton's product;
+                                 identity (0, 0, 0, 1, 0, 0, 0, 0).  No
+                                 renormalisation: rounding drifts |q| by about
+                                 1e-7 per level */
 } tb_monoid;
 
 typedef enum {
@@ -166,7 +173,7 @@ tb_status tb_open_positions(const uint8_t* kind, int64_t n, int32_t* pos,
  * idempotent required).  Values belong to the opens ("joints"): joint r is
  * the r-th open of the stream (pre-order rank), leaves carry none.
  * num_joints must equal the number of opens (at most n / 2); in and out hold
- * num_joints values of the monoid's type (4, 16 or 48 bytes each), are
+ * num_joints values of the monoid's type (4, 16, 48 or 32 bytes each), are
  * 16-byte aligned whatever the monoid, and must not overlap.
  *   TB_DOWN: out[r] = in[root] * ... * in[parent(r)] * in[r]
  *            (ancestor on the left; for transforms, world = parent world

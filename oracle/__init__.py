@@ -19,6 +19,8 @@ tree-structured scenes" (arXiv 2205.11659):
 * :func:`tree_scan_i32`, :func:`tree_scan_box`, :func:`affine_forward`,
   :func:`affine_up` -- Sec. 1 / Sec. 13, any monoid over the tree.
 * :func:`affine_backward` -- adjoint of the root-path transform product.
+* :func:`rigid_scan` -- the same folds over rigid transforms (quaternion and
+  translation).
 """
 import ctypes
 import os
@@ -72,6 +74,7 @@ def _load():
             lib.orc_tree_scan_i32.argtypes = [i32, p, i64, p, p]
             lib.orc_tree_scan_box.argtypes = [i32, i32, p, i64, p, p]
             lib.orc_affine_forward.argtypes = [p, i64, p, p]
+            lib.orc_rigid_scan.argtypes = [ctypes.c_int, p, i64, p, p]
             lib.orc_affine_up.argtypes = [p, i64, p, p]
             lib.orc_affine_loss.argtypes = [p, i64, p, p, i64, p]
             lib.orc_affine_backward.argtypes = [p, i64, p, p, p, i64]
@@ -80,7 +83,7 @@ def _load():
                       lib.orc_tree_scan_i32,
                       lib.orc_tree_scan_box, lib.orc_affine_forward,
                       lib.orc_affine_up, lib.orc_affine_loss,
-                      lib.orc_affine_backward):
+                      lib.orc_affine_backward, lib.orc_rigid_scan):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -210,6 +213,16 @@ def affine_up(kind, values):
     out = np.zeros_like(v)
     st = _load().orc_affine_up(_ptr(k), k.size, _ptr(v), _ptr(out))
     return st, out.reshape(-1, 3, 4)
+
+
+def rigid_scan(direction, kind, values):
+    """Rigid transforms (qx, qy, qz, qw, tx, ty, tz, unused) per joint, fp64:
+    DOWN (0) root-path products, UP (1) stream-order subtree products."""
+    k = _kinds(kind)
+    v = np.ascontiguousarray(values, dtype=np.float64).reshape(-1, 8)
+    out = np.zeros_like(v)
+    st = _load().orc_rigid_scan(int(direction), _ptr(k), k.size, _ptr(v), _ptr(out))
+    return st, out
 
 
 def affine_loss(kind, local, W):

@@ -22,6 +22,8 @@
  *   orc_tree_scan_*         -- Sec. 1 / Sec. 13, "any monoid" over the tree
  *   orc_affine_*            -- the same stack walk for 3x4 affine transforms
  *                              (root-path products) and their adjoint, fp64
+ *   orc_rigid_scan          -- the same for rigid transforms (unit quaternion
+ *                              and translation), DOWN and UP, fp64
  *
  * Element kinds: 0 = LEAF, 1 = OPEN_CLIP, 2 = OPEN_BLEND, 3 = CLOSE.
  * A box is 4 floats (x0, y0, x1, y1).
@@ -443,6 +445,81 @@ int orc_affine_up(const uint8_t* kind, int64_t n, const double* in, double* out)
   }
   if (st == ORC_OK && sp != 0) st = ORC_UNBALANCED;
   free(rank);
+  free(acc);
+  return st;
+}
+
+/* ------------------------------------- rigid transforms (quaternion, t) */
+/* A rigid transform is 8 doubles (qx, qy, qz, qw, tx, ty, tz, unused): a
+ * rotation by the unit quaternion q = w + xi + yj + zk, then a translation:
+ * x -> q x q* + t.  Composition (A*B) = (qA qB, tA + qA tB qA*): B first, so
+ * the ancestor is on the left as for the affine transforms (Sec. 1 and
+ * Sec. 13: any monoid).  Quaternions multiply by Hamilton's rules
+ * i^2 = j^2 = k^2 = ijk = -1. */
+static void quat_mul(const double* a, const double* b, double* c) {
+  const double ax = a[0], ay = a[1], az = a[2], aw = a[3];
+  const double bx = b[0], by = b[1], bz = b[2], bw = b[3];
+  c[0] = aw * bx + ax * bw + ay * bz - az * by;
+  c[1] = aw * by - ax * bz + ay * bw + az * bx;
+  c[2] = aw * bz + ax * by - ay * bx + az * bw;
+  c[3] = aw * bw - ax * bx - ay * by - az * bz;
+}
+
+/* v rotated by q: q v q* with v a pure quaternion. */
+static void quat_rotate(const double* q, const double* v, double* out) {
+  const double p[4] = {v[0], v[1], v[2], 0.0};
+  const double qc[4] = {-q[0], -q[1], -q[2], q[3]};
+  double t[4], r[4];
+  quat_mul(q, p, t);
+  quat_mul(t, qc, r);
+  out[0] = r[0];
+  out[1] = r[1];
+  out[2] = r[2];
+}
+
+static void rigid_mul(const double* A, const double* B, double* C) {
+  double q[4], t[3];
+  quat_mul(A, B, q);
+  quat_rotate(A, B + 4, t);
+  C[0] = q[0];
+  C[1] = q[1];
+  C[2] = q[2];
+  C[3] = q[3];
+  C[4] = A[4] + t[0];
+  C[5] = A[5] + t[1];
+  C[6] = A[6] + t[2];
+  C[7] = 0.0;
+}
+
+/* DOWN (dir 0): each joint gets the product along its root path, the root
+ * first; UP (dir 1): the product over its subtree in stream order, its own
+ * value first.  Same stack walks as the affine forms above. */
+int orc_rigid_scan(int dir, const uint8_t* kind, int64_t n, const double* in, double* out) {
+  int st = check_kinds(kind, n);
+  if (st) return st;
+  int64_t* stack = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  double* acc = (double*)malloc(sizeof(double) * 8 * (size_t)(n + 1));
+  int64_t sp = 0, r = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (is_open(kind[i])) {
+      if (dir == 0) {
+        if (sp > 0) rigid_mul(out + 8 * stack[sp - 1], in + 8 * r, out + 8 * r);
+        else memcpy(out + 8 * r, in + 8 * r, 8 * sizeof(double));
+      } else {
+        memcpy(acc + 8 * sp, in + 8 * r, 8 * sizeof(double));
+      }
+      stack[sp++] = r++;
+    } else if (kind[i] == K_CLOSE) {
+      if (sp == 0) { st = ORC_UNBALANCED; break; }
+      --sp;
+      if (dir != 0) {
+        memcpy(out + 8 * stack[sp], acc + 8 * sp, 8 * sizeof(double));
+        if (sp > 0) rigid_mul(acc + 8 * (sp - 1), acc + 8 * sp, acc + 8 * (sp - 1));
+      }
+    }
+  }
+  if (st == ORC_OK && sp != 0) st = ORC_UNBALANCED;
+  free(stack);
   free(acc);
   return st;
 }

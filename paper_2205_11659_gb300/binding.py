@@ -43,6 +43,7 @@ TB_MONOID_BBOX_ISECT = 0
 TB_MONOID_BBOX_UNION = 1
 TB_MONOID_ADD_I32 = 2
 TB_MONOID_AFFINE3X4_F32 = 3
+TB_MONOID_RIGID_F32 = 4
 TB_DOWN = 0
 TB_UP = 1
 
@@ -418,13 +419,15 @@ def bboxes_batched_host(kind, box, offsets, out):
 _VALUE_SHAPE = {TB_MONOID_BBOX_ISECT: ((4,), torch.float32),
                 TB_MONOID_BBOX_UNION: ((4,), torch.float32),
                 TB_MONOID_ADD_I32: ((), torch.int32),
-                TB_MONOID_AFFINE3X4_F32: ((3, 4), torch.float32)}
+                TB_MONOID_AFFINE3X4_F32: ((3, 4), torch.float32),
+                TB_MONOID_RIGID_F32: ((8,), torch.float32)}
 
 
 def tree_scan(monoid, direction, kind, values, check=True):
     """tb_tree_scan on device tensors: values holds one monoid value per open
-    of ``kind`` in stream order ((J, 4) float32 boxes, (J,) int32, or
-    (J, 3, 4) float32 transforms); returns a tensor of the same shape."""
+    of ``kind`` in stream order ((J, 4) float32 boxes, (J,) int32,
+    (J, 3, 4) float32 affine transforms or (J, 8) float32 rigid transforms);
+    returns a tensor of the same shape."""
     shape, dtype = _VALUE_SHAPE[monoid]
     dev = kind.device
     if not kind.is_cuda or not values.is_cuda:

@@ -29,7 +29,7 @@ tb_status tb_tree_scan(int monoid, int dir, const uint8_t* kind, int64_t n, int6
                        void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   tb_internal::phase_reset();
-  if (monoid < TB_MONOID_BBOX_ISECT || monoid > TB_MONOID_AFFINE3X4_F32) return TB_ERR_INVALID_ARG;
+  if (monoid < TB_MONOID_BBOX_ISECT || monoid > TB_MONOID_RIGID_F32) return TB_ERR_INVALID_ARG;
   if (dir != TB_DOWN && dir != TB_UP) return TB_ERR_INVALID_ARG;
   tb_status st = check_common(kind, n, num_joints, ws, d_status);
   if (st != TB_OK) return st;
@@ -55,6 +55,9 @@ tb_status tb_tree_scan(int monoid, int dir, const uint8_t* kind, int64_t n, int6
       break;
     case TB_MONOID_ADD_I32:
       st = scan_dir<MonoidAddI32>(dir, w, in, out, d_status, s);
+      break;
+    case TB_MONOID_RIGID_F32:
+      st = scan_dir<MonoidRigid>(dir, w, in, out, d_status, s);
       break;
     default:
       st = scan_dir<MonoidAffine>(dir, w, in, out, d_status, s);

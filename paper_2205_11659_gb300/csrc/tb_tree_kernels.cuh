@@ -191,6 +191,58 @@ struct MonoidAffSum {
   __device__ static void store(void* p, int64_t i, const V& v) { st_aff(p, i, v); }
 };
 
+// A rigid transform: rotation by the unit quaternion q = (x, y, z, w), then
+// translation t (t.w unused).  Composition A*B = (qA qB, tA + qA tB qA*): B
+// first, the ancestor on the left, as for the affine transforms.  Quaternions
+// multiply by Hamilton's rules (i^2 = j^2 = k^2 = ijk = -1); the rotation of
+// a vector uses v + 2 u x (u x v + w v), u = (x, y, z), the expansion of
+// q v q* for a unit q.
+struct Rig {
+  float4 q, t;
+};
+__host__ __device__ __forceinline__ float4 quat_mul(float4 a, float4 b) {
+  return make_float4(fmaf(a.w, b.x, fmaf(a.x, b.w, fmaf(a.y, b.z, -a.z * b.y))),
+                     fmaf(a.w, b.y, fmaf(-a.x, b.z, fmaf(a.y, b.w, a.z * b.x))),
+                     fmaf(a.w, b.z, fmaf(a.x, b.y, fmaf(-a.y, b.x, a.z * b.w))),
+                     fmaf(a.w, b.w, fmaf(-a.x, b.x, fmaf(-a.y, b.y, -a.z * b.z))));
+}
+__host__ __device__ __forceinline__ float4 quat_rotate(float4 q, float4 v) {
+  // c = u x v + w v, then v + 2 u x c
+  const float cx = fmaf(q.y, v.z, fmaf(-q.z, v.y, q.w * v.x));
+  const float cy = fmaf(q.z, v.x, fmaf(-q.x, v.z, q.w * v.y));
+  const float cz = fmaf(q.x, v.y, fmaf(-q.y, v.x, q.w * v.z));
+  return make_float4(fmaf(2.f, fmaf(q.y, cz, -q.z * cy), v.x), fmaf(2.f, fmaf(q.z, cx, -q.x * cz), v.y),
+                     fmaf(2.f, fmaf(q.x, cy, -q.y * cx), v.z), 0.f);
+}
+struct MonoidRigid {
+  using V = Rig;
+  __device__ static V identity() {
+    Rig r;
+    r.q = make_float4(0.f, 0.f, 0.f, 1.f);
+    r.t = make_float4(0.f, 0.f, 0.f, 0.f);
+    return r;
+  }
+  __device__ static V combine(const V& a, const V& b) {
+    Rig c;
+    c.q = quat_mul(a.q, b.q);
+    const float4 r = quat_rotate(a.q, b.t);
+    c.t = make_float4(a.t.x + r.x, a.t.y + r.y, a.t.z + r.z, 0.f);
+    return c;
+  }
+  __device__ static V load(const void* p, int64_t i) {
+    const float4* f = reinterpret_cast<const float4*>(p) + 2 * i;
+    Rig r;
+    r.q = f[0];
+    r.t = f[1];
+    return r;
+  }
+  __device__ static void store(void* p, int64_t i, const V& v) {
+    float4* f = reinterpret_cast<float4*>(p) + 2 * i;
+    f[0] = v.q;
+    f[1] = v.t;
+  }
+};
+
 template <class M>
 struct MonoidOp {
   __device__ typename M::V operator()(const typename M::V& a, const typename M::V& b) const {

@@ -312,6 +312,22 @@ def affine_locals(num_joints, seed, angle_sigma=0.3):
     return out.astype(np.float32)
 
 
+def rigid_locals(num_joints, seed, angle_sigma=0.3):
+    """(J, 8) float32 rigid transforms (qx, qy, qz, qw, tx, ty, tz, 0): a
+    rotation by N(0, angle_sigma) about a uniform random axis as a unit
+    quaternion (fp64, then rounded), translation N(0, 1)^3."""
+    rng = _rng(seed, 8)
+    J = int(num_joints)
+    axis = rng.normal(size=(J, 3))
+    axis /= np.linalg.norm(axis, axis=1, keepdims=True)
+    half = 0.5 * rng.normal(0.0, angle_sigma, J)
+    out = np.zeros((J, 8))
+    out[:, :3] = axis * np.sin(half)[:, None]
+    out[:, 3] = np.cos(half)
+    out[:, 4:7] = rng.normal(size=(J, 3))
+    return out.astype(np.float32)
+
+
 def grad_weights(num_joints, seed):
     """W_r ~ N(0,1)^{3x4}: the loss is sum_r <W_r, world_r>."""
     rng = _rng(seed, 7)

@@ -130,7 +130,7 @@ def test_tree_scan_argument_errors(lib):
              ws=fake, nb=big):
         return lib.tb_tree_scan(monoid, d, p(kind), n, J, p(vin), p(vout), p(ws), nb, p(fake), None)
 
-    assert scan(monoid=4) == b.TB_ERR_INVALID_ARG
+    assert scan(monoid=5) == b.TB_ERR_INVALID_ARG
     assert scan(monoid=-1) == b.TB_ERR_INVALID_ARG
     assert scan(d=2) == b.TB_ERR_INVALID_ARG
     assert scan(J=6) == b.TB_ERR_INVALID_ARG          # more joints than n / 2

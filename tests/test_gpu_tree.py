@@ -114,6 +114,36 @@ def test_affine(name, d):
 
 
 @pytest.mark.parametrize("name", list(STREAMS))
+@pytest.mark.parametrize("d", [binding.TB_DOWN, binding.TB_UP])
+def test_rigid(name, d):
+    """Rigid transforms (unit quaternion + translation, Sec. 1 / Sec. 13: any
+    monoid) in fp32 against the fp64 oracle, per joint as for the affine
+    transforms; the quaternion parts also against the unit norm."""
+    k = STREAMS[name]
+    J = n_opens(k)
+    v = inputs.rigid_locals(J, 41)
+    st, ref = oracle.rigid_scan(d, k, v.astype(np.float64))
+    assert st == oracle.OK
+    got = gpu_scan(binding.TB_MONOID_RIGID_F32, d, k, v)
+    assert got.shape == (J, 8)
+    assert rel_err(got[:, :4], ref[:, :4]) < REL_TOL, name
+    assert rel_err(got[:, 4:7], ref[:, 4:7]) < REL_TOL, name
+    if J:
+        assert np.abs(np.linalg.norm(got[:, :4].astype(np.float64), axis=1) - 1.0).max() < 1e-4
+
+
+def test_rigid_large_skeleton():
+    k = inputs.skeleton_kinds(1 << 20, 42)
+    J = n_opens(k)
+    v = inputs.rigid_locals(J, 43)
+    for d in (binding.TB_DOWN, binding.TB_UP):
+        st, ref = oracle.rigid_scan(d, k, v.astype(np.float64))
+        got = gpu_scan(binding.TB_MONOID_RIGID_F32, d, k, v)
+        assert rel_err(got[:, :4], ref[:, :4]) < REL_TOL
+        assert rel_err(got[:, 4:7], ref[:, 4:7]) < REL_TOL
+
+
+@pytest.mark.parametrize("name", list(STREAMS))
 def test_affine_backward(name):
     k = STREAMS[name]
     J = n_opens(k)

@@ -686,3 +686,66 @@ def test_affine_up_stream_order_with_rotations():
             if len(sub) > 1 and not np.allclose(acc[:3], rev[:3], rtol=1e-6, atol=1e-6):
                 swapped_differs = True
         assert swapped_differs  # the pin separates the two orders on these inputs
+
+
+def _quat_matrix(q):
+    """Rotation matrix of unit quaternion (x, y, z, w): the textbook closed form."""
+    x, y, z, w = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                     [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                     [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+
+
+def _rigid_as_affine(v):
+    out = np.zeros((v.shape[0], 3, 4))
+    for r in range(v.shape[0]):
+        out[r, :, :3] = _quat_matrix(v[r, :4])
+        out[r, :, 3] = v[r, 4:7]
+    return out
+
+
+@pytest.mark.parametrize("direction", [0, 1])
+def test_rigid_scan_matches_affine_forms(direction):
+    """Rigid transforms compose like their 3x4 matrices (rotation matrix of
+    the quaternion, translation): both scan directions agree with the affine
+    oracle functions on the matrix forms (a different arithmetic path)."""
+    for k in (inputs.skeleton_kinds(300, 21, max_depth=25), inputs.random_walk_kinds(2000, 22)):
+        J = int(np.count_nonzero((k == 1) | (k == 2)))
+        v = inputs.rigid_locals(J, 23).astype(np.float64)
+        v[:, :4] /= np.linalg.norm(v[:, :4], axis=1, keepdims=True)
+        st, out = oracle.rigid_scan(direction, k, v)
+        assert st == oracle.OK
+        aff = _rigid_as_affine(v)
+        st, ref = (oracle.affine_forward(k, aff) if direction == 0 else oracle.affine_up(k, aff))
+        assert st == oracle.OK
+        assert np.allclose(_rigid_as_affine(out), ref, rtol=1e-11, atol=1e-11)
+        assert np.allclose(np.linalg.norm(out[:, :4], axis=1), 1.0, atol=1e-12)
+
+
+def test_rigid_scan_hamilton_rules_and_translation_sums():
+    # a chain of three joints with quaternions i, j, k: root-path products
+    # i, ij = k, ijk = -1 (Hamilton's rules)
+    k = np.array([1, 1, 1, 3, 3, 3], np.uint8)
+    v = np.zeros((3, 8))
+    v[0, 0] = v[1, 1] = v[2, 2] = 1.0
+    st, out = oracle.rigid_scan(0, k, v)
+    assert st == oracle.OK
+    assert np.allclose(out[:, :4], [[1, 0, 0, 0], [0, 0, 1, 0], [0, 0, 0, -1]])
+    # identity rotations: translations add along the root path (DOWN) and
+    # over the subtree (UP)
+    k = inputs.skeleton_kinds(200, 24, max_depth=20)
+    J = int(np.count_nonzero(k == 1))
+    v = np.zeros((J, 8))
+    v[:, 3] = 1.0
+    v[:, 4:7] = np.random.default_rng(5).integers(-50, 50, (J, 3))
+    opens, mat, par, rank = _opens_ranges(k)
+    _, down = oracle.rigid_scan(0, k, v)
+    _, up = oracle.rigid_scan(1, k, v)
+    for o in opens:
+        t, a = np.zeros(3), int(o)
+        while a >= 0:
+            t += v[rank[a], 4:7]
+            a = int(par[a])
+        assert np.array_equal(down[rank[int(o)], 4:7], t)
+        sub = [rank[int(j)] for j in opens if o <= j < mat[o]]
+        assert np.array_equal(up[rank[int(o)], 4:7], v[sub, 4:7].sum(0))
