@@ -36,6 +36,13 @@ struct Layout {
   int64_t cap;
 };
 
+// Levels of the tiles' union table beyond level 0: floor(log2 T).
+constexpr int union_levels(int T) {
+  int k = 0;
+  while ((2 << k) <= T) ++k;
+  return k;
+}
+
 constexpr Layout scene_layout(int64_t n, bool has_box) {
   Layout L{};
   const int T = (int)((n + TILE - 1) / TILE);
@@ -80,7 +87,7 @@ constexpr Layout scene_layout(int64_t n, bool has_box) {
     L.t_val1 = take(t16);
     L.t_B = take(t16);
     L.t_uall = take(t16);
-    L.uall_tree = take((size_t)2 * P * 16);
+    L.uall_tree = take((size_t)union_levels(T) * T * 16);
     L.slice_rel = take(slots * 16);
     L.usuf = take(slots * 16);
     L.upre = take(slots * 16);
@@ -221,6 +228,45 @@ cudaError_t k2_jump_max_blocks(int* out) {
   return cudaSuccess;
 }
 
+// The same for k4_union_table.
+cudaError_t k4_table_max_blocks(int* out) {
+  static std::atomic<int> cached[kOnceDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool tracked = dev >= 0 && dev < kOnceDevices;
+  if (tracked) {
+    const int c = cached[dev].load(std::memory_order_relaxed);
+    if (c > 0) {
+      *out = c;
+      return cudaSuccess;
+    }
+  }
+  const int sms = current_device_sms();
+  if (sms <= 0) return cudaErrorInvalidDevice;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k4_union_table, NTU, 0);
+  if (e != cudaSuccess) return e;
+  const int nb = sms * (per_sm > 0 ? per_sm : 1);
+  if (tracked) cached[dev].store(nb, std::memory_order_relaxed);
+  *out = nb;
+  return cudaSuccess;
+}
+
+cudaError_t launch_union_table(const SceneWs& w, cudaStream_t s) {
+  int levels = union_levels(w.T) + 1;  // level 0 is t_uall
+  if (levels < 2) return cudaSuccess;  // one tile: nothing to build
+  int maxb = 0;
+  cudaError_t e = k4_table_max_blocks(&maxb);
+  if (e != cudaSuccess) return e;
+  const int want = (w.T + NTU - 1) / NTU;
+  const int blocks = want < maxb ? want : maxb;
+  SceneWs wa = w;
+  void* args[] = {&wa, &levels};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k4_union_table), dim3(blocks),
+                                     dim3(NTU), args, 0, s);
+}
+
 template <bool HAS_BOX>
 cudaError_t launch_k2(const SceneWs& w, cudaStream_t s) {
   const int g = (w.T + NTR - 1) / NTR;
@@ -293,8 +339,7 @@ tb_status run_scene(const uint8_t* kind, const float* box, int64_t n, int32_t* p
   if (e != cudaSuccess) return TB_ERR_CUDA;
   phase_mark(s);
   if (HAS_BOX) {
-    k4_union_tree<<<1, NT2, 0, s>>>(w);
-    if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
+    if (launch_union_table(w, s) != cudaSuccess) return TB_ERR_CUDA;
   }
   K4Args a4{reinterpret_cast<float4*>(box_out), match, w};
   k4_cross_tile_unions<HAS_BOX><<<L.T, NT, 0, s>>>(a4);

@@ -339,7 +339,7 @@ struct SceneWs {
   float4* t_val[2];
   float4* t_B;
   float4* t_uall;
-  float4* uall_tree;  // 2P
+  float4* uall_tree;  // union table levels 1 .. (levels - 1), T entries each
   int* slice_pos;
   float4* slice_rel;
   float4* usuf;

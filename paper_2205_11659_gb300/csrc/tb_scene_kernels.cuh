@@ -878,8 +878,7 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
   // again); with no such chunk it belongs to the tile context.
   const int cps = tree_last_le(s_tree, NT, tid, lo_j - 1);
   const int cq = tree_last_le(s_tree, NT, tid, ds - 1);
-  s_cps[tid] = cps;
-  __syncthreads();
+  s_cps[tid] = cps;  // published by the barrier below (with the jumping's first values)
 
   OutCtx oc;
   oc.s_lo = s_lo;
@@ -919,7 +918,7 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
     }
     s_val[tid] = v;
     s_link[tid] = link;
-    __syncthreads();
+    __syncthreads();  // (also publishes s_cps)
     for (;;) {
       const int l = s_link[cur * NT + tid];
       float4 vv = s_val[cur * NT + tid];
@@ -935,6 +934,7 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
       if (!any) break;
     }
   }
+  if (!HAS_BOX) __syncthreads();  // publishes s_cps
   oc.s_B = s_val + cur * NT;
 
   // ---- scene of the chunk's first element (batched)
@@ -1352,41 +1352,39 @@ __global__ void __launch_bounds__(NT) k3_search(K3Args a) {
 }
 
 // ------------------------------------------------------------------- K4
-// Union tree over the tiles' leaf unions (one block; leaves at [P, 2P)):
-// each warp walks 32 leaves at a time and builds their five lowest levels by
-// shuffles; the levels above come from global memory while a level is wide,
-// then from shared memory.
-__global__ void __launch_bounds__(NT2) k4_union_tree(SceneWs ws) {
-  __shared__ float4 s_top[2 * NT2];
-  const int T = ws.T, P = ws.P, tid = threadIdx.x, lane = lane_id();
-  if (*ws.status != ST_OK) return;
-  float4* tree = ws.uall_tree;
-  const int LP = 31 - __clz(P);
-  for (int r0 = tid - lane; r0 < P; r0 += NT2) {  // warp-uniform: 32 leaves per warp
-    const int u = r0 + lane;
-    float4 v = u < T ? ws.t_uall[u] : box_empty();
-    if (u < P) tree[P + u] = v;
-#pragma unroll
-    for (int l = 1; l <= 5; ++l) {
-      v = box_unite(v, shfl_xor(v, 1 << (l - 1)));
-      if (l <= LP && (lane & ((1 << l) - 1)) == 0 && u < P) tree[(P + u) >> l] = v;
+// Union table over the tiles' leaf unions (a sparse table: level k holds,
+// for every tile u, the union of tiles u .. u + 2^k - 1, clamped at the last
+// tile; level 0 is t_uall itself).  Union is idempotent, so the union of any
+// tile range [l, r] is two entries of one level (overlapping halves): the
+// cross-tile pass asks for one range per owner segment, with two
+// independent loads instead of a walk up a tree.  Built level by level by
+// all the blocks of a cooperative launch with a grid-wide barrier between
+// levels (reads past L1, as in k2_jump).
+constexpr int NTU = 256;
+__global__ void __launch_bounds__(NTU) k4_union_table(SceneWs ws, int levels) {
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  const int T = ws.T;
+  if (*ws.status != ST_OK) return;  // no kernel running now writes it: the whole grid returns
+  const int nthr = gridDim.x * NTU;
+  const float4* prev = ws.t_uall;
+  for (int k = 1; k < levels; ++k) {
+    float4* cur = ws.uall_tree + (size_t)(k - 1) * T;
+    const int half = 1 << (k - 1);
+    for (int u = blockIdx.x * NTU + threadIdx.x; u < T; u += nthr) {
+      const int v = u + half < T ? u + half : T - 1;
+      __stcg(cur + u, box_unite(__ldcg(prev + u), __ldcg(prev + v)));
     }
+    prev = cur;
+    grid.sync();
   }
-  __syncthreads();
-  int h = P >> 6;
-  for (; h > NT2 / 2; h >>= 1) {
-    for (int i = h + tid; i < 2 * h; i += NT2) tree[i] = box_unite(tree[2 * i], tree[2 * i + 1]);
-    __syncthreads();
-  }
-  if (h >= 1) {
-    for (int i = 2 * h + tid; i < 4 * h; i += NT2) s_top[i] = tree[i];  // i < 4h <= 2 * NT2
-    __syncthreads();
-    for (int g = h; g >= 1; g >>= 1) {
-      for (int i = g + tid; i < 2 * g; i += NT2) s_top[i] = box_unite(s_top[2 * i], s_top[2 * i + 1]);
-      __syncthreads();
-    }
-    for (int i = 1 + tid; i < 2 * h; i += NT2) tree[i] = s_top[i];
-  }
+}
+
+// Union of the tiles l .. r (empty box when l > r) from the union table.
+__device__ __forceinline__ float4 tile_range_union(const SceneWs& ws, int l, int r) {
+  if (l > r) return box_empty();
+  const int k = 31 - __clz(r - l + 1);
+  const float4* lev = k == 0 ? ws.t_uall : ws.uall_tree + (size_t)(k - 1) * ws.T;
+  return box_unite(__ldcg(lev + l), __ldcg(lev + r - (1 << k) + 1));
 }
 
 struct K4Args {
@@ -1419,8 +1417,7 @@ __global__ void __launch_bounds__(NT) k4_cross_tile_unions(K4Args a) {
   const bool ovf = nseg > SEGK;
   if (HAS_BOX && !ovf && tid < nseg) {
     const int u = s_seg[tid].x;
-    s_mid[tid] = u >= 0 ? tree_range(ws.uall_tree, ws.P, u + 1, t - 1, box_empty(), OpUnite())
-                        : box_empty();
+    s_mid[tid] = u >= 0 ? tile_range_union(ws, u + 1, t - 1) : box_empty();
   }
   __syncthreads();
   for (int m = tid; m < a_t; m += NT) {
@@ -1434,8 +1431,7 @@ __global__ void __launch_bounds__(NT) k4_cross_tile_unions(K4Args a) {
     const size_t cm = aoff_t + m;
     if (a.match) a.match[o] = ws.cval[cm];
     if (HAS_BOX) {
-      const float4 mid = ovf ? tree_range(ws.uall_tree, ws.P, u + 1, t - 1, box_empty(), OpUnite())
-                             : s_mid[s];
+      const float4 mid = ovf ? tile_range_union(ws, u + 1, t - 1) : s_mid[s];
       const int c = ws.cpos[cm];
       const float4 U = box_unite(box_unite(ws.usuf[si], mid), ws.upre[cm]);
       a.box_out[o] = U;
