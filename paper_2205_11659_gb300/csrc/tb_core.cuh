@@ -37,7 +37,7 @@ constexpr int KPT = TB_KPT;
 constexpr bool PERSIST = TB_PERSIST != 0;
 constexpr int TILE = NT * KPT;
 constexpr int NW = NT / 32;
-static_assert(NT == 128 || NT == 256 || NT == 512, "block size must be 128, 256 or 512");
+static_assert(NT == 64 || NT == 128 || NT == 256 || NT == 512, "block size must be 64, 128, 256 or 512");
 static_assert(KPT == 8 || KPT == 16, "elements per thread must be 8 or 16");
 
 // Element kinds; K_PAD marks positions past the end of the stream.
