@@ -78,6 +78,98 @@ __device__ __forceinline__ bool load_kinds(const uint8_t* __restrict__ kind, int
   return bad;
 }
 
+// The KPT kinds of a chunk as KPT/4 little-endian words of bytes (positions
+// at or past n read as leaves; in-range bytes above 3 are reported and then
+// treated as leaves, as load_kinds does).
+__device__ __forceinline__ bool load_kind_words(const uint8_t* __restrict__ kind, int n, int e0,
+                                                unsigned (&wd)[KPT / 4]) {
+  bool bad = false;
+  if (e0 + KPT <= n) {
+    if constexpr (KPT == 16) {
+      const uint4 v = ld_nc_u4(kind + e0);
+      wd[0] = v.x;
+      wd[1] = v.y;
+      wd[2] = v.z;
+      wd[3] = v.w;
+    } else {
+      const uint2 v = ld_nc_u2(kind + e0);
+      wd[0] = v.x;
+      wd[1] = v.y;
+    }
+#pragma unroll
+    for (int j = 0; j < KPT / 4; ++j) {
+      if (wd[j] & 0xfcfcfcfcu) {  // some byte above 3
+        bad = true;
+        unsigned x = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const unsigned k = (wd[j] >> (8 * b)) & 0xffu;
+          x |= (k > 3u ? 0u : k) << (8 * b);
+        }
+        wd[j] = x;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < KPT / 4; ++j) {
+      unsigned x = 0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int e = e0 + 4 * j + b;
+        unsigned k = e < n ? kind[e] : 0u;
+        if (k > 3u) {
+          bad = true;
+          k = 0u;
+        }
+        x |= k << (8 * b);
+      }
+      wd[j] = x;
+    }
+  }
+  return bad;
+}
+
+// Summary of 4 consecutive kinds (2 bits each in `code`, the first lowest)
+// for the tile-summary pass, with P_e the depth after element e relative to
+// the group start:
+//   bits  0-3   P_3 + 4                 depth change
+//   bits  4-7   min(0, P_0..P_3) + 4    lowest depth, the start included
+//   bits  8-11  min(P_0..P_3) + 4       lowest depth after an element
+//   bits 12-15  opens e with P_e <= P_q for every later q in the group
+//               (unmatched inside the group: its final stack, P rising by one)
+//   bits 16-19  P_e + 4 of the first of those
+//   bits 20-23  clips
+__host__ __device__ __forceinline__ unsigned k1_group_entry(unsigned code) {
+  int P[4];
+  int p = 0, m0 = 0, ma = 4;
+  unsigned clip = 0, opn = 0;
+  for (int e = 0; e < 4; ++e) {
+    const int k = (int)((code >> (2 * e)) & 3u);
+    p += kind_delta(k);
+    P[e] = p;
+    m0 = m0 < p ? m0 : p;
+    ma = ma < p ? ma : p;
+    if (k == K_CLIP) clip |= 1u << e;
+    if (kind_open(k)) opn |= 1u << e;
+  }
+  unsigned wm = 0;
+  int l0 = 0, later = 4;
+  for (int e = 3; e >= 0; --e) {
+    if (((opn >> e) & 1u) && P[e] <= later) {
+      wm |= 1u << e;
+      l0 = P[e];
+    }
+    later = later < P[e] ? later : P[e];
+  }
+  return (unsigned)(p + 4) | (unsigned)(m0 + 4) << 4 | (unsigned)(ma + 4) << 8 | wm << 12 |
+         (unsigned)(l0 + 4) << 16 | clip << 20;
+}
+
+// The 2-bit codes of a word's 4 kind bytes (each 0..3).
+__device__ __forceinline__ unsigned kind_code4(unsigned w) {
+  return (w & 0x3u) | ((w >> 6) & 0xcu) | ((w >> 12) & 0x30u) | ((w >> 18) & 0xc0u);
+}
+
 // ------------------------------------------------------------------- K1
 struct K1Args {
   const uint8_t* kind;
@@ -93,23 +185,27 @@ __global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
   __shared__ int2 s_scr2[NW + 1];
   __shared__ float4 s_fscr[NW + 1];
   __shared__ int s_boff;
+  __shared__ unsigned s_gtab[256];
   const int tid = threadIdx.x;
   const int t = blockIdx.x;
   const int base = t * TILE, p0 = tid * KPT;
 
-  uint8_t kk[KPT];
-  if (load_kinds(a.kind, a.n, base + p0, kk)) atomic_cas_i32(a.status, ST_OK, ST_BAD_KIND);
+  // the group summaries of every 4 kinds (k1_group_entry), one table
+  for (int c = tid; c < 256; c += NT) s_gtab[c] = k1_group_entry((unsigned)c);
+  unsigned wd[KPT / 4];
+  if (load_kind_words(a.kind, a.n, base + p0, wd)) atomic_cas_i32(a.status, ST_OK, ST_BAD_KIND);
+  __syncthreads();
 
-  // Chunk depth profile relative to the chunk start (the kinds are kept
-  // packed, 4 bits each, to hold fewer registers while the scans run).
-  unsigned long long kp = 0;
+  // Chunk depth profile relative to the chunk start, 4 kinds at a time.
+  unsigned ge[KPT / 4];
   int r = 0, mn = 0, mn_after = INT_MAX;
 #pragma unroll
-  for (int i = 0; i < KPT; ++i) {
-    kp |= (unsigned long long)kk[i] << (4 * i);
-    r += kind_delta(kk[i]);
-    mn = mn < r ? mn : r;
-    mn_after = mn_after < r ? mn_after : r;
+  for (int j = 0; j < KPT / 4; ++j) {
+    ge[j] = s_gtab[kind_code4(wd[j])];
+    const int m0 = r + (int)((ge[j] >> 4) & 15u) - 4, ma = r + (int)((ge[j] >> 8) & 15u) - 4;
+    mn = mn < m0 ? mn : m0;
+    mn_after = mn_after < ma ? mn_after : ma;
+    r += (int)(ge[j] & 15u) - 4;
   }
   // one scan gives the tile-relative depth at the chunk start and, in its
   // total, the tile's depth change and lowest depth
@@ -146,21 +242,40 @@ __global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
   // Consecutive unmatched opens of a chunk sit one level apart (an open
   // between them that stayed open would be unmatched too), so the chunk's
   // slots are first_slot, first_slot + 1, ... in element order.
+  // Per group (from the last): its opens unmatched inside it stay unmatched
+  // in the tile while their depth is at most the lowest depth after the
+  // group; they rise one level at a time, so they are the first n of them.
   unsigned umt = 0, clipm = 0;
   int first_slot = 0;
   {
     int suf = suf_after;
-    int A = ds + r;  // depth after element i, walking back from the chunk end
+    int A = ds + r;  // depth at the end of group j
 #pragma unroll
-    for (int i = KPT - 1; i >= 0; --i) {
-      const int k = (int)((kp >> (4 * i)) & 15ull);
-      suf = suf < A ? suf : A;
-      if (k == K_CLIP) clipm |= 1u << i;
-      if (kind_open(k) && A <= suf) {
-        umt |= 1u << i;
-        first_slot = A - 1 + a_t;
+    for (int j = KPT / 4 - 1; j >= 0; --j) {
+      const unsigned e = ge[j];
+      const int As = A - ((int)(e & 15u) - 4);  // depth at the group start
+      clipm |= ((e >> 20) & 15u) << (4 * j);
+      const unsigned wm = (e >> 12) & 15u;
+      if (wm) {
+        const int l0 = (int)((e >> 16) & 15u) - 4;
+        const int nw = popc(wm);
+        const long long room = (long long)suf - As - l0 + 1;  // (suf may be INT_MAX)
+        const int nsel = room < nw ? (int)room : nw;
+        if (nsel > 0) {
+          unsigned m = wm, sel = 0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (q < nsel) {
+              sel |= m & (0u - m);
+              m &= m - 1u;
+            }
+          umt |= sel << (4 * j);
+          first_slot = As + l0 - 1 + a_t;
+        }
       }
-      A -= k == K_PAD ? 0 : kind_delta(k);
+      const int ma = As + (int)((e >> 8) & 15u) - 4;
+      suf = suf < ma ? suf : ma;
+      A = As;
     }
   }
   int* slice_pos = a.ws.slice_pos + boff;

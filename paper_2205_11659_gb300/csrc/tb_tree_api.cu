@@ -128,7 +128,7 @@ tb_status tb_tree_scan_affine_backward_reuse(const uint8_t* kind, int64_t n, int
   void* world = b + L.world;
   void* acc = b + L.acc;
   TB_PHASE_MARK(s);
-  k_jchain<MonoidAffine><<<w.TJ, TNT, 0, s>>>(w, local, d_status);
+  k_jchain<MonoidAffine><<<w.TJ, JNT, 0, s>>>(w, local, d_status);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   st = launch_down_tiles<MonoidAffine>(w, local, world, d_status, s);
   if (st != TB_OK) return st;

@@ -25,7 +25,7 @@
 //                prefix folds of the tile's exported chain (below)
 //
 // Joints are processed in tiles of JT = 1024 consecutive joints, one block of
-// TNT threads each; thread c owns the chunk of JC = 4 joints [c*JC, c*JC+JC).
+// JNT threads each; thread c owns the chunk of JC = 4 joints [c*JC, c*JC+JC).
 //
 // DOWN (root-path fold, ancestor on the left, Sec. 6.1):
 //   * A joint whose subtree runs past the end of its chunk (or tile) is
@@ -65,8 +65,13 @@ constexpr int TNW = TNT / 32;
 constexpr int TKPT = 16;
 constexpr int TTILE = TNT * TKPT;
 constexpr int JC = 4;          // joints per thread
-constexpr int JT = TNT * JC;    // joints per tile
-constexpr int NCH = TNT;        // chunks per tile
+#ifndef TB_TREE_JNT
+#define TB_TREE_JNT 256
+#endif
+constexpr int JNT = TB_TREE_JNT;  // threads per joint tile
+constexpr int JNW = JNT / 32;
+constexpr int JT = JNT * JC;    // joints per tile
+constexpr int NCH = JNT;        // chunks per tile
 constexpr int NO_CHAIN = -2;   // tile without exported joints
 constexpr int kMaxJumpRounds = 40;
 constexpr int STRUCT_MAGIC = 0x54425354;  // header word of a complete joint structure
@@ -255,6 +260,26 @@ struct MonoidOp {
 __host__ __device__ __forceinline__ int jslot(int k) { return k + k / JC; }
 constexpr int JSLOTS = JT + JT / JC;
 
+// The values of joints [R0, R0 + cnt) into their shared slots: asynchronous
+// 16-byte copies when a value is whole 16-byte words (each warp copies one
+// contiguous run; wait with cp_async_wait_all before the next barrier),
+// else plain loads.
+template <class M>
+__device__ __forceinline__ void stage_tile_values(typename M::V* s_val, const void* in, int R0, int cnt) {
+  using V = typename M::V;
+  if constexpr (sizeof(V) % 16 == 0) {
+    constexpr int WPV = (int)(sizeof(V) / 16);
+    const float4* src = reinterpret_cast<const float4*>(in) + (int64_t)R0 * WPV;
+    for (int f = threadIdx.x; f < cnt * WPV; f += blockDim.x) {
+      const int k = f / WPV;
+      cp_async16(reinterpret_cast<float4*>(s_val + jslot(k)) + (f - k * WPV), src + f);
+    }
+    cp_async_commit();
+  } else {
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) s_val[jslot(k)] = M::load(in, (int64_t)R0 + k);
+  }
+}
+
 // ------------------------------------------------------------- workspace
 struct TreeWs {
   // element level
@@ -348,11 +373,11 @@ __global__ void __launch_bounds__(TNT) k_tdepth(const uint8_t* __restrict__ kind
   int tot_o, tot_c, tile_mn;
   const int ex_o = block_excl_scan<TNW>(co, 0, OpAdd(), s_scr, &tot_o);
   const int ex_c = block_excl_scan<TNW>(cc, 0, OpAdd(), s_scr, &tot_c);
+  if (tid == 0 && t != w.withhold) st_release_u64(w.lb + t, oc_pack(1u, (unsigned)tot_o, (unsigned)tot_c));
   block_excl_scan<TNW>(ex_o - ex_c + mn, INT_MAX, OpMin(), s_scr, &tile_mn);
   if (warp_id() == 0) {
     const int lane = lane_id();
     unsigned long long* lb = w.lb;
-    if (lane == 0 && t != w.withhold) st_release_u64(lb + t, oc_pack(1u, (unsigned)tot_o, (unsigned)tot_c));
     unsigned xo = 0, xc = 0;
     bool timed_out = false;
     for (int hi = t - 1; hi >= 0; hi -= 32) {
@@ -412,8 +437,8 @@ __global__ void __launch_bounds__(TNT) k_tdepth(const uint8_t* __restrict__ kind
 }
 
 // Per joint tile: inclusive prefix and suffix minima of jdepth, tile minimum.
-__global__ void __launch_bounds__(TNT) k_jminmax(TreeWs w) {
-  __shared__ int s_scr[TNW + 1];
+__global__ void __launch_bounds__(JNT) k_jminmax(TreeWs w) {
+  __shared__ int s_scr[JNW + 1];
   if (*w.status != ST_OK) return;  // the joint depths are not valid
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT, cnt = min(JT, w.J - R0);
@@ -426,8 +451,8 @@ __global__ void __launch_bounds__(TNT) k_jminmax(TreeWs w) {
     mn = mn < d[i] ? mn : d[i];
   }
   int all;
-  int pre = block_excl_scan<TNW>(mn, INT_MAX, OpMin(), s_scr, &all);
-  int suf = block_excl_suffix_min<TNW>(mn, s_scr);
+  int pre = block_excl_scan<JNW>(mn, INT_MAX, OpMin(), s_scr, &all);
+  int suf = block_excl_suffix_min<JNW>(mn, s_scr);
   int sv[JC];
 #pragma unroll
   for (int i = JC - 1; i >= 0; --i) {
@@ -489,7 +514,7 @@ __device__ __forceinline__ void export_chain(const TreeWs& w, const void* in, in
   using V = typename M::V;
   const int tid = threadIdx.x, R0 = t * JT;
   int nx_all;
-  const int off = block_excl_scan<TNW>(popc(xm), 0, OpAdd(), s_scri, &nx_all);
+  const int off = block_excl_scan<JNW>(popc(xm), 0, OpAdd(), s_scri, &nx_all);
   {
     int o = off;
 #pragma unroll
@@ -515,22 +540,22 @@ __device__ __forceinline__ void export_chain(const TreeWs& w, const void* in, in
 // Parent and subtree end of every joint of the tile; with CHAIN, also the
 // prefix folds of the tile's exported chain (the input of the DOWN scan).
 template <class M, bool CHAIN>
-__global__ void __launch_bounds__(TNT) k_jstruct(TreeWs w, const void* __restrict__ in) {
+__global__ void __launch_bounds__(JNT) k_jstruct(TreeWs w, const void* __restrict__ in) {
   using V = typename M::V;
   __shared__ int s_tree[2 * JT];
   __shared__ int s_rep[JT];
   __shared__ int s_q[2 * JT];
   __shared__ int s_nq;
-  __shared__ int s_scri[TNW + 1];
+  __shared__ int s_scri[JNW + 1];
   if (*w.status != ST_OK) return;
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT, R1 = R0 + JT;
   const int cnt = min(JT, w.J - R0);
-  for (int k = tid; k < JT; k += TNT) s_tree[JT + k] = k < cnt ? w.jdepth[R0 + k] : INT_MAX;
+  for (int k = tid; k < JT; k += JNT) s_tree[JT + k] = k < cnt ? w.jdepth[R0 + k] : INT_MAX;
   if (tid == 0) s_nq = 0;
   __syncthreads();
   for (int h = JT / 2; h >= 1; h >>= 1) {
-    for (int i = h + tid; i < 2 * h; i += TNT) {
+    for (int i = h + tid; i < 2 * h; i += JNT) {
       const int a = s_tree[2 * i], b = s_tree[2 * i + 1];
       s_tree[i] = a < b ? a : b;
     }
@@ -635,7 +660,7 @@ __global__ void __launch_bounds__(TNT) k_jstruct(TreeWs w, const void* __restric
   // first), then the position in that tile's monotone prefix minima (first
   // position <= thr) or suffix minima (last position <= thr) by an 8-way
   // search (eight independent probes per round).
-  for (int qi = tid; qi < s_nq; qi += TNT) {
+  for (int qi = tid; qi < s_nq; qi += JNT) {
     const int qv = s_q[qi];
     const bool is_end = ((qv >> 30) & 1) != 0;
     const int k = qv & ((1 << 30) - 1);
@@ -712,9 +737,9 @@ __global__ void __launch_bounds__(TNT) k_jstruct(TreeWs w, const void* __restric
 // jend already in the workspace, checked against the header): the prefix
 // folds of the tile's exported chain, as k_jstruct<M, true> computes them.
 template <class M>
-__global__ void __launch_bounds__(TNT) k_jchain(TreeWs w, const void* __restrict__ in, int* status) {
+__global__ void __launch_bounds__(JNT) k_jchain(TreeWs w, const void* __restrict__ in, int* status) {
   __shared__ int s_list[JT];
-  __shared__ int s_scri[TNW + 1];
+  __shared__ int s_scri[JNW + 1];
   if (*w.status != ST_OK) return;
   if (w.hdr[0] != STRUCT_MAGIC || w.hdr[1] != w.n || w.hdr[2] != w.J) {
     if (threadIdx.x == 0) atomic_cas_i32(status, ST_OK, ST_INVALID);
@@ -818,7 +843,7 @@ constexpr size_t down_tile_smem() {
 }
 
 template <class M>
-__global__ void __launch_bounds__(TNT, 2) k_down_tile(TreeWs w, const void* __restrict__ in,
+__global__ void __launch_bounds__(JNT, 2) k_down_tile(TreeWs w, const void* __restrict__ in,
                                                      void* __restrict__ out) {
   using V = typename M::V;
   TB_DYNAMIC_SMEM(smem);
@@ -830,9 +855,11 @@ __global__ void __launch_bounds__(TNT, 2) k_down_tile(TreeWs w, const void* __re
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT;
   const int cnt = min(JT, w.J - R0);
-  for (int k = tid; k < cnt; k += TNT) {
-    s_val[jslot(k)] = M::load(in, R0 + k);
-    s_anc[k] = w.jparent[R0 + k];
+  stage_tile_values<M>(s_val, in, R0, cnt);
+#pragma unroll
+  for (int i = 0; i < JT / JNT; ++i) {
+    const int k = tid + i * JNT;
+    if (k < cnt) s_anc[k] = w.jparent[R0 + k];
   }
   const int c0 = tid * JC;
   const int cend = R0 + c0 + JC;  // global end of the chunk
@@ -840,6 +867,7 @@ __global__ void __launch_bounds__(TNT, 2) k_down_tile(TreeWs w, const void* __re
 #pragma unroll
   for (int i = 0; i < JC; ++i)
     if (c0 + i < cnt && w.jend[R0 + c0 + i] > cend) xm |= 1u << i;
+  cp_async_wait_all();
   __syncthreads();
 
   // In-chunk walk: fold relative to the nearest ancestor outside the chunk.
@@ -916,7 +944,7 @@ __global__ void __launch_bounds__(TNT, 2) k_down_tile(TreeWs w, const void* __re
     }
   }
   __syncthreads();
-  for (int k = tid; k < cnt; k += TNT) M::store(out, R0 + k, s_val[jslot(k)]);
+  for (int k = tid; k < cnt; k += JNT) M::store(out, R0 + k, s_val[jslot(k)]);
 }
 
 // ------------------------------------------------------------- adjoint
@@ -1050,7 +1078,7 @@ constexpr size_t up_tile_smem() {
 }
 
 template <class M, class Values, class Finish>
-__global__ void __launch_bounds__(TNT, 2) k_up_tile(TreeWs w, Values values, void* __restrict__ out,
+__global__ void __launch_bounds__(JNT, 2) k_up_tile(TreeWs w, Values values, void* __restrict__ out,
                                                    Finish fin) {
   using V = typename M::V;
   TB_DYNAMIC_SMEM(smem);
@@ -1061,9 +1089,13 @@ __global__ void __launch_bounds__(TNT, 2) k_up_tile(TreeWs w, Values values, voi
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT;
   const int cnt = min(JT, w.J - R0);
-  for (int k = tid; k < cnt; k += TNT) {
-    s_val[jslot(k)] = values(R0 + k);
-    s_end[k] = w.jend[R0 + k] - R0;
+#pragma unroll
+  for (int i = 0; i < JT / JNT; ++i) {  // unrolled: every load of the tile in flight at once
+    const int k = tid + i * JNT;
+    if (k < cnt) {
+      s_val[jslot(k)] = values(R0 + k);
+      s_end[k] = w.jend[R0 + k] - R0;
+    }
   }
   __syncthreads();
   const int c0 = tid * JC, ce = c0 + JC;
@@ -1112,12 +1144,12 @@ __global__ void __launch_bounds__(TNT, 2) k_up_tile(TreeWs w, Values values, voi
   }
   // The chunk tree, for subtrees of earlier tiles ending here (their end
   // tile's prefix over whole chunks) and for the tile total.
-  for (int i = tid; i < 2 * NCH; i += TNT)
+  for (int i = tid; i < 2 * NCH; i += JNT)
     if (i > 0) M::store(w.ctree, (int64_t)t * 2 * NCH + i, s_tree[i]);
   __syncthreads();  // every chunk's folds are complete before they are stored
   // Store the folds (with a finish, only the partial folds of the subtrees
   // leaving the tile are needed later; the others are finished here).
-  for (int k = tid; k < cnt; k += TNT) {
+  for (int k = tid; k < cnt; k += JNT) {
     const V A = s_val[jslot(k)];
     if (!Finish::active || s_end[k] > JT) M::store(out, R0 + k, A);
     if (Finish::active && s_end[k] <= JT) fin(w, R0 + k, A);

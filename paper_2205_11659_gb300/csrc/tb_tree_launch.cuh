@@ -163,7 +163,7 @@ inline tb_status prelude(const uint8_t* kind, int64_t n, int J, const TreeLayout
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   if (J > 0) {
     TB_PHASE_MARK(s);
-    k_jminmax<<<w.TJ, TNT, 0, s>>>(w);
+    k_jminmax<<<w.TJ, JNT, 0, s>>>(w);
     if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
     TB_PHASE_MARK(s);
     k_jmin_tree<<<1, 1024, 0, s>>>(w);
@@ -176,7 +176,7 @@ inline tb_status prelude(const uint8_t* kind, int64_t n, int J, const TreeLayout
 template <class M, bool CHAIN>
 tb_status launch_jstruct(const TreeWs& w, const void* in, cudaStream_t s) {
   TB_PHASE_MARK(s);
-  k_jstruct<M, CHAIN><<<w.TJ, TNT, 0, s>>>(w, in);
+  k_jstruct<M, CHAIN><<<w.TJ, JNT, 0, s>>>(w, in);
   return cudaGetLastError() == cudaSuccess ? TB_OK : TB_ERR_CUDA;
 }
 
@@ -199,7 +199,7 @@ tb_status launch_down_tiles(const TreeWs& w, const void* in, void* out, int32_t*
   constexpr size_t smem = down_tile_smem<M>();
   static std::atomic<unsigned long long> attr_set{0};
   if (smem_limit_once(attr_set, k_down_tile<M>, smem) != cudaSuccess) return TB_ERR_CUDA;
-  k_down_tile<M><<<w.TJ, TNT, smem, s>>>(w, in, out);
+  k_down_tile<M><<<w.TJ, JNT, smem, s>>>(w, in, out);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   return TB_OK;
 }
@@ -217,7 +217,7 @@ tb_status launch_up(const TreeWs& w, Values values, void* out, Finish fin, cudaS
   constexpr size_t smem = up_tile_smem<M>();
   static std::atomic<unsigned long long> attr_set{0};
   if (smem_limit_once(attr_set, k_up_tile<M, Values, Finish>, smem) != cudaSuccess) return TB_ERR_CUDA;
-  k_up_tile<M, Values, Finish><<<w.TJ, TNT, smem, s>>>(w, values, out, fin);
+  k_up_tile<M, Values, Finish><<<w.TJ, JNT, smem, s>>>(w, values, out, fin);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   TB_PHASE_MARK(s);
   k_up_tiles<M><<<1, 1024, 0, s>>>(w);
