@@ -539,9 +539,17 @@ __device__ __forceinline__ void export_chain(const TreeWs& w, const void* in, in
 
 // Parent and subtree end of every joint of the tile; with CHAIN, also the
 // prefix folds of the tile's exported chain (the input of the DOWN scan).
+// Dynamic shared memory of k_jstruct: a copy of the tiles' min tree when it
+// is small (its searches then stay in shared memory), else none.
+constexpr int kJTreeSmemPJ = 2048;
+__host__ __device__ constexpr size_t jstruct_smem(int PJ) {
+  return (PJ >= 2 && PJ <= kJTreeSmemPJ) ? (size_t)PJ * 2 * sizeof(int) : 0;
+}
+
 template <class M, bool CHAIN>
 __global__ void __launch_bounds__(JNT) k_jstruct(TreeWs w, const void* __restrict__ in) {
   using V = typename M::V;
+  TB_DYNAMIC_SMEM(dsm);
   __shared__ int s_tree[2 * JT];
   __shared__ int s_rep[JT];
   __shared__ int s_q[2 * JT];
@@ -551,6 +559,14 @@ __global__ void __launch_bounds__(JNT) k_jstruct(TreeWs w, const void* __restric
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT, R1 = R0 + JT;
   const int cnt = min(JT, w.J - R0);
+  // the tiles' min tree, copied while the tile's own tree is built
+  const bool gt_smem = jstruct_smem(w.PJ) != 0;
+  int* s_gt = reinterpret_cast<int*>(dsm);
+  if (gt_smem) {
+    for (int f = tid; f < w.PJ / 2; f += JNT) cp_async16(s_gt + 4 * f, w.g_tree + 4 * f);
+    cp_async_commit();
+  }
+  const int* gt = gt_smem ? s_gt : w.g_tree;
   for (int k = tid; k < JT; k += JNT) s_tree[JT + k] = k < cnt ? w.jdepth[R0 + k] : INT_MAX;
   if (tid == 0) s_nq = 0;
   __syncthreads();
@@ -561,69 +577,46 @@ __global__ void __launch_bounds__(JNT) k_jstruct(TreeWs w, const void* __restric
     }
     __syncthreads();
   }
-  // In the tile: parent = the previous joint if it is shallower, else the
-  // last shallower joint (tree search); end = the next joint if it is not
-  // deeper, else the first later joint not deeper (tree search).
+  // In the tile: parent = the last earlier joint that is shallower, end = the
+  // first later joint that is not deeper.  Inside the thread's chunk of JC
+  // joints by direct comparison; else in the nearest chunk that holds one,
+  // found by the up/down search of the tree's level of chunk minima (node
+  // NCH + c covers chunk c), then by a scan of that chunk's JC depths.
   int par[JC], end[JC], dep[JC], rep[JC];
-  // The JC searches of each kind run in lockstep with fixed trip counts, so
-  // their dependent shared-memory loads overlap.
-  int pl[JC], pr[JC], pn[JC];  // parent: last earlier leaf <= d-1 (climb, then descend)
-  int en[JC];                  // end: first later leaf <= d (0 = none)
-  bool ef[JC];
+  const int c0 = tid * JC;
 #pragma unroll
   for (int i = 0; i < JC; ++i) {
-    const int k = tid * JC + i;
     par[i] = end[i] = rep[i] = -1;
-    dep[i] = k < cnt ? s_tree[JT + k] : INT_MAX;
+    dep[i] = c0 + i < cnt ? s_tree[JT + c0 + i] : INT_MAX;
+  }
+#pragma unroll
+  for (int i = 0; i < JC; ++i) {
+#pragma unroll
+    for (int j = i - 1; j >= 0; --j)
+      if (par[i] < 0 && dep[j] < dep[i]) par[i] = R0 + c0 + j;
+#pragma unroll
+    for (int j = i + 1; j < JC; ++j)
+      if (end[i] < 0 && dep[j] <= dep[i]) end[i] = R0 + c0 + j;
+  }
+#pragma unroll
+  for (int i = 0; i < JC; ++i) {
+    if (c0 + i >= cnt) continue;
     const int d = dep[i];
-    // shortcuts: the previous joint is the parent when shallower, the next
-    // joint is the end when not deeper
-    const bool pdone = k >= cnt || k == 0 || s_tree[JT + k - 1] < d;
-    if (k < cnt && k > 0 && s_tree[JT + k - 1] < d) par[i] = R0 + k - 1;
-    pl[i] = JT;
-    pr[i] = pdone ? JT : JT + k;  // empty range when done
-    pn[i] = -1;
-    const bool edone = k >= cnt || (k + 1 < cnt && s_tree[JT + k + 1] <= d);
-    if (k < cnt && k + 1 < cnt && s_tree[JT + k + 1] <= d) end[i] = R0 + k + 1;
-    en[i] = (!edone && k + 1 < JT) ? JT + k + 1 : 0;
-    ef[i] = false;
-  }
-  constexpr int LOGJT = ilog2(JT);
-  for (int it = 0; it <= LOGJT; ++it) {
+    if (par[i] < 0 && d > 1) {
+      const int cc = tree_last_le(s_tree, NCH, tid, d - 1);
+      if (cc >= 0) {
 #pragma unroll
-    for (int i = 0; i < JC; ++i) {
-      if (pn[i] < 0 && pl[i] < pr[i]) {
-        if (pr[i] & 1) {
-          --pr[i];
-          if (s_tree[pr[i]] <= dep[i] - 1) pn[i] = pr[i];
-        }
-        if (pn[i] < 0) {
-          pl[i] >>= 1;
-          pr[i] >>= 1;
-        }
+        for (int q = JC - 1; q >= 0; --q)
+          if (par[i] < 0 && s_tree[JT + cc * JC + q] <= d - 1) par[i] = R0 + cc * JC + q;
       }
     }
-  }
-  for (int it = 0; it < 2 * LOGJT + 1; ++it) {
+    if (end[i] < 0) {
+      const int cc = tree_first_le(s_tree, NCH, tid + 1, d);
+      if (cc >= 0) {
 #pragma unroll
-    for (int i = 0; i < JC; ++i) {
-      if (en[i] > 0 && !ef[i]) {
-        if (s_tree[en[i]] <= dep[i]) {
-          ef[i] = true;
-        } else {
-          // next subtree to the right: drop the trailing right-child steps
-          const int t1 = lowest_set(~(unsigned)en[i]);
-          const int up = en[i] >> t1;
-          en[i] = up == 0 ? 0 : up + 1;
-        }
+        for (int q = 0; q < JC; ++q)
+          if (end[i] < 0 && s_tree[JT + cc * JC + q] <= d) end[i] = R0 + cc * JC + q;
       }
-    }
-  }
-  for (int it = 0; it < LOGJT; ++it) {
-#pragma unroll
-    for (int i = 0; i < JC; ++i) {
-      if (pn[i] >= 1 && pn[i] < JT) pn[i] = s_tree[2 * pn[i] + 1] <= dep[i] - 1 ? 2 * pn[i] + 1 : 2 * pn[i];
-      if (ef[i] && en[i] < JT) en[i] = s_tree[2 * en[i]] <= dep[i] ? 2 * en[i] : 2 * en[i] + 1;
     }
   }
   // What the tile cannot answer goes to a queue served below.  All joints of
@@ -636,25 +629,22 @@ __global__ void __launch_bounds__(JNT) k_jstruct(TreeWs w, const void* __restric
     const int k = tid * JC + i;
     if (k >= cnt) continue;
     const int d = dep[i];
-    if (par[i] < 0) {
-      if (pn[i] >= 0) {
-        par[i] = R0 + pn[i] - JT;
-      } else if (d > 1) {
-        rep[i] = tree_first_le(s_tree, JT, 0, d);
-        if (rep[i] == k) s_rep[k] = atomicAdd(&s_nq, 1);
-        if (rep[i] == k) s_q[s_rep[k]] = k;
-      }
+    if (par[i] < 0 && d > 1) {
+      // the first joint of the tile at depth <= d
+      const int cr = tree_first_le(s_tree, NCH, 0, d);
+#pragma unroll
+      for (int q = 0; q < JC; ++q)
+        if (rep[i] < 0 && s_tree[JT + cr * JC + q] <= d) rep[i] = cr * JC + q;
+      if (rep[i] == k) s_rep[k] = atomicAdd(&s_nq, 1);
+      if (rep[i] == k) s_q[s_rep[k]] = k;
     }
     if (end[i] < 0) {
-      if (ef[i]) {
-        end[i] = R0 + en[i] - JT;
-      } else {
-        const int slot = atomicAdd(&s_nq, 1);
-        s_q[slot] = k | (1 << 30);
-        end[i] = -2 - slot;
-      }
+      const int slot = atomicAdd(&s_nq, 1);
+      s_q[slot] = k | (1 << 30);
+      end[i] = -2 - slot;
     }
   }
+  cp_async_wait_all();
   __syncthreads();
   // One question per thread, all in parallel: find the tile (the neighbour
   // first), then the position in that tile's monotone prefix minima (first
@@ -668,11 +658,11 @@ __global__ void __launch_bounds__(JNT) k_jstruct(TreeWs w, const void* __restric
     const int thr = is_end ? d : d - 1;
     int tt;
     if (is_end) {
-      if (t + 1 < w.TJ && w.g_tree[w.PJ + t + 1] <= thr) tt = t + 1;
-      else tt = tree_first_le(w.g_tree, w.PJ, t + 1, thr);
+      if (t + 1 < w.TJ && gt[w.PJ + t + 1] <= thr) tt = t + 1;
+      else tt = tree_first_le(gt, w.PJ, t + 1, thr);
     } else {
-      if (t > 0 && w.g_tree[w.PJ + t - 1] <= thr) tt = t - 1;
-      else tt = tree_last_le(w.g_tree, w.PJ, t, thr);
+      if (t > 0 && gt[w.PJ + t - 1] <= thr) tt = t - 1;
+      else tt = tree_last_le(gt, w.PJ, t, thr);
     }
     int res = is_end ? w.J : -1;
     if (tt >= 0) {
