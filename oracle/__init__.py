@@ -75,6 +75,7 @@ def _load():
             lib.orc_tree_scan_box.argtypes = [i32, i32, p, i64, p, p]
             lib.orc_affine_forward.argtypes = [p, i64, p, p]
             lib.orc_rigid_scan.argtypes = [ctypes.c_int, p, i64, p, p]
+            lib.orc_tree_structure.argtypes = [p, i64, p, p, p]
             lib.orc_affine_up.argtypes = [p, i64, p, p]
             lib.orc_affine_loss.argtypes = [p, i64, p, p, i64, p]
             lib.orc_affine_backward.argtypes = [p, i64, p, p, p, i64]
@@ -83,7 +84,7 @@ def _load():
                       lib.orc_tree_scan_i32,
                       lib.orc_tree_scan_box, lib.orc_affine_forward,
                       lib.orc_affine_up, lib.orc_affine_loss,
-                      lib.orc_affine_backward, lib.orc_rigid_scan):
+                      lib.orc_affine_backward, lib.orc_rigid_scan, lib.orc_tree_structure):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -223,6 +224,17 @@ def rigid_scan(direction, kind, values):
     out = np.zeros_like(v)
     st = _load().orc_rigid_scan(int(direction), _ptr(k), k.size, _ptr(v), _ptr(out))
     return st, out
+
+
+def tree_structure(kind):
+    """(status, depth, parent, left_sibling) per joint (the r-th open): int32."""
+    k = _kinds(kind)
+    J = _num_opens(k)
+    d = np.zeros(J, np.int32)
+    p_ = np.zeros(J, np.int32)
+    l = np.zeros(J, np.int32)
+    st = _load().orc_tree_structure(_ptr(k), k.size, _ptr(d), _ptr(p_), _ptr(l))
+    return st, d, p_, l
 
 
 def affine_loss(kind, local, W):

@@ -24,6 +24,9 @@
  *                              (root-path products) and their adjoint, fp64
  *   orc_rigid_scan          -- the same for rigid transforms (unit quaternion
  *                              and translation), DOWN and UP, fp64
+ *   orc_tree_structure      -- the joint-level depth, parent and left-sibling
+ *                              vectors (Sec. 13 relates the matching to parent
+ *                              and left-sibling vectors of a depth vector)
  *
  * Element kinds: 0 = LEAF, 1 = OPEN_CLIP, 2 = OPEN_BLEND, 3 = CLOSE.
  * A box is 4 floats (x0, y0, x1, y1).
@@ -333,6 +336,38 @@ int orc_tree_scan_i32(int dir, const uint8_t* kind, int64_t n,
   if (st == ORC_OK && sp != 0) st = ORC_UNBALANCED;
   free(rank);
   free(acc);
+  return st;
+}
+
+/* Joint r is the r-th open.  depth[r] = the number of opens enclosing it
+ * plus one; parent[r] = the joint of the enclosing open, -1 at a root;
+ * left_sibling[r] = the previous joint with the same parent (roots are the
+ * children of one virtual root), -1 for a first child.  Any output may be
+ * NULL. */
+int orc_tree_structure(const uint8_t* kind, int64_t n, int32_t* depth, int32_t* parent,
+                       int32_t* left_sibling) {
+  int st = check_kinds(kind, n);
+  if (st) return st;
+  int64_t* joint = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));     /* joint on the stack */
+  int64_t* lastc = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 2));     /* last child per level */
+  int64_t sp = 0, r = 0;
+  lastc[0] = -1;
+  for (int64_t i = 0; i < n; ++i) {
+    if (is_open(kind[i])) {
+      if (depth) depth[r] = (int32_t)(sp + 1);
+      if (parent) parent[r] = sp > 0 ? (int32_t)joint[sp - 1] : -1;
+      if (left_sibling) left_sibling[r] = (int32_t)lastc[sp];
+      lastc[sp] = r;
+      joint[sp++] = r++;
+      lastc[sp] = -1;
+    } else if (kind[i] == K_CLOSE) {
+      if (sp == 0) { st = ORC_UNBALANCED; break; }
+      --sp;
+    }
+  }
+  if (st == ORC_OK && sp != 0) st = ORC_UNBALANCED;
+  free(joint);
+  free(lastc);
   return st;
 }
 

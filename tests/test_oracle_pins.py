@@ -749,3 +749,66 @@ def test_rigid_scan_hamilton_rules_and_translation_sums():
         assert np.array_equal(down[rank[int(o)], 4:7], t)
         sub = [rank[int(j)] for j in opens if o <= j < mat[o]]
         assert np.array_equal(up[rank[int(o)], 4:7], v[sub, 4:7].sum(0))
+
+
+def _structure_brute(k):
+    """Depth, parent and left sibling of every joint by brute force: the
+    depth counts the opens before it minus the closes before it, plus one;
+    the parent is the last earlier joint one level up (everything between a
+    parent and its child is inside the parent); the left sibling is the last
+    earlier joint with the same parent."""
+    opens = [i for i in range(k.size) if k[i] in (1, 2)]
+    delta = np.where((k == 1) | (k == 2), 1, np.where(k == 3, -1, 0))
+    depth = [int(delta[:o].sum()) + 1 for o in opens]
+    parent = []
+    for r, d in enumerate(depth):
+        p = -1
+        for q in range(r - 1, -1, -1):
+            if depth[q] == d - 1:
+                p = q
+                break
+            if depth[q] < d - 1:
+                break
+        parent.append(p)
+    left = []
+    for r in range(len(opens)):
+        q = -1
+        for j in range(r - 1, -1, -1):
+            if parent[j] == parent[r] and depth[j] == depth[r]:
+                q = j
+                break
+        left.append(q)
+    return np.array(depth), np.array(parent), np.array(left)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_tree_structure_brute_force(seed):
+    for k in (inputs.skeleton_kinds(150, seed, max_depth=6), inputs.random_walk_kinds(400, seed),
+              np.concatenate([inputs.skeleton_kinds(40, seed + 10), inputs.skeleton_kinds(30, seed + 20)])):
+        st, d, p, l = oracle.tree_structure(k)
+        assert st == oracle.OK
+        bd, bp, bl = _structure_brute(k)
+        assert np.array_equal(d, bd) and np.array_equal(p, bp) and np.array_equal(l, bl)
+        # the depth is also the ADD root-path fold of ones
+        _, d2 = oracle.tree_scan_i32(0, k, np.ones(d.size, np.int32))
+        assert np.array_equal(d, d2)
+
+
+def test_tree_structure_closed_forms():
+    m = 9
+    # a chain: depth r + 1, parent r - 1, no siblings
+    st, d, p, l = oracle.tree_structure(np.array([1] * m + [3] * m, np.uint8))
+    assert st == oracle.OK
+    assert np.array_equal(d, np.arange(1, m + 1)) and np.array_equal(p, np.arange(-1, m - 1))
+    assert np.array_equal(l, np.full(m, -1))
+    # m roots one after another: each root's left sibling is the one before
+    st, d, p, l = oracle.tree_structure(np.array([2, 0, 3] * m, np.uint8))
+    assert np.array_equal(d, np.ones(m)) and np.array_equal(p, np.full(m, -1))
+    assert np.array_equal(l, np.arange(-1, m - 1))
+    # a star: one root with m children
+    st, d, p, l = oracle.tree_structure(np.array([1] + [2, 3] * m + [3], np.uint8))
+    assert np.array_equal(p, np.array([-1] + [0] * m))
+    assert np.array_equal(l, np.array([-1, -1] + list(range(1, m))))
+    # errors
+    assert oracle.tree_structure(np.array([1, 3, 3], np.uint8))[0] == oracle.UNBALANCED
+    assert oracle.tree_structure(np.array([1, 5, 3], np.uint8))[0] == oracle.BAD_KIND
