@@ -229,15 +229,34 @@ tb_status tb_tree_scan_affine_backward_reuse(const uint8_t* kind, int64_t n,
                                              size_t ws_bytes, int32_t* d_status,
                                              void* stream);
 
+/* Joint-level structure of the tree the kind stream describes: the depth,
+ * parent and left-sibling vectors (the paper relates parentheses matching
+ * to deriving parent and left-sibling vectors from a depth vector, Sec. 12).
+ * Joint r is the r-th open of the stream (pre-order).  For every joint:
+ *   depth_out[r]         1 at a root, one more than its parent otherwise;
+ *   parent_out[r]        the parent joint, -1 at a root;
+ *   left_sibling_out[r]  the previous joint with the same parent, -1 for a
+ *                        first child (the roots of a forest are siblings).
+ * Each output is a device array of num_joints int32, or NULL to skip it.
+ * num_joints must be the number of opens in the stream (else
+ * TB_ERR_INVALID_ARG in d_status).  ws: at least
+ * tb_workspace_size(TB_OP_TREE_SCAN, n) bytes.  Errors of the stream are
+ * reported in d_status as for tb_tree_scan; the outputs are then undefined. */
+tb_status tb_tree_structure(const uint8_t* kind, int64_t n, int64_t num_joints,
+                            int32_t* depth_out, int32_t* parent_out,
+                            int32_t* left_sibling_out, void* ws, size_t ws_bytes,
+                            int32_t* d_status, void* stream);
+
 /* Tracing hook.  After tb_set_phase_events(events, k) (1 <= k <= 16) every
  * later call on this host thread records, on its own stream, events[0],
  * events[1], ... in launch order: one before each kernel of the call and
  * one after its last kernel, until the k events run out.  The matching
  * calls (tb_match_parens, tb_bboxes, tb_bboxes_batched) use five: before the
  * tile-summary pass, the tile-level resolve, the main tile pass and the
- * cross-tile union step, and at the end.  The tree scans start with the same
- * five for their matching pass, then the rank pass, the joint pass and the
- * scan kernels in order.  events holds cudaEvent_t handles created by the
+ * cross-tile union step, and at the end.  The tree calls record one before
+ * each of their kernels (depth pass, tile minima, min tree over the tiles,
+ * structure pass, then the scan's own kernels) and one at the end.  events
+ * holds cudaEvent_t handles created by the
  * caller; tb_set_phase_events(NULL, 0) turns the hook off. */
 tb_status tb_set_phase_events(void* const* events, int num_events);
 

@@ -25,7 +25,7 @@
  *   orc_rigid_scan          -- the same for rigid transforms (unit quaternion
  *                              and translation), DOWN and UP, fp64
  *   orc_tree_structure      -- the joint-level depth, parent and left-sibling
- *                              vectors (Sec. 13 relates the matching to parent
+ *                              vectors (Sec. 12 relates the matching to parent
  *                              and left-sibling vectors of a depth vector)
  *
  * Element kinds: 0 = LEAF, 1 = OPEN_CLIP, 2 = OPEN_BLEND, 3 = CLOSE.

@@ -10,6 +10,6 @@ from .binding import (  # noqa: F401
     bboxes_clip, tb_bboxes_clip,
     match_parens, open_positions, tb_bboxes, tb_bboxes_batched, tb_match_parens, tb_open_positions,
     tb_set_phase_events, tb_tree_scan,
-    tb_tree_scan_affine_backward, tb_tree_scan_affine_backward_reuse, tb_version,
-    tb_workspace_size, tree_scan,
+    tb_tree_scan_affine_backward, tb_tree_scan_affine_backward_reuse, tb_tree_structure, tb_version,
+    tb_workspace_size, tree_scan, tree_structure,
 )

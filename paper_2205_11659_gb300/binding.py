@@ -89,10 +89,11 @@ def lib():
             L.tb_tree_scan_affine_backward_reuse.argtypes = [p, i64, i64, p, p, p, p, sz, p, p]
             L.tb_open_positions.argtypes = [p, i64, p, i64, p, p, sz, p, p]
             L.tb_bboxes_clip.argtypes = [p, p, p, i64, i64, p, p, p, p, p, sz, p, p]
+            L.tb_tree_structure.argtypes = [p, i64, i64, p, p, p, p, sz, p, p]
             for f in (L.tb_match_parens, L.tb_bboxes, L.tb_bboxes_batched, L.tb_set_phase_events,
                       L.tb_bboxes_static_ws, L.tb_tree_scan, L.tb_tree_scan_affine_backward,
                       L.tb_tree_scan_affine_backward_reuse, L.tb_open_positions,
-                      L.tb_bboxes_clip):
+                      L.tb_bboxes_clip, L.tb_tree_structure):
                 f.restype = i32
             L.tb_version.argtypes = []
             L.tb_version.restype = ctypes.c_char_p
@@ -189,6 +190,13 @@ def tb_tree_scan_affine_backward_reuse(kind, n, num_joints, local, grad_world, g
     return lib().tb_tree_scan_affine_backward_reuse(
         _ptr(kind), int(n), int(num_joints), _ptr(local), _ptr(grad_world), _ptr(grad_local),
         _ptr(ws), int(ws_bytes), _ptr(d_status), _stream(stream))
+
+
+def tb_tree_structure(kind, n, num_joints, depth_out, parent_out, left_sibling_out, ws, ws_bytes,
+                      d_status, stream=None):
+    return lib().tb_tree_structure(_ptr(kind), int(n), int(num_joints), _ptr(depth_out),
+                                   _ptr(parent_out), _ptr(left_sibling_out), _ptr(ws), int(ws_bytes),
+                                   _ptr(d_status), _stream(stream))
 
 
 def tb_debug_withhold_tile(tile):
@@ -446,6 +454,25 @@ def tree_scan(monoid, direction, kind, values, check=True):
     if check:
         check_status(ws, "tb_tree_scan")
     return out
+
+
+def tree_structure(kind, check=True):
+    """tb_tree_structure on a device kind tensor: (depth, parent,
+    left_sibling), three (J,) int32 tensors over the J opens of ``kind``."""
+    if not kind.is_cuda:
+        raise ValueError("tree_structure takes a CUDA tensor")
+    dev = kind.device
+    k = _on_device(kind, torch.uint8, "kind", dev)
+    n = k.numel()
+    J = int(((k == OPEN_CLIP) | (k == OPEN_BLEND)).sum().item())
+    outs = [torch.empty(J, dtype=torch.int32, device=dev) for _ in range(3)]
+    ws = workspace(dev)
+    nb = tb_workspace_size(TB_OP_TREE_SCAN, n)
+    _check(tb_tree_structure(k, n, J, outs[0], outs[1], outs[2], ws.get(nb), nb, ws.status),
+           "tb_tree_structure")
+    if check:
+        check_status(ws, "tb_tree_structure")
+    return tuple(outs)
 
 
 def affine_backward(kind, local, grad_world, check=True):

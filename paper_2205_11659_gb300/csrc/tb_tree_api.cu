@@ -139,4 +139,39 @@ tb_status tb_tree_scan_affine_backward_reuse(const uint8_t* kind, int64_t n, int
   return TB_OK;
 }
 
+tb_status tb_tree_structure(const uint8_t* kind, int64_t n, int64_t num_joints, int32_t* depth_out,
+                            int32_t* parent_out, int32_t* left_sibling_out, void* ws, size_t ws_bytes,
+                            int32_t* d_status, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tb_internal::phase_reset();
+  tb_status st = check_common(kind, n, num_joints, ws, d_status);
+  if (st != TB_OK) return st;
+  if ((depth_out != nullptr && !aligned(depth_out, 4)) || (parent_out != nullptr && !aligned(parent_out, 4)) ||
+      (left_sibling_out != nullptr && !aligned(left_sibling_out, 4)))
+    return TB_ERR_INVALID_ARG;
+  const TreeLayout L = tree_layout(n, false);
+  if (n > 0 && ws_bytes < L.total) return TB_ERR_WORKSPACE;
+  if (n == 0) return cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) == cudaSuccess ? TB_OK : TB_ERR_CUDA;
+  TreeWs w;
+  st = prelude(kind, n, (int)num_joints, L, ws, d_status, s, &w);
+  if (st != TB_OK || num_joints == 0) return st;
+  st = launch_jstruct<MonoidAddI32, false>(w, nullptr, s);
+  if (st != TB_OK) return st;
+  const size_t bytes = (size_t)num_joints * sizeof(int32_t);
+  if (depth_out != nullptr &&
+      cudaMemcpyAsync(depth_out, w.jdepth, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return TB_ERR_CUDA;
+  if (parent_out != nullptr &&
+      cudaMemcpyAsync(parent_out, w.jparent, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return TB_ERR_CUDA;
+  if (left_sibling_out != nullptr) {
+    if (cudaMemsetAsync(left_sibling_out, 0xff, bytes, s) != cudaSuccess) return TB_ERR_CUDA;  // -1
+    TB_PHASE_MARK(s);
+    k_left_sibling<<<grid_for(w.J, 256), 256, 0, s>>>(w, left_sibling_out);
+    if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
+  }
+  TB_PHASE_MARK(s);
+  return TB_OK;
+}
+
 }  // extern "C"

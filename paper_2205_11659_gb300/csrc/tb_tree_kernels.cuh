@@ -751,6 +751,19 @@ __global__ void __launch_bounds__(JNT) k_jchain(TreeWs w, const void* __restrict
   export_chain<M>(w, in, t, xm, first_par, s_list, s_scri);
 }
 
+// Left sibling of every joint (the previous joint with the same parent, -1
+// for a first child; the caller fills `left` with -1 first): the subtree of
+// joint q ends at jend[q], the first later joint not deeper than q; when that
+// joint is exactly as deep, everything between is inside q, so the two share
+// q's parent and q is its left sibling.  Each joint has at most one such q.
+__global__ void k_left_sibling(TreeWs w, int* __restrict__ left) {
+  if (*w.status != ST_OK) return;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < w.J; q += gridDim.x * blockDim.x) {
+    const int e = w.jend[q];
+    if (e < w.J && in_range(e, q + 1, w.J, w.status) && w.jdepth[e] == w.jdepth[q]) left[e] = q;
+  }
+}
+
 // ------------------------------------------------------------- DOWN
 // Pointer jumping over the tiles (one block): the fold at each tile's base is
 // the fold at its base's tile base times the base's chain prefix.  With SM

@@ -152,6 +152,16 @@ def test_tree_scan_argument_errors(lib):
     assert bwd(local=fake + 8) == b.TB_ERR_INVALID_ARG
     assert bwd(nb=1 << 10) == b.TB_ERR_WORKSPACE
 
+    def structure(J=5, n=10, kind=fake, d=fake, par=fake + 4096, left=fake + 8192, nb=big, st=fake):
+        return lib.tb_tree_structure(p(kind), n, J, p(d), p(par), p(left), p(fake), nb, p(st), None)
+
+    assert structure(J=6) == b.TB_ERR_INVALID_ARG
+    assert structure(n=-1, J=0) == b.TB_ERR_INVALID_ARG
+    assert structure(kind=fake + 1) == b.TB_ERR_INVALID_ARG
+    assert structure(left=fake + 2) == b.TB_ERR_INVALID_ARG  # misaligned output
+    assert structure(nb=16) == b.TB_ERR_WORKSPACE
+    assert structure(st=0) == b.TB_ERR_INVALID_ARG           # no status word
+
     def bwd_reuse(J=5, local=fake, g=fake + 4096, gl=fake + 8192, nb=big):
         return lib.tb_tree_scan_affine_backward_reuse(p(fake), 10, J, p(local), p(g), p(gl),
                                                       p(fake), nb, p(fake), None)

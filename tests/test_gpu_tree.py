@@ -132,6 +132,30 @@ def test_rigid(name, d):
         assert np.abs(np.linalg.norm(got[:, :4].astype(np.float64), axis=1) - 1.0).max() < 1e-4
 
 
+@pytest.mark.parametrize("name", list(STREAMS))
+def test_tree_structure(name):
+    """Joint depth, parent and left-sibling vectors, bit for bit."""
+    k = STREAMS[name]
+    d, p, l = binding.tree_structure(torch.from_numpy(k).cuda())
+    torch.cuda.synchronize()
+    st, od, op, ol = oracle.tree_structure(k)
+    assert st == oracle.OK
+    assert np.array_equal(d.cpu().numpy(), od)
+    assert np.array_equal(p.cpu().numpy(), op)
+    assert np.array_equal(l.cpu().numpy(), ol)
+
+
+def test_tree_structure_large_and_errors():
+    k = inputs.skeleton_kinds(1 << 20, 31)
+    d, p, l = binding.tree_structure(torch.from_numpy(k).cuda())
+    torch.cuda.synchronize()
+    st, od, op, ol = oracle.tree_structure(k)
+    assert np.array_equal(d.cpu().numpy(), od) and np.array_equal(p.cpu().numpy(), op)
+    assert np.array_equal(l.cpu().numpy(), ol)
+    with pytest.raises(binding.TBError):
+        binding.tree_structure(torch.tensor([1, 3, 3], dtype=torch.uint8, device="cuda"))
+
+
 def test_rigid_large_skeleton():
     k = inputs.skeleton_kinds(1 << 20, 42)
     J = n_opens(k)
