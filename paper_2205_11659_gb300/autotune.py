@@ -28,8 +28,8 @@ from . import _build
 # matcher of the matching-only pass: 0 = chunk walk, 1 = binary search over a
 # tree of depths, Fig. "core")
 CANDIDATES = [(256, 16, False, 0), (256, 16, True, 0), (256, 8, False, 0), (128, 16, False, 0),
-              (512, 8, False, 0), (64, 16, False, 0), (128, 16, True, 0), (128, 16, False, 1),
-              (256, 16, False, 1)]
+              (512, 8, False, 0), (64, 16, False, 0), (128, 16, True, 0), (128, 12, False, 0),
+              (256, 12, False, 0), (128, 16, False, 1), (256, 16, False, 1)]
 
 
 def _time_calls(call, reps):

@@ -38,7 +38,7 @@ constexpr bool PERSIST = TB_PERSIST != 0;
 constexpr int TILE = NT * KPT;
 constexpr int NW = NT / 32;
 static_assert(NT == 64 || NT == 128 || NT == 256 || NT == 512, "block size must be 64, 128, 256 or 512");
-static_assert(KPT == 8 || KPT == 16, "elements per thread must be 8 or 16");
+static_assert(KPT == 8 || KPT == 12 || KPT == 16, "elements per thread must be 8, 12 or 16");
 
 // Element kinds; K_PAD marks positions past the end of the stream.
 constexpr int K_LEAF = 0, K_CLIP = 1, K_BLEND = 2, K_CLOSE = 3, K_PAD = 4;

@@ -53,6 +53,11 @@ __device__ __forceinline__ bool load_kinds(const uint8_t* __restrict__ kind, int
       w[1] = v.y;
       w[2] = v.z;
       w[3] = v.w;
+    } else if constexpr (KPT == 12) {  // e0 a multiple of 12: three aligned words
+      const unsigned* q = reinterpret_cast<const unsigned*>(kind + e0);
+      w[0] = __ldg(q);
+      w[1] = __ldg(q + 1);
+      w[2] = __ldg(q + 2);
     } else {
       const uint2 v = ld_nc_u2(kind + e0);
       w[0] = v.x;
@@ -91,6 +96,11 @@ __device__ __forceinline__ bool load_kind_words(const uint8_t* __restrict__ kind
       wd[1] = v.y;
       wd[2] = v.z;
       wd[3] = v.w;
+    } else if constexpr (KPT == 12) {  // e0 a multiple of 12: three aligned words
+      const unsigned* q = reinterpret_cast<const unsigned*>(kind + e0);
+      wd[0] = __ldg(q);
+      wd[1] = __ldg(q + 1);
+      wd[2] = __ldg(q + 2);
     } else {
       const uint2 v = ld_nc_u2(kind + e0);
       wd[0] = v.x;
@@ -776,8 +786,13 @@ __device__ __forceinline__ OutRes out_lookup(const OutCtx& c, const SceneWs& ws,
 // tile through K3_TILE_DONE (a return, or a break to the next ticket).  The
 // matching-only pass is held to 64 registers a thread so that 1024 threads
 // per SM stay resident.
+// Blocks of the main pass that fit an SM together: five when a tile's box
+// staging leaves room for them (at most 1536 elements: 42 KB of shared memory
+// per block, and 96 registers per thread asked of the compiler), else two.
+constexpr int K3_MIN_BLOCKS = TILE <= 1536 && NT == 128 ? 5 : 2;
+
 template <bool HAS_BOX, bool BATCHED, bool CLIP = false>
-__global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a) {
+__global__ void __launch_bounds__(NT, HAS_BOX ? K3_MIN_BLOCKS : 1024 / NT) k3_tile(K3Args a) {
   TB_DYNAMIC_SMEM(smem);
   __shared__ int s_scr[NW + 1];
   __shared__ int4 s_seg[SEGK];
@@ -1379,6 +1394,8 @@ __global__ void __launch_bounds__(NT, HAS_BOX ? 2 : 1024 / NT) k3_tile(K3Args a)
 #endif
 
 __host__ __device__ constexpr int k3s_smem_bytes() { return 2 * TILE * 4; }
+static_assert(TB_MATCHER != 1 || (TILE & (TILE - 1)) == 0,
+              "the search matcher's min tree over a tile needs a power-of-two tile");
 
 __global__ void __launch_bounds__(NT) k3_search(K3Args a) {
   TB_DYNAMIC_SMEM(smem);
