@@ -1140,10 +1140,28 @@ __global__ void __launch_bounds__(JNT, 2) k_up_tile(TreeWs w, Values values, voi
       }
     } else {
       acc = M::combine(acc, seg_fold<M>(node, NCH, tid + 1, NCH - 1));
-      const unsigned at = atomic_add_u32(w.xcount, 1u);
-      w.xlist[at] = R0 + k;
     }
     s_val[jslot(k)] = acc;
+  }
+  // Joints whose subtree leaves the tile go to the list k_up_cross serves:
+  // one atomic per warp for the warp's entries.
+  {
+    unsigned xm = 0;
+    for (int k = c0; k < lim; ++k)
+      if (s_end[k] > JT) xm |= 1u << (k - c0);
+    const int nx = popc(xm);
+    int incl = nx;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int o = shfl_up(incl, d);
+      if (lane_id() >= d) incl += o;
+    }
+    const int wtot = shfl_idx(incl, 31);
+    unsigned wbase = 0;
+    if (lane_id() == 31 && wtot > 0) wbase = atomic_add_u32(w.xcount, (unsigned)wtot);
+    wbase = (unsigned)shfl_idx((int)wbase, 31);
+    unsigned at = wbase + (unsigned)(incl - nx);
+    for (unsigned m = xm; m; m &= m - 1) w.xlist[at++] = R0 + c0 + lowest_set(m);
   }
   // The chunk tree, for subtrees of earlier tiles ending here (their end
   // tile's prefix over whole chunks) and for the tile total.
