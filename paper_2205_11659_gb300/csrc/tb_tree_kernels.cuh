@@ -579,16 +579,23 @@ __global__ void __launch_bounds__(JNT) k_jstruct(TreeWs w, const void* __restric
   }
   // In the tile: parent = the last earlier joint that is shallower, end = the
   // first later joint that is not deeper.  Inside the thread's chunk of JC
-  // joints by direct comparison; else in the nearest chunk that holds one,
-  // found by the up/down search of the tree's level of chunk minima (node
-  // NCH + c covers chunk c), then by a scan of that chunk's JC depths.
-  int par[JC], end[JC], dep[JC], rep[JC];
+  // joints by direct comparison.  The joints a chunk cannot resolve are its
+  // records (no shallower joint before them in the chunk: their parents are
+  // the levels m_c - 1 .. df_c - 1 of the stack at the chunk start) and its
+  // chain (no later joint as shallow in the chunk: levels m_c .. dl_c, one
+  // joint each).  The stack levels a chunk needs are held by a few earlier
+  // chunks, each covering a run of levels with its own chain; one search of
+  // the tree's level of chunk minima (node NCH + c covers chunk c) per run
+  // finds the next owner (the same for the chunks that pop the chain).  What
+  // no chunk of the tile holds becomes one question per stack level.
+  int par[JC], end[JC], dep[JC];
   const int c0 = tid * JC;
 #pragma unroll
   for (int i = 0; i < JC; ++i) {
-    par[i] = end[i] = rep[i] = -1;
+    par[i] = end[i] = -1;
     dep[i] = c0 + i < cnt ? s_tree[JT + c0 + i] : INT_MAX;
   }
+  unsigned recm = 0, chm = 0;  // records, chain
 #pragma unroll
   for (int i = 0; i < JC; ++i) {
 #pragma unroll
@@ -597,53 +604,77 @@ __global__ void __launch_bounds__(JNT) k_jstruct(TreeWs w, const void* __restric
 #pragma unroll
     for (int j = i + 1; j < JC; ++j)
       if (end[i] < 0 && dep[j] <= dep[i]) end[i] = R0 + c0 + j;
+    if (c0 + i < cnt) {
+      if (par[i] < 0) recm |= 1u << i;
+      if (end[i] < 0) chm |= 1u << i;
+    }
   }
+  const int mc = s_tree[NCH + tid];  // chunk minimum (INT_MAX past the last joint)
+  int* s_cpos = s_rep;               // chunk chains: the joint at level mc + j of chunk c
 #pragma unroll
-  for (int i = 0; i < JC; ++i) {
-    if (c0 + i >= cnt) continue;
-    const int d = dep[i];
-    if (par[i] < 0 && d > 1) {
-      const int cc = tree_last_le(s_tree, NCH, tid, d - 1);
-      if (cc >= 0) {
+  for (int i = 0; i < JC; ++i)
+    if ((chm >> i) & 1u) s_cpos[c0 + (dep[i] - mc)] = c0 + i;
+  const int mt = s_tree[1];                    // tile minimum
+  const int dlt = s_tree[JT + cnt - 1];        // depth of the tile's last joint
+  // ends beyond the tile: one question per level of the tile's chain (mt ..
+  // dlt, one joint each), slots 0 .. ne-1; parents before the tile: one slot
+  // per record asking (at most one per joint), after them
+  const int ne = cnt > 0 ? dlt - mt + 1 : 0;
+  if (tid == 0) s_nq = ne;
+  __syncthreads();  // chains written
+  // parents of the records, run by run of stack levels downwards
+  if (recm) {
+    int cur = dep[0] - 1, pos = tid;  // the chunk's first joint is always a record
+    const int need = mc - 1 > 1 ? mc - 1 : 1;
+    while (cur >= need) {
+      const int cc = tree_last_le(s_tree, NCH, pos, cur);
+      if (cc < 0) break;
+      const int mcc = s_tree[NCH + cc];
 #pragma unroll
-        for (int q = JC - 1; q >= 0; --q)
-          if (par[i] < 0 && s_tree[JT + cc * JC + q] <= d - 1) par[i] = R0 + cc * JC + q;
+      for (int i = 0; i < JC; ++i) {
+        const int l = dep[i] - 1;
+        if (((recm >> i) & 1u) && l >= mcc && l <= cur) par[i] = R0 + s_cpos[cc * JC + (l - mcc)];
+      }
+      cur = mcc - 1;
+      pos = cc;
+    }
+#pragma unroll
+    for (int i = 0; i < JC; ++i) {
+      const int l = dep[i] - 1;
+      if (((recm >> i) & 1u) && l >= 1 && l <= cur) {  // the level l entry before the tile
+        const int slot = atomicAdd(&s_nq, 1);
+        s_q[slot] = l;
+        par[i] = -2 - slot;
       }
     }
-    if (end[i] < 0) {
-      const int cc = tree_first_le(s_tree, NCH, tid + 1, d);
-      if (cc >= 0) {
+  }
+  // ends of the chain, run by run of levels downwards (the chunks that pop it)
+  if (chm) {
+    int cur = -1, pos = tid + 1;
+#pragma unroll
+    for (int i = 0; i < JC; ++i)
+      if ((chm >> i) & 1u) cur = dep[i];  // the last chain joint is the deepest
+    while (cur >= mc) {
+      const int cc = tree_first_le(s_tree, NCH, pos, cur);
+      if (cc < 0) break;
+      const int mcc = s_tree[NCH + cc];
+#pragma unroll
+      for (int i = 0; i < JC; ++i) {
+        if (!((chm >> i) & 1u) || dep[i] < mcc || dep[i] > cur) continue;
+        int e = -1;
 #pragma unroll
         for (int q = 0; q < JC; ++q)
-          if (end[i] < 0 && s_tree[JT + cc * JC + q] <= d) end[i] = R0 + cc * JC + q;
+          if (e < 0 && s_tree[JT + cc * JC + q] <= dep[i]) e = cc * JC + q;
+        end[i] = R0 + e;
       }
+      cur = mcc - 1;
+      pos = cc + 1;
     }
-  }
-  // What the tile cannot answer goes to a queue served below.  All joints of
-  // the tile at depth d whose parent lies before the tile share that parent
-  // (the stack entry at depth d-1 at the tile start), so only the first
-  // joint of the tile at or above depth d (its representative) queues the
-  // question; s_rep maps a representative to its queue slot.
 #pragma unroll
-  for (int i = 0; i < JC; ++i) {
-    const int k = tid * JC + i;
-    if (k >= cnt) continue;
-    const int d = dep[i];
-    if (par[i] < 0 && d > 1) {
-      // the first joint of the tile at depth <= d
-      const int cr = tree_first_le(s_tree, NCH, 0, d);
-#pragma unroll
-      for (int q = 0; q < JC; ++q)
-        if (rep[i] < 0 && s_tree[JT + cr * JC + q] <= d) rep[i] = cr * JC + q;
-      if (rep[i] == k) s_rep[k] = atomicAdd(&s_nq, 1);
-      if (rep[i] == k) s_q[s_rep[k]] = k;
-    }
-    if (end[i] < 0) {
-      const int slot = atomicAdd(&s_nq, 1);
-      s_q[slot] = k | (1 << 30);
-      end[i] = -2 - slot;
-    }
+    for (int i = 0; i < JC; ++i)
+      if (((chm >> i) & 1u) && dep[i] <= cur) end[i] = -2 - (dep[i] - mt);  // question of its level
   }
+  for (int qi = tid; qi < ne; qi += JNT) s_q[qi] = (mt + qi) | (1 << 30);
   cp_async_wait_all();
   __syncthreads();
   // One question per thread, all in parallel: find the tile (the neighbour
@@ -653,9 +684,7 @@ __global__ void __launch_bounds__(JNT) k_jstruct(TreeWs w, const void* __restric
   for (int qi = tid; qi < s_nq; qi += JNT) {
     const int qv = s_q[qi];
     const bool is_end = ((qv >> 30) & 1) != 0;
-    const int k = qv & ((1 << 30) - 1);
-    const int d = s_tree[JT + k];
-    const int thr = is_end ? d : d - 1;
+    const int thr = qv & ((1 << 30) - 1);
     int tt;
     if (is_end) {
       if (t + 1 < w.TJ && gt[w.PJ + t + 1] <= thr) tt = t + 1;
@@ -708,7 +737,7 @@ __global__ void __launch_bounds__(JNT) k_jstruct(TreeWs w, const void* __restric
   for (int i = 0; i < JC; ++i) {
     const int k = tid * JC + i;
     if (k >= cnt) continue;
-    if (rep[i] >= 0) par[i] = s_q[s_rep[rep[i]]];
+    if (par[i] < -1) par[i] = s_q[-2 - par[i]];
     if (end[i] < -1) end[i] = s_q[-2 - end[i]];
     w.jparent[R0 + k] = par[i];
     w.jend[R0 + k] = end[i];
