@@ -539,17 +539,11 @@ __device__ __forceinline__ void export_chain(const TreeWs& w, const void* in, in
 
 // Parent and subtree end of every joint of the tile; with CHAIN, also the
 // prefix folds of the tile's exported chain (the input of the DOWN scan).
-// Dynamic shared memory of k_jstruct: a copy of the tiles' min tree when it
-// is small (its searches then stay in shared memory), else none.
-constexpr int kJTreeSmemPJ = 2048;
-__host__ __device__ constexpr size_t jstruct_smem(int PJ) {
-  return (PJ >= 2 && PJ <= kJTreeSmemPJ) ? (size_t)PJ * 2 * sizeof(int) : 0;
-}
-
 template <class M, bool CHAIN>
-__global__ void __launch_bounds__(JNT) k_jstruct(TreeWs w, const void* __restrict__ in) {
+// (seven blocks of 256 threads per SM: a 2^20-joint skeleton's 1024 tiles in
+// one wave)
+__global__ void __launch_bounds__(JNT, 7) k_jstruct(TreeWs w, const void* __restrict__ in) {
   using V = typename M::V;
-  TB_DYNAMIC_SMEM(dsm);
   __shared__ int s_tree[2 * JT];
   __shared__ int s_rep[JT];
   __shared__ int s_q[2 * JT];
@@ -559,14 +553,7 @@ __global__ void __launch_bounds__(JNT) k_jstruct(TreeWs w, const void* __restric
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT, R1 = R0 + JT;
   const int cnt = min(JT, w.J - R0);
-  // the tiles' min tree, copied while the tile's own tree is built
-  const bool gt_smem = jstruct_smem(w.PJ) != 0;
-  int* s_gt = reinterpret_cast<int*>(dsm);
-  if (gt_smem) {
-    for (int f = tid; f < w.PJ / 2; f += JNT) cp_async16(s_gt + 4 * f, w.g_tree + 4 * f);
-    cp_async_commit();
-  }
-  const int* gt = gt_smem ? s_gt : w.g_tree;
+  const int* gt = w.g_tree;  // the tiles' min tree
   for (int k = tid; k < JT; k += JNT) s_tree[JT + k] = k < cnt ? w.jdepth[R0 + k] : INT_MAX;
   if (tid == 0) s_nq = 0;
   __syncthreads();
@@ -675,7 +662,6 @@ __global__ void __launch_bounds__(JNT) k_jstruct(TreeWs w, const void* __restric
       if (((chm >> i) & 1u) && dep[i] <= cur) end[i] = -2 - (dep[i] - mt);  // question of its level
   }
   for (int qi = tid; qi < ne; qi += JNT) s_q[qi] = (mt + qi) | (1 << 30);
-  cp_async_wait_all();
   __syncthreads();
   // One question per thread, all in parallel: find the tile (the neighbour
   // first), then the position in that tile's monotone prefix minima (first

@@ -176,8 +176,7 @@ inline tb_status prelude(const uint8_t* kind, int64_t n, int J, const TreeLayout
 template <class M, bool CHAIN>
 tb_status launch_jstruct(const TreeWs& w, const void* in, cudaStream_t s) {
   TB_PHASE_MARK(s);
-  // (at most 16 KB of dynamic shared memory: within the default limit)
-  k_jstruct<M, CHAIN><<<w.TJ, JNT, jstruct_smem(w.PJ), s>>>(w, in);
+  k_jstruct<M, CHAIN><<<w.TJ, JNT, 0, s>>>(w, in);
   return cudaGetLastError() == cudaSuccess ? TB_OK : TB_ERR_CUDA;
 }
 
