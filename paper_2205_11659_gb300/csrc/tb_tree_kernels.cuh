@@ -255,10 +255,17 @@ struct MonoidOp {
   }
 };
 
-// Shared-memory slot of joint k of a tile: one padding value per chunk keeps
-// the JC-strided accesses of a warp on distinct banks.
-__host__ __device__ __forceinline__ int jslot(int k) { return k + k / JC; }
-constexpr int JSLOTS = JT + JT / JC;
+// Shared-memory slot of joint k of a tile: one padding value per JPAD joints
+// keeps the chunk-strided accesses of a warp on distinct banks.  Values of up
+// to 32 bytes pad once per chunk; the 48-byte affine pads once per two chunks
+// (its three 16-byte words per value then still fall on distinct banks in each
+// quarter warp), which keeps a DOWN tile within a third of the shared memory.
+template <class V>
+__host__ __device__ constexpr int jpad() { return sizeof(V) > 32 ? 2 * JC : JC; }
+template <class V>
+__host__ __device__ __forceinline__ int jslot(int k) { return k + k / jpad<V>(); }
+template <class V>
+__host__ __device__ constexpr int jslots() { return JT + JT / jpad<V>(); }
 
 // The values of joints [R0, R0 + cnt) into their shared slots: asynchronous
 // 16-byte copies when a value is whole 16-byte words (each warp copies one
@@ -272,11 +279,11 @@ __device__ __forceinline__ void stage_tile_values(typename M::V* s_val, const vo
     const float4* src = reinterpret_cast<const float4*>(in) + (int64_t)R0 * WPV;
     for (int f = threadIdx.x; f < cnt * WPV; f += blockDim.x) {
       const int k = f / WPV;
-      cp_async16(reinterpret_cast<float4*>(s_val + jslot(k)) + (f - k * WPV), src + f);
+      cp_async16(reinterpret_cast<float4*>(s_val + jslot<V>(k)) + (f - k * WPV), src + f);
     }
     cp_async_commit();
   } else {
-    for (int k = threadIdx.x; k < cnt; k += blockDim.x) s_val[jslot(k)] = M::load(in, (int64_t)R0 + k);
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) s_val[jslot<V>(k)] = M::load(in, (int64_t)R0 + k);
   }
 }
 
@@ -849,6 +856,22 @@ __global__ void __launch_bounds__(1024) k_down_tiles(TreeWs w, int* status) {
   }
 }
 
+// The JC entries of joint array a for the chunk starting at joint cs (one
+// 16-byte load when the chunk is whole: cs is a multiple of JC and the
+// workspace arrays start on 256-byte boundaries); -1 past joint n.
+__device__ __forceinline__ void load_chunk_ints(const int* __restrict__ a, int cs, int n, int (&v)[JC]) {
+  if (JC == 4 && cs + JC <= n) {
+    const int4 q = *reinterpret_cast<const int4*>(a + cs);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < JC; ++i) v[i] = cs + i < n ? a[cs + i] : -1;
+  }
+}
+
 template <class M>
 __device__ __forceinline__ typename M::V fold_outside(const TreeWs& w, int a) {
   return M::combine(M::load(w.t_world, a / JT), M::load(w.relT, a));
@@ -856,65 +879,102 @@ __device__ __forceinline__ typename M::V fold_outside(const TreeWs& w, int a) {
 
 template <class M>
 constexpr size_t down_tile_smem() {
-  return (size_t)JSLOTS * sizeof(typename M::V) + (size_t)NCH * sizeof(typename M::V) +
-         (size_t)JT * sizeof(int) + (size_t)NCH * sizeof(int);
+  return (size_t)jslots<typename M::V>() * sizeof(typename M::V) + (size_t)NCH * sizeof(typename M::V) +
+         (size_t)NCH * sizeof(int);
 }
 
 template <class M>
-__global__ void __launch_bounds__(JNT, 2) k_down_tile(TreeWs w, const void* __restrict__ in,
+__global__ void __launch_bounds__(JNT, 3) k_down_tile(TreeWs w, const void* __restrict__ in,
                                                      void* __restrict__ out) {
   using V = typename M::V;
   TB_DYNAMIC_SMEM(smem);
   V* s_val = reinterpret_cast<V*>(smem);
-  V* s_cm = s_val + JSLOTS;
-  int* s_anc = reinterpret_cast<int*>(s_cm + NCH);
-  int* s_cl = s_anc + JT;
+  V* s_cm = s_val + jslots<V>();
+  int* s_cl = reinterpret_cast<int*>(s_cm + NCH);
   if (*w.status != ST_OK) return;
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT;
   const int cnt = min(JT, w.J - R0);
   stage_tile_values<M>(s_val, in, R0, cnt);
-#pragma unroll
-  for (int i = 0; i < JT / JNT; ++i) {
-    const int k = tid + i * JNT;
-    if (k < cnt) s_anc[k] = w.jparent[R0 + k];
-  }
+  // While the tile's values arrive: the chunk's parents and subtree ends,
+  // each joint's nearest ancestor outside the chunk (from the parents alone),
+  // and the world values in earlier tiles below which the chunk hangs.
   const int c0 = tid * JC;
-  const int cend = R0 + c0 + JC;  // global end of the chunk
-  unsigned xm = 0;
+  const int cs = R0 + c0, cend = cs + JC;  // global range of the chunk
+  int par[JC], anc[JC];
+  unsigned xm = 0, inm = 0;  // exported joints; parent inside the chunk
+  {
+    int e[JC];
+    load_chunk_ints(w.jparent, cs, w.J, par);
+    load_chunk_ints(w.jend, cs, w.J, e);
+#pragma unroll
+    for (int i = 0; i < JC; ++i) {
+      anc[i] = par[i];
+      if (par[i] >= cs && in_range(par[i], cs, cs + i, w.status)) {  // parent before i in the chunk
+        inm |= 1u << i;
+#pragma unroll
+        for (int j = 0; j < i; ++j)
+          if (par[i] == cs + j) anc[i] = anc[j];
+      }
+      if (c0 + i < cnt && e[i] > cend) xm |= 1u << i;
+    }
+  }
+  // The exported joints of a chunk hang below one base joint, the nearest
+  // outside ancestor of the first of them.  A base in an earlier tile is
+  // final: its world value is that tile's world fold times its relative
+  // fold.  So is the nearest outside ancestor of the chunk's other joints
+  // when it lies in an earlier tile (one such ancestor is loaded here, any
+  // other where it is used).
+  int abase = -1, apre = -1;
+  if (xm) {
+    int a = -1;
+#pragma unroll
+    for (int i = JC - 1; i >= 0; --i)
+      if ((xm >> i) & 1u) a = anc[i];  // the first exported joint's
+    if (in_range(a, -1, cs, w.status)) abase = a;
+    // (debug builds: an ancestor at or after the chunk; left at the identity)
+  }
 #pragma unroll
   for (int i = 0; i < JC; ++i)
-    if (c0 + i < cnt && w.jend[R0 + c0 + i] > cend) xm |= 1u << i;
+    if (apre < 0 && c0 + i < cnt && !(xm & (1u << i)) && anc[i] >= 0 && anc[i] < R0) apre = anc[i];
+  V m = M::identity(), fpre = M::identity();
+  if (abase >= 0 && abase < R0) m = fold_outside<M>(w, abase);
+  if (apre >= 0) fpre = apre == abase ? m : fold_outside<M>(w, apre);
   cp_async_wait_all();
   __syncthreads();
 
-  // In-chunk walk: fold relative to the nearest ancestor outside the chunk.
+  // In-chunk walk: fold relative to the nearest ancestor outside the chunk;
+  // then the joints below a joint of an earlier tile take its world value.
+#pragma unroll
+  for (int i = 0; i < JC; ++i)
+    if ((inm >> i) & 1u)
+      s_val[jslot<V>(c0 + i)] = M::combine(s_val[jslot<V>(par[i] - R0)], s_val[jslot<V>(c0 + i)]);
 #pragma unroll
   for (int i = 0; i < JC; ++i) {
-    const int k = c0 + i;
-    if (k < cnt) {
-      const int p = s_anc[k];
-      if (p >= R0 + c0 && in_range(p, R0 + c0, R0 + k, w.status)) {  // parent before k
-        s_val[jslot(k)] = M::combine(s_val[jslot(p - R0)], s_val[jslot(k)]);
-        s_anc[k] = s_anc[p - R0];
-      }
+    if (c0 + i < cnt && !(xm & (1u << i)) && anc[i] >= 0 && anc[i] < R0) {
+      const V f = anc[i] == apre ? fpre : fold_outside<M>(w, anc[i]);
+      s_val[jslot<V>(c0 + i)] = M::combine(f, s_val[jslot<V>(c0 + i)]);
     }
   }
   __syncthreads();
-
-  // Chunk level: the exported joints of a chunk hang below one base joint,
-  // the nearest outside ancestor of the first of them.
   int link = -1;
-  V m = M::identity();
-  if (xm) {
-    const int a = s_anc[c0 + lowest_set(xm)];
-    if (!in_range(a, -1, R0 + c0, w.status)) {
-      // (debug builds: an ancestor at or after the chunk; left at the identity)
-    } else if (a >= R0) {
-      link = (a - R0) / JC;
-      m = s_val[jslot(a - R0)];
-    } else if (a >= 0) {
-      m = fold_outside<M>(w, a);
+  if (abase >= R0) {
+    link = (abase - R0) / JC;
+    m = s_val[jslot<V>(abase - R0)];
+  }
+  // base of chunk c = base of chunk link(c) times m(c), link(c) < c: pointer
+  // jumping, first over the links inside the warp (shuffles, no barrier;
+  // the chain inside a warp halves every round), then over the block
+  {
+    const int wbase = tid & ~31, lane = tid & 31;
+    for (int round = 0; round < 5 && ballot(link >= wbase) != 0u; ++round) {
+      const int src = link >= wbase ? link - wbase : lane;
+      const V lm = shfl_idx(m, src);
+      const int ll = shfl_idx(link, src);
+      if (link >= wbase) {
+        m = M::combine(lm, m);
+        link = ll;
+      }
     }
   }
   s_cm[tid] = m;
@@ -936,33 +996,23 @@ __global__ void __launch_bounds__(JNT, 2) k_down_tile(TreeWs w, const void* __re
   // Exported joints: base fold times the relative fold.
 #pragma unroll
   for (int i = 0; i < JC; ++i)
-    if (xm & (1u << i)) s_val[jslot(c0 + i)] = M::combine(m, s_val[jslot(c0 + i)]);
+    if (xm & (1u << i)) s_val[jslot<V>(c0 + i)] = M::combine(m, s_val[jslot<V>(c0 + i)]);
   __syncthreads();
-  // Every other joint: its outside ancestor is an exported joint of an
-  // earlier chunk of this tile (final by now), a joint of an earlier tile, or
-  // none.
-  int last_a = -1;
-  V last_f = M::identity();
+  // Every other joint whose outside ancestor is an exported joint of an
+  // earlier chunk of this tile (final by now); those below a joint of an
+  // earlier tile are done, the roots have no ancestor.
 #pragma unroll
   for (int i = 0; i < JC; ++i) {
     const int k = c0 + i;
     if (k < cnt && !(xm & (1u << i))) {
-      const int a = s_anc[k];
-      if (!in_range(a, -1, R0 + c0, w.status)) {
-        // (debug builds: an ancestor at or after the chunk; left as it is)
-      } else if (a >= R0) {
-        s_val[jslot(k)] = M::combine(s_val[jslot(a - R0)], s_val[jslot(k)]);
-      } else if (a >= 0) {
-        if (a != last_a) {
-          last_f = fold_outside<M>(w, a);
-          last_a = a;
-        }
-        s_val[jslot(k)] = M::combine(last_f, s_val[jslot(k)]);
-      }
+      const int a = anc[i];
+      if (a >= R0 && in_range(a, R0, cs, w.status))
+        s_val[jslot<V>(k)] = M::combine(s_val[jslot<V>(a - R0)], s_val[jslot<V>(k)]);
+      // (debug builds: an ancestor at or after the chunk is left as it is)
     }
   }
   __syncthreads();
-  for (int k = tid; k < cnt; k += JNT) M::store(out, R0 + k, s_val[jslot(k)]);
+  for (int k = tid; k < cnt; k += JNT) M::store(out, R0 + k, s_val[jslot<V>(k)]);
 }
 
 // ------------------------------------------------------------- adjoint
@@ -1091,7 +1141,7 @@ struct AdjointValues {
 
 template <class M>
 constexpr size_t up_tile_smem() {
-  return (size_t)JSLOTS * sizeof(typename M::V) + (size_t)2 * NCH * sizeof(typename M::V) +
+  return (size_t)jslots<typename M::V>() * sizeof(typename M::V) + (size_t)2 * NCH * sizeof(typename M::V) +
          (size_t)JT * sizeof(int);
 }
 
@@ -1101,7 +1151,7 @@ __global__ void __launch_bounds__(JNT, 2) k_up_tile(TreeWs w, Values values, voi
   using V = typename M::V;
   TB_DYNAMIC_SMEM(smem);
   V* s_val = reinterpret_cast<V*>(smem);
-  V* s_tree = s_val + JSLOTS;  // chunk totals at [NCH, 2 NCH)
+  V* s_tree = s_val + jslots<V>();  // chunk totals at [NCH, 2 NCH)
   int* s_end = reinterpret_cast<int*>(s_tree + 2 * NCH);  // local subtree ends
   if (*w.status != ST_OK) return;
   const int t = blockIdx.x, tid = threadIdx.x;
@@ -1111,7 +1161,7 @@ __global__ void __launch_bounds__(JNT, 2) k_up_tile(TreeWs w, Values values, voi
   for (int i = 0; i < JT / JNT; ++i) {  // unrolled: every load of the tile in flight at once
     const int k = tid + i * JNT;
     if (k < cnt) {
-      s_val[jslot(k)] = values(R0 + k);
+      s_val[jslot<V>(k)] = values(R0 + k);
       s_end[k] = w.jend[R0 + k] - R0;
     }
   }
@@ -1121,17 +1171,17 @@ __global__ void __launch_bounds__(JNT, 2) k_up_tile(TreeWs w, Values values, voi
   // Walk the chunk backwards: a joint's fold is its own value followed by its
   // children's folds; a child leaving the chunk contributes its suffix.
   for (int k = lim - 1; k >= c0; --k) {
-    V acc = s_val[jslot(k)];
+    V acc = s_val[jslot<V>(k)];
     const int stop = min(s_end[k], ce);
     for (int c = k + 1; c < stop; c = s_end[c]) {
-      acc = M::combine(acc, s_val[jslot(c)]);
+      acc = M::combine(acc, s_val[jslot<V>(c)]);
       if (!in_range(s_end[c], c + 1, (long long)w.J - R0 + 1, w.status)) break;  // ends lie after the joint
     }
-    s_val[jslot(k)] = acc;
+    s_val[jslot<V>(k)] = acc;
   }
   V tot = M::identity();
   for (int c = c0; c < lim; c = s_end[c]) {
-    tot = M::combine(tot, s_val[jslot(c)]);
+    tot = M::combine(tot, s_val[jslot<V>(c)]);
     if (!in_range(s_end[c], c + 1, (long long)w.J - R0 + 1, w.status)) break;
   }
   s_tree[NCH + tid] = tot;
@@ -1145,18 +1195,18 @@ __global__ void __launch_bounds__(JNT, 2) k_up_tile(TreeWs w, Values values, voi
   for (int k = c0; k < lim; ++k) {
     const int e = s_end[k];
     if (e <= ce) continue;
-    V acc = s_val[jslot(k)];
+    V acc = s_val[jslot<V>(k)];
     if (e <= JT) {
       const int c2 = e / JC;
       acc = M::combine(acc, seg_fold<M>(node, NCH, tid + 1, c2 - 1));
       for (int j = c2 * JC; j < e; j = s_end[j]) {
-        acc = M::combine(acc, s_val[jslot(j)]);
+        acc = M::combine(acc, s_val[jslot<V>(j)]);
         if (!in_range(s_end[j], j + 1, (long long)w.J - R0 + 1, w.status)) break;
       }
     } else {
       acc = M::combine(acc, seg_fold<M>(node, NCH, tid + 1, NCH - 1));
     }
-    s_val[jslot(k)] = acc;
+    s_val[jslot<V>(k)] = acc;
   }
   // Joints whose subtree leaves the tile go to the list k_up_cross serves:
   // one atomic per warp for the warp's entries.
@@ -1186,7 +1236,7 @@ __global__ void __launch_bounds__(JNT, 2) k_up_tile(TreeWs w, Values values, voi
   // Store the folds (with a finish, only the partial folds of the subtrees
   // leaving the tile are needed later; the others are finished here).
   for (int k = tid; k < cnt; k += JNT) {
-    const V A = s_val[jslot(k)];
+    const V A = s_val[jslot<V>(k)];
     if (!Finish::active || s_end[k] > JT) M::store(out, R0 + k, A);
     if (Finish::active && s_end[k] <= JT) fin(w, R0 + k, A);
   }
