@@ -1077,8 +1077,15 @@ __device__ __forceinline__ Aff adjoint_grad(const Aff& A, const Aff& Wr, const A
 
 // What the UP kernels do with a completed subtree fold besides storing it:
 // nothing, or turn the adjoint's A_r into grad_local[r].
+// A finish reads its inputs (load, given the joint's parent) apart from
+// using them (apply), so that a caller can have several joints' reads in
+// flight at once.
 struct NoFinish {
   static constexpr bool active = false;
+  struct In {};
+  __device__ In load(int, int) const { return In{}; }
+  template <class V>
+  __device__ void apply(int, const V&, const In&) const {}
   template <class V>
   __device__ void operator()(const TreeWs&, int, const V&) const {}
 };
@@ -1086,13 +1093,21 @@ struct AdjointFinish {
   static constexpr bool active = true;
   const void* world;
   void* grad_local;
-  __device__ void operator()(const TreeWs& w, int r, const Aff& A) const {
-    const Aff Wr = ld_aff(world, r);
-    const int p = w.jparent[r];
-    Aff Wp;
-    if (p >= 0) Wp = ld_aff(world, p);
-    st_aff(grad_local, r, adjoint_grad(A, Wr, p >= 0 ? &Wp : nullptr));
+  struct In {
+    Aff Wr, Wp;
+    bool root;
+  };
+  __device__ In load(int r, int p) const {
+    In x;
+    x.Wr = ld_aff(world, r);
+    x.root = p < 0;
+    if (p >= 0) x.Wp = ld_aff(world, p);
+    return x;
   }
+  __device__ void apply(int r, const Aff& A, const In& x) const {
+    st_aff(grad_local, r, adjoint_grad(A, x.Wr, x.root ? nullptr : &x.Wp));
+  }
+  __device__ void operator()(const TreeWs& w, int r, const Aff& A) const { apply(r, A, load(r, w.jparent[r])); }
 };
 
 // ------------------------------------------------------------- UP
@@ -1157,17 +1172,45 @@ __global__ void __launch_bounds__(JNT, 2) k_up_tile(TreeWs w, Values values, voi
   const int t = blockIdx.x, tid = threadIdx.x;
   const int R0 = t * JT;
   const int cnt = min(JT, w.J - R0);
+  constexpr int NI = JT / JNT;
+  static_assert(NI % 2 == 0, "the finish loop takes joints in pairs");
+  int pr[NI];  // parents of the joints this thread finishes (a finish only)
 #pragma unroll
-  for (int i = 0; i < JT / JNT; ++i) {  // unrolled: every load of the tile in flight at once
+  for (int i = 0; i < NI; ++i) {  // unrolled: every load of the tile in flight at once
     const int k = tid + i * JNT;
+    pr[i] = -1;
     if (k < cnt) {
       s_val[jslot<V>(k)] = values(R0 + k);
       s_end[k] = w.jend[R0 + k] - R0;
+      if (Finish::active) pr[i] = w.jparent[R0 + k];
     }
   }
   __syncthreads();
   const int c0 = tid * JC, ce = c0 + JC;
   const int lim = min(ce, cnt);
+  // Joints whose subtree leaves the tile go to the list k_up_cross serves:
+  // one atomic per warp for the warp's entries (issued first: only the ends
+  // are needed, and the atomic's latency then overlaps the walks below).
+  {
+    unsigned xm = 0;
+    for (int k = c0; k < lim; ++k)
+      if (s_end[k] > JT) xm |= 1u << (k - c0);
+    const int nx = popc(xm);
+    int incl = nx;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int o = shfl_up(incl, d);
+      if (lane_id() >= d) incl += o;
+    }
+    const int wtot = shfl_idx(incl, 31);
+    if (wtot > 0) {
+      unsigned wbase = 0;
+      if (lane_id() == 31) wbase = atomic_add_u32(w.xcount, (unsigned)wtot);
+      wbase = (unsigned)shfl_idx((int)wbase, 31);
+      unsigned at = wbase + (unsigned)(incl - nx);
+      for (unsigned m = xm; m; m &= m - 1) w.xlist[at++] = R0 + c0 + lowest_set(m);
+    }
+  }
   // Walk the chunk backwards: a joint's fold is its own value followed by its
   // children's folds; a child leaving the chunk contributes its suffix.
   for (int k = lim - 1; k >= c0; --k) {
@@ -1190,55 +1233,59 @@ __global__ void __launch_bounds__(JNT, 2) k_up_tile(TreeWs w, Values values, voi
     if (tid < h) s_tree[h + tid] = M::combine(s_tree[2 * (h + tid)], s_tree[2 * (h + tid) + 1]);
     __syncthreads();
   }
-  // Joints whose subtree leaves the chunk.
-  auto node = [s_tree](int i) { return s_tree[i]; };
-  for (int k = c0; k < lim; ++k) {
-    const int e = s_end[k];
-    if (e <= ce) continue;
-    V acc = s_val[jslot<V>(k)];
-    if (e <= JT) {
-      const int c2 = e / JC;
-      acc = M::combine(acc, seg_fold<M>(node, NCH, tid + 1, c2 - 1));
-      for (int j = c2 * JC; j < e; j = s_end[j]) {
-        acc = M::combine(acc, s_val[jslot<V>(j)]);
-        if (!in_range(s_end[j], j + 1, (long long)w.J - R0 + 1, w.status)) break;
-      }
-    } else {
-      acc = M::combine(acc, seg_fold<M>(node, NCH, tid + 1, NCH - 1));
-    }
-    s_val[jslot<V>(k)] = acc;
-  }
-  // Joints whose subtree leaves the tile go to the list k_up_cross serves:
-  // one atomic per warp for the warp's entries.
-  {
-    unsigned xm = 0;
-    for (int k = c0; k < lim; ++k)
-      if (s_end[k] > JT) xm |= 1u << (k - c0);
-    const int nx = popc(xm);
-    int incl = nx;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int o = shfl_up(incl, d);
-      if (lane_id() >= d) incl += o;
-    }
-    const int wtot = shfl_idx(incl, 31);
-    unsigned wbase = 0;
-    if (lane_id() == 31 && wtot > 0) wbase = atomic_add_u32(w.xcount, (unsigned)wtot);
-    wbase = (unsigned)shfl_idx((int)wbase, 31);
-    unsigned at = wbase + (unsigned)(incl - nx);
-    for (unsigned m = xm; m; m &= m - 1) w.xlist[at++] = R0 + c0 + lowest_set(m);
-  }
   // The chunk tree, for subtrees of earlier tiles ending here (their end
-  // tile's prefix over whole chunks) and for the tile total.
+  // tile's prefix over whole chunks) and for the tile total (stored now, so
+  // that the stores drain during the folds below).
   for (int i = tid; i < 2 * NCH; i += JNT)
     if (i > 0) M::store(w.ctree, (int64_t)t * 2 * NCH + i, s_tree[i]);
+  // Joints whose subtree leaves the chunk: its in-chunk fold, the whole
+  // chunks up to the one holding its end (all chunks after this one when the
+  // subtree leaves the tile), then the joints of that chunk before the end.
+  // These joints are nested, so taken innermost (last) first their end
+  // chunks only grow: the fold over whole chunks is extended, not redone.
+  auto node = [s_tree](int i) { return s_tree[i]; };
+  {
+    V R = M::identity();  // fold of chunks tid + 1 .. cr - 1
+    int cr = tid + 1;
+    for (int k = lim - 1; k >= c0; --k) {
+      const int e = s_end[k];
+      if (e <= ce) continue;
+      const int c2 = e <= JT ? e / JC : NCH;
+      if (c2 > cr) {
+        R = M::combine(R, seg_fold<M>(node, NCH, cr, c2 - 1));
+        cr = c2;
+      }
+      V acc = M::combine(s_val[jslot<V>(k)], R);
+      if (e <= JT) {
+        for (int j = c2 * JC; j < e; j = s_end[j]) {
+          acc = M::combine(acc, s_val[jslot<V>(j)]);
+          if (!in_range(s_end[j], j + 1, (long long)w.J - R0 + 1, w.status)) break;
+        }
+      }
+      s_val[jslot<V>(k)] = acc;
+    }
+  }
   __syncthreads();  // every chunk's folds are complete before they are stored
   // Store the folds (with a finish, only the partial folds of the subtrees
-  // leaving the tile are needed later; the others are finished here).
-  for (int k = tid; k < cnt; k += JNT) {
-    const V A = s_val[jslot<V>(k)];
-    if (!Finish::active || s_end[k] > JT) M::store(out, R0 + k, A);
-    if (Finish::active && s_end[k] <= JT) fin(w, R0 + k, A);
+  // leaving the tile are needed later; the others are finished here, two
+  // joints' finish reads in flight at a time).
+#pragma unroll
+  for (int i0 = 0; i0 < NI; i0 += 2) {
+    typename Finish::In x[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int k = tid + (i0 + j) * JNT;
+      if (Finish::active && k < cnt && s_end[k] <= JT) x[j] = fin.load(R0 + k, pr[i0 + j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int k = tid + (i0 + j) * JNT;
+      if (k < cnt) {
+        const V A = s_val[jslot<V>(k)];
+        if (!Finish::active || s_end[k] > JT) M::store(out, R0 + k, A);
+        if (Finish::active && s_end[k] <= JT) fin.apply(R0 + k, A, x[j]);
+      }
+    }
   }
 }
 
