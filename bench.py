@@ -593,7 +593,7 @@ def run_tree(args, torch, world, rank, dev):
         assert int(binding.workspace(dev).status.item()) == binding.TB_OK
 
     K = args.steps
-    nf, nbk = 7, 10
+    nf, nbk = 7, 9
     ev_f = [[torch.cuda.Event(enable_timing=True) for _ in range(nf)] for _ in range(K)]
     ev_b = [[torch.cuda.Event(enable_timing=True) for _ in range(nbk)] for _ in range(K)]
     for evs in ev_f + ev_b:
@@ -627,7 +627,7 @@ def run_tree(args, torch, world, rank, dev):
 
     # per-kernel times of the plain calls (event pairs in launch order)
     fnames = ["depth", "minmax", "min_tree", "jstruct_chain", "down_tiles", "down_tile"]
-    bnames = fnames + ["up_tile", "up_tiles", "up_cross"]
+    bnames = fnames[:5] + ["adjoint_tile", "up_tiles", "up_cross"]
     if graph is not None:
         for i in range(K):
             flush()
@@ -756,7 +756,7 @@ def run_tree(args, torch, world, rank, dev):
                 "d2h_bytes_per_step": int(2 * L.nbytes), "jobs": e2e_steps,
                 "how": "TreePipeline: copies of consecutive jobs overlap the forward + "
                        "structure-reusing backward; fill and drain timed"},
-            "gpu_launches": (6 + 6) * K,
+            "gpu_launches": (6 + 5) * K,
             "clocks": clk,
             "kernel_hash": kernel_hash(TREE_SOURCES),
         }

@@ -93,10 +93,9 @@ tb_status tb_tree_scan_affine_backward(const uint8_t* kind, int64_t n, int64_t n
   unsigned char* b = static_cast<unsigned char*>(ws);
   void* world = b + L.world;
   void* acc = b + L.acc;
-  st = launch_down<MonoidAffine>(w, local, world, d_status, s);
+  st = launch_jstruct<MonoidAffine, true>(w, local, s);
   if (st != TB_OK) return st;
-  st = launch_up<MonoidAffSum>(w, AdjointValues{grad_world, world}, acc,
-                               AdjointFinish{world, grad_local}, s);
+  st = launch_adjoint(w, local, grad_world, world, acc, grad_local, d_status, s);
   if (st != TB_OK) return st;
   TB_PHASE_MARK(s);
   return TB_OK;
@@ -130,10 +129,7 @@ tb_status tb_tree_scan_affine_backward_reuse(const uint8_t* kind, int64_t n, int
   TB_PHASE_MARK(s);
   k_jchain<MonoidAffine><<<w.TJ, JNT, 0, s>>>(w, local, d_status);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
-  st = launch_down_tiles<MonoidAffine>(w, local, world, d_status, s);
-  if (st != TB_OK) return st;
-  st = launch_up<MonoidAffSum>(w, AdjointValues{grad_world, world}, acc,
-                               AdjointFinish{world, grad_local}, s);
+  st = launch_adjoint(w, local, grad_world, world, acc, grad_local, d_status, s);
   if (st != TB_OK) return st;
   TB_PHASE_MARK(s);
   return TB_OK;

@@ -255,17 +255,24 @@ struct MonoidOp {
   }
 };
 
-// Shared-memory slot of joint k of a tile: one padding value per JPAD joints
-// keeps the chunk-strided accesses of a warp on distinct banks.  Values of up
-// to 32 bytes pad once per chunk; the 48-byte affine pads once per two chunks
-// (its three 16-byte words per value then still fall on distinct banks in each
-// quarter warp), which keeps a DOWN tile within a third of the shared memory.
+// Shared-memory slot of joint k of a tile, chosen so that the chunk-strided
+// accesses of a warp (joints c0 + i of the threads' chunks) and the
+// consecutive ones (joints tid + i JNT) fall on distinct banks.  Values of up
+// to 32 bytes take one padding slot per chunk.  The 48-byte affine (three
+// 16-byte words) takes no padding: within each aligned group of eight joints
+// the slots are rotated by the group's index, so that the eight threads of a
+// quarter warp, eight chunks apart in the group index, hit eight distinct
+// 16-byte bank groups; the tile then fits three DOWN blocks, or three
+// adjoint blocks, per SM.
 template <class V>
-__host__ __device__ constexpr int jpad() { return sizeof(V) > 32 ? 2 * JC : JC; }
+__host__ __device__ __forceinline__ int jslot(int k) {
+  if constexpr (sizeof(V) > 32) return (k & ~7) | ((k + (k >> 3)) & 7);
+  else return k + k / JC;
+}
 template <class V>
-__host__ __device__ __forceinline__ int jslot(int k) { return k + k / jpad<V>(); }
-template <class V>
-__host__ __device__ constexpr int jslots() { return JT + JT / jpad<V>(); }
+__host__ __device__ constexpr int jslots() { return sizeof(V) > 32 ? JT : JT + JT / JC; }
+static_assert(JT % 8 == 0, "the affine slots rotate within groups of eight joints");
+static_assert(JT + 1 <= 32767, "tile-local subtree ends are 16-bit");
 
 // The values of joints [R0, R0 + cnt) into their shared slots: asynchronous
 // 16-byte copies when a value is whole 16-byte words (each warp copies one
@@ -883,28 +890,25 @@ constexpr size_t down_tile_smem() {
          (size_t)NCH * sizeof(int);
 }
 
+// The DOWN fold of joint tile R0 / JT (cnt joints): the world value of every
+// joint in its shared slot when it returns (after a barrier).  s_cm and s_cl
+// hold NCH values and NCH ints of scratch; par and e return the parents and
+// subtree ends of the thread's chunk.
 template <class M>
-__global__ void __launch_bounds__(JNT, 3) k_down_tile(TreeWs w, const void* __restrict__ in,
-                                                     void* __restrict__ out) {
+__device__ __forceinline__ void down_tile_fold(const TreeWs& w, const void* __restrict__ in,
+                                               typename M::V* s_val, typename M::V* s_cm, int* s_cl,
+                                               int R0, int cnt, int (&par)[JC], int (&e)[JC]) {
   using V = typename M::V;
-  TB_DYNAMIC_SMEM(smem);
-  V* s_val = reinterpret_cast<V*>(smem);
-  V* s_cm = s_val + jslots<V>();
-  int* s_cl = reinterpret_cast<int*>(s_cm + NCH);
-  if (*w.status != ST_OK) return;
-  const int t = blockIdx.x, tid = threadIdx.x;
-  const int R0 = t * JT;
-  const int cnt = min(JT, w.J - R0);
+  const int tid = threadIdx.x;
   stage_tile_values<M>(s_val, in, R0, cnt);
   // While the tile's values arrive: the chunk's parents and subtree ends,
   // each joint's nearest ancestor outside the chunk (from the parents alone),
   // and the world values in earlier tiles below which the chunk hangs.
   const int c0 = tid * JC;
   const int cs = R0 + c0, cend = cs + JC;  // global range of the chunk
-  int par[JC], anc[JC];
+  int anc[JC];
   unsigned xm = 0, inm = 0;  // exported joints; parent inside the chunk
   {
-    int e[JC];
     load_chunk_ints(w.jparent, cs, w.J, par);
     load_chunk_ints(w.jend, cs, w.J, e);
 #pragma unroll
@@ -1012,7 +1016,22 @@ __global__ void __launch_bounds__(JNT, 3) k_down_tile(TreeWs w, const void* __re
     }
   }
   __syncthreads();
-  for (int k = tid; k < cnt; k += JNT) M::store(out, R0 + k, s_val[jslot<V>(k)]);
+}
+
+template <class M>
+__global__ void __launch_bounds__(JNT, 3) k_down_tile(TreeWs w, const void* __restrict__ in,
+                                                     void* __restrict__ out) {
+  using V = typename M::V;
+  TB_DYNAMIC_SMEM(smem);
+  V* s_val = reinterpret_cast<V*>(smem);
+  V* s_cm = s_val + jslots<V>();
+  int* s_cl = reinterpret_cast<int*>(s_cm + NCH);
+  if (*w.status != ST_OK) return;
+  const int R0 = blockIdx.x * JT;
+  const int cnt = min(JT, w.J - R0);
+  int par[JC], e[JC];
+  down_tile_fold<M>(w, in, s_val, s_cm, s_cl, R0, cnt, par, e);
+  for (int k = threadIdx.x; k < cnt; k += JNT) M::store(out, R0 + k, s_val[jslot<V>(k)]);
 }
 
 // ------------------------------------------------------------- adjoint
@@ -1083,7 +1102,7 @@ __device__ __forceinline__ Aff adjoint_grad(const Aff& A, const Aff& Wr, const A
 struct NoFinish {
   static constexpr bool active = false;
   struct In {};
-  __device__ In load(int, int) const { return In{}; }
+  __device__ In load(const TreeWs&, int, int, int) const { return In{}; }
   template <class V>
   __device__ void apply(int, const V&, const In&) const {}
   template <class V>
@@ -1097,17 +1116,22 @@ struct AdjointFinish {
     Aff Wr, Wp;
     bool root;
   };
-  __device__ In load(int r, int p) const {
+  // (a parent before own_lo takes its world value from the tile pass's
+  // folds instead: its tile's world fold times its relative fold)
+  __device__ In load(const TreeWs& w, int r, int p, int own_lo) const {
     In x;
     x.Wr = ld_aff(world, r);
     x.root = p < 0;
-    if (p >= 0) x.Wp = ld_aff(world, p);
+    if (p >= own_lo) x.Wp = ld_aff(world, p);
+    else if (p >= 0) x.Wp = fold_outside<MonoidAffine>(w, p);
     return x;
   }
   __device__ void apply(int r, const Aff& A, const In& x) const {
     st_aff(grad_local, r, adjoint_grad(A, x.Wr, x.root ? nullptr : &x.Wp));
   }
-  __device__ void operator()(const TreeWs& w, int r, const Aff& A) const { apply(r, A, load(r, w.jparent[r])); }
+  __device__ void operator()(const TreeWs& w, int r, const Aff& A) const {
+    apply(r, A, load(w, r, w.jparent[r], 0));
+  }
 };
 
 // ------------------------------------------------------------- UP
@@ -1143,49 +1167,32 @@ struct AdjointValues {
     x.w = g.w;
     return x;
   }
-  __device__ Aff operator()(int r) const {
-    const Aff G = ld_aff(grad_world, r);
-    const Aff W = ld_aff(world, r);
+  __device__ static Aff apply(const Aff& G, const Aff& W) {
     Aff X;
     X.r0 = row(G.r0, W);
     X.r1 = row(G.r1, W);
     X.r2 = row(G.r2, W);
     return X;
   }
+  __device__ Aff operator()(int r) const { return apply(ld_aff(grad_world, r), ld_aff(world, r)); }
 };
 
 template <class M>
 constexpr size_t up_tile_smem() {
   return (size_t)jslots<typename M::V>() * sizeof(typename M::V) + (size_t)2 * NCH * sizeof(typename M::V) +
-         (size_t)JT * sizeof(int);
+         (size_t)JT * sizeof(short);
 }
 
-template <class M, class Values, class Finish>
-__global__ void __launch_bounds__(JNT, 2) k_up_tile(TreeWs w, Values values, void* __restrict__ out,
-                                                   Finish fin) {
+// The UP fold of joint tile R0 / JT (cnt joints) from its values in s_val
+// and its tile-local subtree ends in s_end (both complete, after a barrier):
+// every joint's fold over its subtree within the tile in its slot when it
+// returns (after a barrier); the chunk tree (2 NCH values of scratch in
+// s_tree) goes to the workspace, the joints leaving the tile to its list.
+template <class M>
+__device__ __forceinline__ void up_tile_fold(const TreeWs& w, typename M::V* s_val, typename M::V* s_tree,
+                                             const short* s_end, int R0, int cnt) {
   using V = typename M::V;
-  TB_DYNAMIC_SMEM(smem);
-  V* s_val = reinterpret_cast<V*>(smem);
-  V* s_tree = s_val + jslots<V>();  // chunk totals at [NCH, 2 NCH)
-  int* s_end = reinterpret_cast<int*>(s_tree + 2 * NCH);  // local subtree ends
-  if (*w.status != ST_OK) return;
-  const int t = blockIdx.x, tid = threadIdx.x;
-  const int R0 = t * JT;
-  const int cnt = min(JT, w.J - R0);
-  constexpr int NI = JT / JNT;
-  static_assert(NI % 2 == 0, "the finish loop takes joints in pairs");
-  int pr[NI];  // parents of the joints this thread finishes (a finish only)
-#pragma unroll
-  for (int i = 0; i < NI; ++i) {  // unrolled: every load of the tile in flight at once
-    const int k = tid + i * JNT;
-    pr[i] = -1;
-    if (k < cnt) {
-      s_val[jslot<V>(k)] = values(R0 + k);
-      s_end[k] = w.jend[R0 + k] - R0;
-      if (Finish::active) pr[i] = w.jparent[R0 + k];
-    }
-  }
-  __syncthreads();
+  const int t = R0 / JT, tid = threadIdx.x;
   const int c0 = tid * JC, ce = c0 + JC;
   const int lim = min(ce, cnt);
   // Joints whose subtree leaves the tile go to the list k_up_cross serves:
@@ -1266,16 +1273,28 @@ __global__ void __launch_bounds__(JNT, 2) k_up_tile(TreeWs w, Values values, voi
     }
   }
   __syncthreads();  // every chunk's folds are complete before they are stored
-  // Store the folds (with a finish, only the partial folds of the subtrees
-  // leaving the tile are needed later; the others are finished here, two
-  // joints' finish reads in flight at a time).
+}
+
+// Stores the folds of the tile's joints (with a finish, only the partial
+// folds of the subtrees leaving the tile are needed later; the others are
+// finished here, two joints' finish reads in flight at a time).  pr holds
+// the parents of the joints tid + i JNT; the finish reads the world values
+// of joints from own_lo on from the workspace (see the finish).
+template <class M, class Finish>
+__device__ __forceinline__ void up_tile_store(const TreeWs& w, void* __restrict__ out, const Finish& fin,
+                                              const typename M::V* s_val, const short* s_end,
+                                              const int (&pr)[JT / JNT], int R0, int cnt, int own_lo) {
+  using V = typename M::V;
+  const int tid = threadIdx.x;
+  constexpr int NI = JT / JNT;
+  static_assert(NI % 2 == 0, "the finish loop takes joints in pairs");
 #pragma unroll
   for (int i0 = 0; i0 < NI; i0 += 2) {
     typename Finish::In x[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int k = tid + (i0 + j) * JNT;
-      if (Finish::active && k < cnt && s_end[k] <= JT) x[j] = fin.load(R0 + k, pr[i0 + j]);
+      if (Finish::active && k < cnt && s_end[k] <= JT) x[j] = fin.load(w, R0 + k, pr[i0 + j], own_lo);
     }
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -1287,6 +1306,87 @@ __global__ void __launch_bounds__(JNT, 2) k_up_tile(TreeWs w, Values values, voi
       }
     }
   }
+}
+
+template <class M, class Values, class Finish>
+__global__ void __launch_bounds__(JNT, 2) k_up_tile(TreeWs w, Values values, void* __restrict__ out,
+                                                   Finish fin) {
+  using V = typename M::V;
+  TB_DYNAMIC_SMEM(smem);
+  V* s_val = reinterpret_cast<V*>(smem);
+  V* s_tree = s_val + jslots<V>();  // chunk totals at [NCH, 2 NCH)
+  short* s_end = reinterpret_cast<short*>(s_tree + 2 * NCH);  // local subtree ends (JT + 1: past the tile)
+  if (*w.status != ST_OK) return;
+  const int t = blockIdx.x, tid = threadIdx.x;
+  const int R0 = t * JT;
+  const int cnt = min(JT, w.J - R0);
+  constexpr int NI = JT / JNT;
+  int pr[NI];  // parents of the joints this thread finishes (a finish only)
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {  // unrolled: every load of the tile in flight at once
+    const int k = tid + i * JNT;
+    pr[i] = -1;
+    if (k < cnt) {
+      s_val[jslot<V>(k)] = values(R0 + k);
+      s_end[k] = (short)min(w.jend[R0 + k] - R0, JT + 1);
+      if (Finish::active) pr[i] = w.jparent[R0 + k];
+    }
+  }
+  __syncthreads();
+  up_tile_fold<M>(w, s_val, s_tree, s_end, R0, cnt);
+  up_tile_store<M>(w, out, fin, s_val, s_end, pr, R0, cnt, 0);
+}
+
+// The adjoint of the affine DOWN scan for one joint tile in one pass: the
+// tile's world values (the DOWN fold; stored to the workspace for the
+// cross-tile completion and the finish), then in place the adjoint values
+// (AdjointValues), their UP fold and the finish.  A parent in an earlier
+// tile takes its world value from the tile pass's folds, since that tile's
+// block may still be running.  Shared memory: the tile's values, its local
+// subtree ends, and the DOWN's chunk bases and links, later the UP's chunk
+// tree.
+constexpr size_t adjoint_tile_smem() {
+  return (size_t)jslots<Aff>() * sizeof(Aff) + (size_t)JT * sizeof(short) + (size_t)2 * NCH * sizeof(Aff);
+}
+static_assert((size_t)NCH * sizeof(Aff) + (size_t)NCH * sizeof(int) <= (size_t)2 * NCH * sizeof(Aff),
+              "the DOWN's scratch fits where the chunk tree goes");
+
+__global__ void __launch_bounds__(JNT, 3) k_adjoint_tile(TreeWs w, const void* __restrict__ local,
+                                                        const void* __restrict__ grad_world, void* world,
+                                                        void* __restrict__ acc, AdjointFinish fin) {
+  using V = Aff;
+  TB_DYNAMIC_SMEM(smem);
+  V* s_val = reinterpret_cast<V*>(smem);
+  short* s_end = reinterpret_cast<short*>(s_val + jslots<V>());  // local subtree ends (JT + 1: past the tile)
+  V* s_scr = reinterpret_cast<V*>(s_end + JT);
+  if (*w.status != ST_OK) return;
+  const int tid = threadIdx.x;
+  const int R0 = blockIdx.x * JT;
+  const int cnt = min(JT, w.J - R0);
+  if (tid == 0 && cnt > 0)  // read after the DOWN fold
+    prefetch_l2_bulk(static_cast<const V*>(grad_world) + R0, (unsigned)(cnt * sizeof(V)));
+  int par[JC], e[JC];
+  down_tile_fold<MonoidAffine>(w, local, s_val, s_scr, reinterpret_cast<int*>(s_scr + NCH), R0, cnt, par, e);
+  const int c0 = tid * JC;
+#pragma unroll
+  for (int i = 0; i < JC; ++i)
+    if (c0 + i < cnt) s_end[c0 + i] = (short)min(e[i] - R0, JT + 1);
+  constexpr int NI = JT / JNT;
+  int pr[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int k = tid + i * JNT;
+    pr[i] = -1;
+    if (k < cnt) {
+      const V W = s_val[jslot<V>(k)];
+      st_aff(world, R0 + k, W);
+      s_val[jslot<V>(k)] = AdjointValues::apply(ld_aff(grad_world, R0 + k), W);
+      pr[i] = w.jparent[R0 + k];
+    }
+  }
+  __syncthreads();
+  up_tile_fold<MonoidAffSum>(w, s_val, s_scr, s_end, R0, cnt);
+  up_tile_store<MonoidAffSum>(w, acc, fin, s_val, s_end, pr, R0, cnt, R0);
 }
 
 // Segment tree over the tiles' totals (one block).

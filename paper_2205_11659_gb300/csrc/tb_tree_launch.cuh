@@ -182,8 +182,7 @@ tb_status launch_jstruct(const TreeWs& w, const void* in, cudaStream_t s) {
 
 // The DOWN scan after its chain input (k_jstruct<M, true> or k_jchain).
 template <class M>
-tb_status launch_down_tiles(const TreeWs& w, const void* in, void* out, int32_t* d_status,
-                            cudaStream_t s) {
+tb_status launch_tile_links(const TreeWs& w, int32_t* d_status, cudaStream_t s) {
   TB_PHASE_MARK(s);
   const size_t tsm = down_tiles_smem<M>(w.TJ);
   if (tsm <= kMaxBlockSmem) {
@@ -194,7 +193,14 @@ tb_status launch_down_tiles(const TreeWs& w, const void* in, void* out, int32_t*
   } else {
     k_down_tiles<M, false><<<1, 1024, 0, s>>>(w, d_status);
   }
-  if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? TB_OK : TB_ERR_CUDA;
+}
+
+template <class M>
+tb_status launch_down_tiles(const TreeWs& w, const void* in, void* out, int32_t* d_status,
+                            cudaStream_t s) {
+  const tb_status st = launch_tile_links<M>(w, d_status, s);
+  if (st != TB_OK) return st;
   TB_PHASE_MARK(s);
   constexpr size_t smem = down_tile_smem<M>();
   static std::atomic<unsigned long long> attr_set{0};
@@ -226,6 +232,30 @@ tb_status launch_up(const TreeWs& w, Values values, void* out, Finish fin, cudaS
   k_up_cross<M, Values, Finish><<<grid_for(w.TJ * 64, 256), 256, 0, s>>>(w, values, out, fin);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   return TB_OK;
+}
+
+// The affine adjoint once the joint structure and the tiles' exported
+// chains are in the workspace: the tile pass's world folds, one pass per
+// tile (world values, adjoint values, their UP fold and the finish), then
+// the UP's cross-tile completion.
+inline tb_status launch_adjoint(const TreeWs& w, const void* local, const void* grad_world, void* world,
+                                void* acc, float* grad_local, int32_t* d_status, cudaStream_t s) {
+  tb_status st = launch_tile_links<MonoidAffine>(w, d_status, s);
+  if (st != TB_OK) return st;
+  TB_PHASE_MARK(s);
+  constexpr size_t smem = adjoint_tile_smem();
+  static std::atomic<unsigned long long> attr_set{0};
+  if (smem_limit_once(attr_set, k_adjoint_tile, smem) != cudaSuccess) return TB_ERR_CUDA;
+  const AdjointFinish fin{world, grad_local};
+  k_adjoint_tile<<<w.TJ, JNT, smem, s>>>(w, local, grad_world, world, acc, fin);
+  if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
+  TB_PHASE_MARK(s);
+  k_up_tiles<MonoidAffSum><<<1, 1024, 0, s>>>(w);
+  if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
+  TB_PHASE_MARK(s);
+  k_up_cross<MonoidAffSum, AdjointValues, AdjointFinish><<<grid_for(w.TJ * 64, 256), 256, 0, s>>>(
+      w, AdjointValues{grad_world, world}, acc, fin);
+  return cudaGetLastError() == cudaSuccess ? TB_OK : TB_ERR_CUDA;
 }
 
 template <class M>
