@@ -1363,8 +1363,6 @@ __global__ void __launch_bounds__(JNT, 3) k_adjoint_tile(TreeWs w, const void* _
   const int tid = threadIdx.x;
   const int R0 = blockIdx.x * JT;
   const int cnt = min(JT, w.J - R0);
-  if (tid == 0 && cnt > 0)  // read after the DOWN fold
-    prefetch_l2_bulk(static_cast<const V*>(grad_world) + R0, (unsigned)(cnt * sizeof(V)));
   int par[JC], e[JC];
   down_tile_fold<MonoidAffine>(w, local, s_val, s_scr, reinterpret_cast<int*>(s_scr + NCH), R0, cnt, par, e);
   const int c0 = tid * JC;
@@ -1412,11 +1410,47 @@ __global__ void __launch_bounds__(1024) k_up_tiles(TreeWs w) {
   }
 }
 
+// Fold of leaves l..r (inclusive) of a segment tree with P leaves, its node
+// reads eight at a time: the nodes of the range are, in fold order, the left
+// nodes of levels 0, 1, ... (level k: ceil((l + P) / 2^k) when odd) and then
+// the right nodes from the top level down (level k: floor((r + P + 1) / 2^k)
+// - 1 when that quotient is odd), over the levels where the range is still
+// open; each batch's reads are independent, so their latencies overlap.
+template <class M, class Node>
+__device__ __forceinline__ typename M::V seg_fold_batched(Node node, int P, int l, int r) {
+  using V = typename M::V;
+  V acc = M::identity();
+  if (l > r) return acc;
+  const int L0 = l + P, R1 = r + P + 1;
+  int nlev = 0;  // levels 0 .. nlev - 1 are open
+  while (nlev < 31 && ((L0 + (1 << nlev) - 1) >> nlev) < (R1 >> nlev)) ++nlev;
+  const int slots = 2 * nlev;
+  for (int s0 = 0; s0 < slots; s0 += 8) {
+    V v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int sl = s0 + j;
+      const int k = sl < nlev ? sl : slots - 1 - sl;
+      const int lk = (L0 + (1 << k) - 1) >> k, rk = R1 >> k;
+      int nd = 0;
+      if (sl < nlev) nd = (lk & 1) ? lk : 0;
+      else if (sl < slots) nd = (rk & 1) ? rk - 1 : 0;
+      v[j] = nd > 0 ? node(nd) : M::identity();
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc = M::combine(acc, v[j]);
+  }
+  return acc;
+}
+
 // Completes the folds of the subtrees that leave their tile: the partial fold
 // written by k_up_tile, the whole tiles in between, and the prefix of the
-// tile where the subtree ends.
+// tile where the subtree ends (its whole chunks, then the joints of the chunk
+// holding the end).  One thread per subtree; the reads that do not depend on
+// one another are issued together.
 template <class M, class Values, class Finish>
-__global__ void k_up_cross(TreeWs w, Values values, void* __restrict__ out, Finish fin) {
+__global__ void __launch_bounds__(128) k_up_cross(TreeWs w, Values values, void* __restrict__ out,
+                                                  Finish fin) {
   using V = typename M::V;
   if (*w.status != ST_OK) return;
   const int count = (int)*w.xcount;
@@ -1425,24 +1459,33 @@ __global__ void k_up_cross(TreeWs w, Values values, void* __restrict__ out, Fini
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     const int r = w.xlist[i];
     if (!in_range(r, 0, w.J, w.status)) continue;
-    const int t = r / JT;
     const int e = w.jend[r];
+    const int p = Finish::active ? w.jparent[r] : -1;
     if (!in_range(e, r + 1, (long long)w.J + 1, w.status)) continue;
+    const typename Finish::In x = fin.load(w, r, p, 0);
+    const int t = r / JT;
     const int t2 = e / JT;
     V acc = M::load(out, r);
-    acc = M::combine(acc, seg_fold<M>(node, w.PJ, t + 1, t2 - 1));
+    acc = M::combine(acc, seg_fold_batched<M>(node, w.PJ, t + 1, t2 - 1));
     const int R2 = t2 * JT;
     if (e > R2) {
       const int c2 = (e - R2) / JC;
       const void* ct = static_cast<const unsigned char*>(w.ctree) +
                        (size_t)t2 * 2 * NCH * sizeof(V);
       auto cnode = [ct](int j) { return M::load(ct, j); };
-      acc = M::combine(acc, seg_fold<M>(cnode, NCH, 0, c2 - 1));
+      acc = M::combine(acc, seg_fold_batched<M>(cnode, NCH, 0, c2 - 1));
       // the joints of the end tile's chunk c2 before e (fewer than JC), from
       // their values: the fold over a range is the fold of its elements
-      for (int j = R2 + c2 * JC; j < e; ++j) acc = M::combine(acc, values(j));
+      V vj[JC - 1];
+#pragma unroll
+      for (int q = 0; q < JC - 1; ++q) {
+        const int j = R2 + c2 * JC + q;
+        vj[q] = j < e ? values(j) : M::identity();
+      }
+#pragma unroll
+      for (int q = 0; q < JC - 1; ++q) acc = M::combine(acc, vj[q]);
     }
-    if (Finish::active) fin(w, r, acc);
+    if (Finish::active) fin.apply(r, acc, x);
     else M::store(out, r, acc);
   }
 }

@@ -217,6 +217,12 @@ tb_status launch_down(const TreeWs& w, const void* in, void* out, int32_t* d_sta
   return launch_down_tiles<M>(w, in, out, d_status, s);
 }
 
+template <class M>
+tb_status launch_up_tiles(const TreeWs& w, cudaStream_t s) {
+  k_up_tiles<M><<<1, 1024, 0, s>>>(w);
+  return cudaGetLastError() == cudaSuccess ? TB_OK : TB_ERR_CUDA;
+}
+
 template <class M, class Values, class Finish>
 tb_status launch_up(const TreeWs& w, Values values, void* out, Finish fin, cudaStream_t s) {
   TB_PHASE_MARK(s);
@@ -226,10 +232,10 @@ tb_status launch_up(const TreeWs& w, Values values, void* out, Finish fin, cudaS
   k_up_tile<M, Values, Finish><<<w.TJ, JNT, smem, s>>>(w, values, out, fin);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   TB_PHASE_MARK(s);
-  k_up_tiles<M><<<1, 1024, 0, s>>>(w);
-  if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
+  const tb_status st = launch_up_tiles<M>(w, s);
+  if (st != TB_OK) return st;
   TB_PHASE_MARK(s);
-  k_up_cross<M, Values, Finish><<<grid_for(w.TJ * 64, 256), 256, 0, s>>>(w, values, out, fin);
+  k_up_cross<M, Values, Finish><<<grid_for(w.TJ * 64, 128), 128, 0, s>>>(w, values, out, fin);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   return TB_OK;
 }
@@ -250,10 +256,10 @@ inline tb_status launch_adjoint(const TreeWs& w, const void* local, const void* 
   k_adjoint_tile<<<w.TJ, JNT, smem, s>>>(w, local, grad_world, world, acc, fin);
   if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
   TB_PHASE_MARK(s);
-  k_up_tiles<MonoidAffSum><<<1, 1024, 0, s>>>(w);
-  if (cudaGetLastError() != cudaSuccess) return TB_ERR_CUDA;
+  st = launch_up_tiles<MonoidAffSum>(w, s);
+  if (st != TB_OK) return st;
   TB_PHASE_MARK(s);
-  k_up_cross<MonoidAffSum, AdjointValues, AdjointFinish><<<grid_for(w.TJ * 64, 256), 256, 0, s>>>(
+  k_up_cross<MonoidAffSum, AdjointValues, AdjointFinish><<<grid_for(w.TJ * 64, 128), 128, 0, s>>>(
       w, AdjointValues{grad_world, world}, acc, fin);
   return cudaGetLastError() == cudaSuccess ? TB_OK : TB_ERR_CUDA;
 }
