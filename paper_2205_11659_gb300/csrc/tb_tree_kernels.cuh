@@ -50,6 +50,9 @@
 // Affine adjoint (loss = sum_r <W_r, world_r>): world by DOWN, then
 // A_r = sum over the subtree of W_d (x) world_d^T by UP, and in the same
 // kernels Gbar_r = A_r world_r^{-T} and dL_r = R_parent^T Gbar_r.
+//   * k_adjoint_tile: per tile, the DOWN fold of k_down_tile, the adjoint
+//     values in place of the world values, the UP fold of k_up_tile and the
+//     finish, in one block; then k_up_tiles and k_up_cross as for UP.
 #ifndef TB_TREE_KERNELS_CUH
 #define TB_TREE_KERNELS_CUH
 
