@@ -70,10 +70,10 @@ __host__ __device__ __forceinline__ int box_slot(int p) { return p + p / KPT; }
 // second with the backoff of poll_backoff) and reports ST_TIMEOUT.
 constexpr unsigned SPIN_LIMIT = 1u << 20;
 
-__host__ __device__ __forceinline__ int kind_delta(int k) {
+__host__ __device__ __forceinline__ constexpr int kind_delta(int k) {
   return k == K_CLOSE ? -1 : ((k == K_CLIP || k == K_BLEND) ? 1 : 0);
 }
-__host__ __device__ __forceinline__ bool kind_open(int k) { return k == K_CLIP || k == K_BLEND; }
+__host__ __device__ __forceinline__ constexpr bool kind_open(int k) { return k == K_CLIP || k == K_BLEND; }
 
 // ------------------------------------------------------------- box algebra
 // Intersection (clip, Sec. 6.1) and union (blend, Sec. 6.2) of (x0,y0,x1,y1)

@@ -149,8 +149,8 @@ __device__ __forceinline__ bool load_kind_words(const uint8_t* __restrict__ kind
 //               (unmatched inside the group: its final stack, P rising by one)
 //   bits 16-19  P_e + 4 of the first of those
 //   bits 20-23  clips
-__host__ __device__ __forceinline__ unsigned k1_group_entry(unsigned code) {
-  int P[4];
+__host__ __device__ __forceinline__ constexpr unsigned k1_group_entry(unsigned code) {
+  int P[4] = {0, 0, 0, 0};
   int p = 0, m0 = 0, ma = 4;
   unsigned clip = 0, opn = 0;
   for (int e = 0; e < 4; ++e) {
@@ -175,6 +175,18 @@ __host__ __device__ __forceinline__ unsigned k1_group_entry(unsigned code) {
          (unsigned)(l0 + 4) << 16 | clip << 20;
 }
 
+// The 256 group summaries, computed by the compiler; the tile-summary pass
+// reads them through the read-only path (one kilobyte, which stays in L1).
+struct K1GroupTable {
+  unsigned e[256];
+};
+__host__ __device__ constexpr K1GroupTable k1_group_table() {
+  K1GroupTable g{};
+  for (unsigned c = 0; c < 256; ++c) g.e[c] = k1_group_entry(c);
+  return g;
+}
+static __device__ const K1GroupTable k1_gtab = k1_group_table();
+
 // The 2-bit codes of a word's 4 kind bytes (each 0..3).
 __device__ __forceinline__ unsigned kind_code4(unsigned w) {
   return (w & 0x3u) | ((w >> 6) & 0xcu) | ((w >> 12) & 0x30u) | ((w >> 18) & 0xc0u);
@@ -195,23 +207,19 @@ __global__ void __launch_bounds__(NT, 4) k1_tile_summary(K1Args a) {
   __shared__ int2 s_scr2[NW + 1];
   __shared__ float4 s_fscr[NW + 1];
   __shared__ int s_boff;
-  __shared__ unsigned s_gtab[256];
   const int tid = threadIdx.x;
   const int t = blockIdx.x;
   const int base = t * TILE, p0 = tid * KPT;
 
-  // the group summaries of every 4 kinds (k1_group_entry), one table
-  for (int c = tid; c < 256; c += NT) s_gtab[c] = k1_group_entry((unsigned)c);
   unsigned wd[KPT / 4];
   if (load_kind_words(a.kind, a.n, base + p0, wd)) atomic_cas_i32(a.status, ST_OK, ST_BAD_KIND);
-  __syncthreads();
 
   // Chunk depth profile relative to the chunk start, 4 kinds at a time.
   unsigned ge[KPT / 4];
   int r = 0, mn = 0, mn_after = INT_MAX;
 #pragma unroll
   for (int j = 0; j < KPT / 4; ++j) {
-    ge[j] = s_gtab[kind_code4(wd[j])];
+    ge[j] = __ldg(&k1_gtab.e[kind_code4(wd[j])]);  // the group summary (k1_group_entry)
     const int m0 = r + (int)((ge[j] >> 4) & 15u) - 4, ma = r + (int)((ge[j] >> 8) & 15u) - 4;
     mn = mn < m0 ? mn : m0;
     mn_after = mn_after < ma ? mn_after : ma;
