@@ -56,15 +56,15 @@ BWD_BYTES_PER_JOINT = 146  # 2 kinds + 48 local + 48 grad_world read, 48 grad_lo
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the
 # kernel sources they were taken on; a changed kernel reports null.
 NCU_TRAFFIC = {
-    # 641.9 MB per launch measured on the 2^24 random walk (2048-element
+    # 641.5 MB per launch measured on the 2^24 random walk (2048-element
     # tiles, profiles/k3_tile_bbox_rw24.md); the 2^26 entry scales it by the
     # element count (traffic tracks the 41 B/elem).
-    "a7dcbb0ad6da91ca": {"rw24": 641.9e6, "rw26": 641.9e6 * 4},
+    "33758ae913d869fc": {"rw24": 641.5e6, "rw26": 641.5e6 * 4},
 }
 # The same for one tb_open_positions call (its three launches summed), keyed
 # by the hash of the compaction sources: the kinds read twice, and the part
 # of the positions that already left L2 when the scatter ended.
-OPEN_NCU_TRAFFIC = {"34128a0e0e5210eb": {"opens26": 139.4e6}}
+OPEN_NCU_TRAFFIC = {"3df41487eb6d93e2": {"opens26": 139.3e6}}
 
 
 def make_workload(name, seed=0):
