@@ -825,23 +825,43 @@ __global__ void __launch_bounds__(1024) k_down_tiles(TreeWs w, int* status) {
     if (SM) sv[buf * TJ + t] = v;
     else M::store(w.t_val[buf], t, v);
   };
+  // world base of tile t = world base of tile link(t) times v(t), link(t) < t:
+  // pointer jumping, first over the links inside each warp's run of 32 tiles
+  // (shuffles, no barrier and no round trip through the link and value
+  // buffers, which live in the workspace when the tiles are many), then over
+  // the block
   bool bad = false;
-  for (int t = threadIdx.x; t < TJ; t += blockDim.x) {
-    const int b = w.t_base[t];
+  const int lane = threadIdx.x & 31;
+  for (int tb = threadIdx.x & ~31; tb < TJ; tb += blockDim.x) {  // warp-uniform
+    const int t = tb + lane;
     int l = -1;
     V v = M::identity();
-    if (b >= 0) {
-      l = b / JT;
-      if (l >= t) {
-        l = -1;
-        bad = true;
-      } else {
-        v = M::load(w.relT, b);
+    if (t < TJ) {
+      const int b = w.t_base[t];
+      if (b >= 0) {
+        l = b / JT;
+        if (l >= t) {
+          l = -1;
+          bad = true;
+        } else {
+          v = M::load(w.relT, b);
+        }
       }
     }
-    link(0, t) = l;
-    set_val(0, t, v);
-    if (l < 0) M::store(w.t_world, t, v);
+    for (int round = 0; round < 5 && ballot(l >= tb) != 0u; ++round) {
+      const int src = l >= tb ? l - tb : lane;
+      const V lv = shfl_idx(v, src);
+      const int ll = shfl_idx(l, src);
+      if (l >= tb) {
+        v = M::combine(lv, v);
+        l = ll;
+      }
+    }
+    if (t < TJ) {
+      link(0, t) = l;
+      set_val(0, t, v);
+      if (l < 0) M::store(w.t_world, t, v);
+    }
   }
   if (bad) atomic_cas_i32(status, ST_OK, ST_INVALID);
   int cur = 0;
